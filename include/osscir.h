@@ -1,0 +1,165 @@
+/*
+ * osscir: one-step spectral CT image reconstruction of three basis-material
+ * maps by MOCCA with m-block-diagonal step-preconditioning, on one GB300 GPU.
+ *
+ * Method: Sidky, Barber, Gilat-Schmidt, Pan, "Three material decomposition
+ * for spectral computed tomography enabled by block-diagonal
+ * step-preconditioning" (arXiv:1801.06263), Sec. 2.  Notation:
+ *   f_{k,m}   material maps, pixel k = iy * n + ix, material m = 0 (PMMA), 1 (Al), 2 (Gd)
+ *   l         ray (view v, detector bin b), l = v * n_bins + b
+ *   w         energy window, 4 windows
+ *   X_{l,k}   length (mm) of ray l inside pixel k
+ *   c^_{w,l}  counts model N_{w,l} sum_i s_{w,l,i} softexp(-sum_{m,k} mu_{m,i} X_{l,k} f_{k,m})  (Eq. finalModel)
+ *   D_TPL     transmission-Poisson Kullback-Leibler data discrepancy                        (Eq. DTPL)
+ *
+ * Conventions for every entry point:
+ *   - The return value is an osscir_status; 0 is success, negative is an error;
+ *     no call aborts the process.
+ *   - Arguments documented as "device" are device pointers that the CALLER owns
+ *     (for example PyTorch tensors); they must stay valid until the enqueued
+ *     work finishes.  Arguments documented as "host" are read during the call
+ *     and copied; the caller may free them on return.
+ *   - Work on device pointers is enqueued on the given stream (0 = the legacy
+ *     default stream) and is asynchronous unless stated.  The context must be
+ *     used from one host thread at a time.
+ *   - Every float4-shaped array is `float[count][4]`, 16-byte aligned, with the
+ *     three materials (or four windows) in the first components.
+ */
+#ifndef OSSCIR_H_
+#define OSSCIR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int osscir_status;
+#define OSSCIR_OK 0
+#define OSSCIR_E_INVALID (-1)  /* an argument failed validation                          */
+#define OSSCIR_E_NOMEM (-2)    /* a device or host allocation failed                      */
+#define OSSCIR_E_CUDA (-3)     /* a CUDA call or kernel launch failed                     */
+#define OSSCIR_E_TIMEOUT (-4)  /* osscir_poll: the request is still running               */
+#define OSSCIR_E_DIVERGED (-5) /* a solve produced a non-finite D_TPL                     */
+#define OSSCIR_E_BUSY (-6)     /* admission refused: memory budget or slots exhausted     */
+#define OSSCIR_E_NOTFOUND (-7) /* unknown ticket                                          */
+
+typedef struct osscir_ctx *osscir_t;
+
+/* Fan-beam geometry with a flat detector (Sec. 3 names a bench-top system; the
+ * geometry itself is not given in the paper).  Image: n x n square pixels of side
+ * pixel_mm centred on the rotation axis, pixel (ix, iy) covering
+ * [x0 + ix h, x0 + (ix+1) h) x [x0 + iy h, x0 + (iy+1) h), x0 = -n h / 2.
+ * View v: source angle start_deg + v * arc_deg / n_views (counter-clockwise),
+ * source at distance sid_mm from the axis, detector line at distance sdd_mm from
+ * the source, bin b centred at (b - (n_bins-1)/2) * bin_mm.  Requires
+ * sid_mm > n * pixel_mm / sqrt(2) (the source outside the image) and sdd_mm > sid_mm. */
+typedef struct {
+    int n;
+    double pixel_mm;
+    int n_views;
+    double arc_deg, start_deg;
+    int n_bins;
+    double bin_mm, sid_mm, sdd_mm;
+} osscir_geometry;
+
+/* Normalised spectral response and incident photons of Eq. (fullModel):
+ *   s  host float[n_bins][n_energies][4]: s_{w,b,i} >= 0 with sum_i s_{w,b,i} = 1 (within 1e-4)
+ *   N  host float[n_bins][4]:             N_{w,b} > 0 (photons per ray and window)
+ * The response depends on the detector bin, not on the view. */
+typedef struct {
+    int n_energies; /* 1 .. 256 */
+    const float *s;
+    const float *N;
+} osscir_spectra;
+
+/* Solver parameters.  lambda is the step-size ratio of the step-preconditioner
+ * (Sec. 2, "must be tuned").  model = 0 uses the per-ray Hessian of Sec. 2 with
+ * its negative eigenvalues removed as the curvature of the local quadratic;
+ * model = 1 uses zero curvature (a preconditioned gradient step).  use_box = 1
+ * constrains every iterate to lo <= f <= hi per material (the convex constraint
+ * set of the one-step framework, Sec. 1); 0 leaves f unconstrained (Sec. 2: the
+ * softexp model avoids the need for constraints). */
+typedef struct {
+    double lambda;
+    int model;
+    int use_box;
+    float lo[3], hi[3];
+} osscir_params;
+
+/* Human-readable name of a status code (static string). */
+const char *osscir_status_string(osscir_status s);
+
+/* Create a reconstruction context on the current CUDA device (Sec. 2, the data
+ * model's fixed inputs: geometry X, spectra s and N, attenuation mu).
+ *   geom, spectra, params: host structs, copied.
+ *   mu: host float[3][n_energies], mu_{m,i} in 1/mm per unit of f (Eq. matdecomp), copied.
+ *   out: receives the handle.
+ * Builds the per-geometry ray tables and footprint tables on the device and
+ * synchronises before returning.  Errors: OSSCIR_E_INVALID (geometry outside
+ * its limits, non-finite or negative inputs, sum_i s != 1), OSSCIR_E_NOMEM,
+ * OSSCIR_E_CUDA.  On error *out is NULL and nothing is leaked. */
+osscir_status osscir_create(const osscir_geometry *geom, const osscir_spectra *spectra, const float *mu,
+                            const osscir_params *params, osscir_t *out);
+
+/* Release every device and host resource of the context (synchronises). NULL is a no-op. */
+osscir_status osscir_destroy(osscir_t h);
+
+/* Sizes of the context: pixels P = n*n, rays L = n_views*n_bins, and the
+ * number of footprint pairs decided in FP64 (any pointer may be NULL). */
+osscir_status osscir_info(osscir_t h, int *n_pixels, int *n_rays, int *n_fp64_pairs);
+
+/* Forward projection g_l = sum_k X_{l,k} x_k of four channels (the X of Eq. fullModel).
+ *   x: device float[P][4] (input), g: device float[L][4] (output). */
+osscir_status osscir_forward(osscir_t h, const float *x, float *g, void *stream);
+
+/* Back-projection (the adjoint X^T) img_k = sum_l X_{l,k} rf_l of four channels.
+ *   rf: device float[L][4] (input), img: device float[P][4] (output). */
+osscir_status osscir_backproject(osscir_t h, const float *rf, float *img, void *stream);
+
+/* Expected counts c^(f) of Eq. (finalModel) for material maps f.
+ *   f: device float[P][4] (first three components used), chat: device float[L][4] (output). */
+osscir_status osscir_simulate(osscir_t h, const float *f, float *chat, void *stream);
+
+/* Load measured counts c_{w,l} (Eq. DTPL) and reset the solver state to
+ * x_0 = xbar_0 = 0, y_0 = 0, iteration 0.
+ *   c: device float[L][4], c >= 0 (copied on the stream). */
+osscir_status osscir_set_counts(osscir_t h, const float *c, void *stream);
+
+/* Run n_iters MOCCA iterations (Sec. 1: local convex quadratic, removal of
+ * negative curvature, one preconditioned CPPD step; Sec. 2: the m-block-diagonal
+ * Sigma and T).  Library-owned state; asynchronous on the stream. */
+osscir_status osscir_mocca_step(osscir_t h, int n_iters, void *stream);
+
+/* Copy the current material maps x_n to x_out: device float[P][4]. */
+osscir_status osscir_get_maps(osscir_t h, float *x_out, void *stream);
+
+/* Checkpoint / resume of the solver state (x_n, xbar_n, y_n, n).  All arrays
+ * are device pointers: x, xbar float[P][4], y float[L][4].  get copies out,
+ * set copies in; resuming from a saved state reproduces the uninterrupted
+ * iterates bit for bit.  iter: host int. */
+osscir_status osscir_get_state(osscir_t h, float *x, float *xbar, float *y, int *iter, void *stream);
+osscir_status osscir_set_state(osscir_t h, const float *x, const float *xbar, const float *y, int iter,
+                               void *stream);
+
+/* D_TPL (Eq. DTPL) of the loaded counts: which = 0 evaluates it at the current
+ * maps x_n (one extra forward projection); which = 1 returns the value the last
+ * iteration computed at its expansion point xbar.  Synchronises the stream;
+ * out: host double. */
+osscir_status osscir_dtpl(osscir_t h, int which, double *out, void *stream);
+
+/* Footprint dumps for verification: for rays [l0, l0+n) (or pixels [k0, k0+n))
+ * the pixels (rays) with nonzero X_{l,k} as the forward (back-)projection uses
+ * them, and their weights.  cnt: device int[n]; idx: device int[n][cap];
+ * wt: device float[n][cap]; entries beyond cap are counted but not stored. */
+osscir_status osscir_footprint_rays(osscir_t h, int l0, int n, int cap, int *cnt, int *idx, float *wt,
+                                    void *stream);
+osscir_status osscir_footprint_pixels(osscir_t h, int k0, int n, int cap, int *cnt, int *idx, float *wt,
+                                      void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSSCIR_H_ */

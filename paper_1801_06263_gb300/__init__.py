@@ -1,0 +1,94 @@
+"""One-step three-material spectral CT reconstruction (MOCCA with m-block-diagonal
+step-preconditioning, arXiv:1801.06263) on a GB300 GPU.
+
+The compute path is the CUDA library libosscir.so (C-ABI in include/osscir.h);
+``_lib`` mirrors its entry points one to one and ``Reconstructor`` holds one
+context with its device tensors.  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+from . import inputs
+from ._lib import (OsscirError, load, osscir_backproject, osscir_create, osscir_destroy, osscir_dtpl,
+                   osscir_footprint_pixels, osscir_footprint_rays, osscir_forward, osscir_get_maps,
+                   osscir_get_state, osscir_info, osscir_mocca_step, osscir_set_counts, osscir_set_state,
+                   osscir_simulate)
+
+__all__ = ["inputs", "Reconstructor", "OsscirError", "load"]
+
+
+class Reconstructor:
+    """One reconstruction context on the current CUDA device.
+
+    Device arrays are torch float32 tensors: maps [P, 4] (PMMA, Al, Gd, unused),
+    ray fields [L, 4] (four windows or four channels).
+    """
+
+    def __init__(self, geom, spectra, lam: float, *, model: int = 0, box=None, mu=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.geom = geom
+        self.handle = osscir_create(geom, spectra.s, spectra.N, spectra.mu if mu is None else mu, lam,
+                                    model=model, box=box)
+        self.n_pixels, self.n_rays, self.n_fp64_pairs = osscir_info(self.handle)
+
+    # -- tensors
+    def _new(self, rows):
+        import torch
+        return torch.zeros((rows, 4), dtype=torch.float32, device="cuda")
+
+    def image(self):
+        return self._new(self.n_pixels)
+
+    def rays(self):
+        return self._new(self.n_rays)
+
+    # -- operators
+    def forward(self, x, out=None, stream=None):
+        out = self.rays() if out is None else out
+        osscir_forward(self.handle, x, out, stream)
+        return out
+
+    def backproject(self, rf, out=None, stream=None):
+        out = self.image() if out is None else out
+        osscir_backproject(self.handle, rf, out, stream)
+        return out
+
+    def simulate(self, f, out=None, stream=None):
+        out = self.rays() if out is None else out
+        osscir_simulate(self.handle, f, out, stream)
+        return out
+
+    # -- solver
+    def set_counts(self, c, stream=None):
+        osscir_set_counts(self.handle, c, stream)
+
+    def step(self, n_iters: int, stream=None):
+        osscir_mocca_step(self.handle, n_iters, stream)
+
+    def maps(self, out=None, stream=None):
+        out = self.image() if out is None else out
+        osscir_get_maps(self.handle, out, stream)
+        return out
+
+    def dtpl(self, which: int = 0, stream=None) -> float:
+        return osscir_dtpl(self.handle, which, stream)
+
+    def get_state(self, stream=None):
+        x, xbar, y = self.image(), self.image(), self.rays()
+        it = osscir_get_state(self.handle, x, xbar, y, stream)
+        return x, xbar, y, it
+
+    def set_state(self, x, xbar, y, iteration, stream=None):
+        osscir_set_state(self.handle, x, xbar, y, iteration, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            osscir_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,213 @@
+"""Thin ctypes binding of the C-ABI in include/osscir.h (argument marshalling only).
+
+Every function here forwards to the CUDA library libosscir.so with the same
+name; torch tensors are passed as raw device pointers and streams as raw
+cudaStream_t handles.  There is no CPU fallback: if the library is missing or
+a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OSSCIR_OK = 0
+OSSCIR_E_INVALID = -1
+OSSCIR_E_NOMEM = -2
+OSSCIR_E_CUDA = -3
+OSSCIR_E_TIMEOUT = -4
+OSSCIR_E_DIVERGED = -5
+OSSCIR_E_BUSY = -6
+OSSCIR_E_NOTFOUND = -7
+
+# Every symbol include/osscir.h declares.
+EXPORTS = (
+    "osscir_status_string", "osscir_create", "osscir_destroy", "osscir_info", "osscir_forward",
+    "osscir_backproject", "osscir_simulate", "osscir_set_counts", "osscir_mocca_step", "osscir_get_maps",
+    "osscir_get_state", "osscir_set_state", "osscir_dtpl", "osscir_footprint_rays",
+    "osscir_footprint_pixels",
+)
+
+
+class OsscirError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        super().__init__(f"{fn} failed: {status} ({_status_string(status)})")
+
+
+class Geometry(ct.Structure):
+    _fields_ = [("n", ct.c_int), ("pixel_mm", ct.c_double), ("n_views", ct.c_int),
+                ("arc_deg", ct.c_double), ("start_deg", ct.c_double), ("n_bins", ct.c_int),
+                ("bin_mm", ct.c_double), ("sid_mm", ct.c_double), ("sdd_mm", ct.c_double)]
+
+
+class Spectra(ct.Structure):
+    _fields_ = [("n_energies", ct.c_int), ("s", ct.POINTER(ct.c_float)), ("N", ct.POINTER(ct.c_float))]
+
+
+class Params(ct.Structure):
+    _fields_ = [("lambda_", ct.c_double), ("model", ct.c_int), ("use_box", ct.c_int),
+                ("lo", ct.c_float * 3), ("hi", ct.c_float * 3)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libosscir.so (building it first if allowed); raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built: {_build.LIB}")
+        _build.build()
+    L = ct.CDLL(_build.LIB)
+    vp, ip, fp, dp = ct.c_void_p, ct.POINTER(ct.c_int), ct.c_void_p, ct.POINTER(ct.c_double)
+    sig = {
+        "osscir_status_string": ([ct.c_int], ct.c_char_p),
+        "osscir_create": ([ct.POINTER(Geometry), ct.POINTER(Spectra), ct.POINTER(ct.c_float),
+                           ct.POINTER(Params), ct.POINTER(ct.c_void_p)], ct.c_int),
+        "osscir_destroy": ([vp], ct.c_int),
+        "osscir_info": ([vp, ip, ip, ip], ct.c_int),
+        "osscir_forward": ([vp, fp, fp, vp], ct.c_int),
+        "osscir_backproject": ([vp, fp, fp, vp], ct.c_int),
+        "osscir_simulate": ([vp, fp, fp, vp], ct.c_int),
+        "osscir_set_counts": ([vp, fp, vp], ct.c_int),
+        "osscir_mocca_step": ([vp, ct.c_int, vp], ct.c_int),
+        "osscir_get_maps": ([vp, fp, vp], ct.c_int),
+        "osscir_get_state": ([vp, fp, fp, fp, ip, vp], ct.c_int),
+        "osscir_set_state": ([vp, fp, fp, fp, ct.c_int, vp], ct.c_int),
+        "osscir_dtpl": ([vp, ct.c_int, dp, vp], ct.c_int),
+        "osscir_footprint_rays": ([vp, ct.c_int, ct.c_int, ct.c_int, vp, vp, vp, vp], ct.c_int),
+        "osscir_footprint_pixels": ([vp, ct.c_int, ct.c_int, ct.c_int, vp, vp, vp, vp], ct.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _status_string(s: int) -> str:
+    try:
+        return load().osscir_status_string(int(s)).decode()
+    except Exception:  # pragma: no cover - only used for messages
+        return "?"
+
+
+def _check(fn, st):
+    if st != OSSCIR_OK:
+        raise OsscirError(fn, st)
+
+
+def _ptr(t):
+    """Device pointer of a contiguous torch tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ct.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ct.c_void_p(stream)
+    return ct.c_void_p(stream.cuda_stream)
+
+
+# --------------------------------------------------------------------------- C-ABI mirrors
+
+def osscir_create(geom, s, N, mu, lam, model=0, box=None):
+    """geom: object with the osscir_geometry fields; s [n_bins, nE, 4], N [n_bins, 4],
+    mu [3, nE] host arrays (copied).  Returns the handle (int)."""
+    L = load()
+    s32 = np.ascontiguousarray(s, dtype=np.float32)
+    N32 = np.ascontiguousarray(N, dtype=np.float32)
+    mu32 = np.ascontiguousarray(mu, dtype=np.float32)
+    g = Geometry(int(geom.n), float(geom.pixel_mm), int(geom.n_views), float(geom.arc_deg),
+                 float(geom.start_deg), int(geom.n_bins), float(geom.bin_mm), float(geom.sid_mm),
+                 float(geom.sdd_mm))
+    sp = Spectra(int(s32.shape[1]), s32.ctypes.data_as(ct.POINTER(ct.c_float)),
+                 N32.ctypes.data_as(ct.POINTER(ct.c_float)))
+    lo, hi = (box if box is not None else ((0.0,) * 3, (0.0,) * 3))
+    p = Params(float(lam), int(model), int(box is not None), (ct.c_float * 3)(*lo), (ct.c_float * 3)(*hi))
+    h = ct.c_void_p()
+    _check("osscir_create", L.osscir_create(ct.byref(g), ct.byref(sp),
+                                            mu32.ctypes.data_as(ct.POINTER(ct.c_float)), ct.byref(p),
+                                            ct.byref(h)))
+    return h.value
+
+
+def osscir_destroy(h):
+    _check("osscir_destroy", load().osscir_destroy(ct.c_void_p(h)))
+
+
+def osscir_info(h):
+    P, Lr, E = ct.c_int(), ct.c_int(), ct.c_int()
+    _check("osscir_info", load().osscir_info(ct.c_void_p(h), ct.byref(P), ct.byref(Lr), ct.byref(E)))
+    return P.value, Lr.value, E.value
+
+
+def osscir_forward(h, x, g, stream=None):
+    _check("osscir_forward", load().osscir_forward(ct.c_void_p(h), _ptr(x), _ptr(g), _stream(stream)))
+
+
+def osscir_backproject(h, rf, img, stream=None):
+    _check("osscir_backproject", load().osscir_backproject(ct.c_void_p(h), _ptr(rf), _ptr(img),
+                                                           _stream(stream)))
+
+
+def osscir_simulate(h, f, chat, stream=None):
+    _check("osscir_simulate", load().osscir_simulate(ct.c_void_p(h), _ptr(f), _ptr(chat), _stream(stream)))
+
+
+def osscir_set_counts(h, c, stream=None):
+    _check("osscir_set_counts", load().osscir_set_counts(ct.c_void_p(h), _ptr(c), _stream(stream)))
+
+
+def osscir_mocca_step(h, n_iters, stream=None):
+    _check("osscir_mocca_step", load().osscir_mocca_step(ct.c_void_p(h), int(n_iters), _stream(stream)))
+
+
+def osscir_get_maps(h, x_out, stream=None):
+    _check("osscir_get_maps", load().osscir_get_maps(ct.c_void_p(h), _ptr(x_out), _stream(stream)))
+
+
+def osscir_get_state(h, x, xbar, y, stream=None):
+    it = ct.c_int()
+    _check("osscir_get_state", load().osscir_get_state(ct.c_void_p(h), _ptr(x), _ptr(xbar), _ptr(y),
+                                                       ct.byref(it), _stream(stream)))
+    return it.value
+
+
+def osscir_set_state(h, x, xbar, y, iteration, stream=None):
+    _check("osscir_set_state", load().osscir_set_state(ct.c_void_p(h), _ptr(x), _ptr(xbar), _ptr(y),
+                                                       int(iteration), _stream(stream)))
+
+
+def osscir_dtpl(h, which=0, stream=None):
+    out = ct.c_double()
+    _check("osscir_dtpl", load().osscir_dtpl(ct.c_void_p(h), int(which), ct.byref(out), _stream(stream)))
+    return out.value
+
+
+def osscir_footprint_rays(h, l0, n, cap, cnt, idx, wt, stream=None):
+    _check("osscir_footprint_rays", load().osscir_footprint_rays(
+        ct.c_void_p(h), int(l0), int(n), int(cap), _ptr(cnt), _ptr(idx), _ptr(wt), _stream(stream)))
+
+
+def osscir_footprint_pixels(h, k0, n, cap, cnt, idx, wt, stream=None):
+    _check("osscir_footprint_pixels", load().osscir_footprint_pixels(
+        ct.c_void_p(h), int(k0), int(n), int(cap), _ptr(cnt), _ptr(idx), _ptr(wt), _stream(stream)))

@@ -1,0 +1,618 @@
+// Per-iteration kernels of MOCCA with the m-block-diagonal SPC (Sec. 2) and the
+// plain projectors behind osscir_forward / osscir_backproject / osscir_simulate.
+//
+// One iteration is two fused launches (plus a tiny deterministic reduction):
+//   k_mocca_fwd (ray-driven):   g = X xbar for the three maps, the counts model
+//       of Eq. (finalModel) summed over energies (compensated), D_TPL of
+//       Eq. (DTPL), alpha_w = sum_i A_wi mu_i (K = alpha X, Eq. aeq), the per-ray
+//       Hessian of Sec. 2 in g with its negative eigenvalues removed (FP64),
+//       the dual step matrix Sigma^-1 = lambda |alpha_w| (X 1)_l, the exact
+//       preconditioned dual prox y' = y - Sigma (W + Sigma)^-1 (y - r), and the
+//       per-ray products b = alpha^T y' and S = sum_w alpha_w alpha_w^T / |alpha_w|.
+//   k_mocca_bp (pixel-driven):  v_k = sum_l X_lk b_l (= K^T y') and
+//       P_k = sum_l X_lk S_l (so T^-1_k = P_k / lambda, the m-block SPC), the
+//       FP64 3x3 solve, the primal step (optionally onto a box) and the
+//       extrapolation xbar' = 2 x' - x.
+#include "osscir_internal.cuh"
+#include "osscir_launch.h"
+
+namespace osscir {
+namespace {
+
+constexpr int kMaxEnergies = 256;
+constexpr int kSmemStride = 12;   // per energy: mu0 mu1 mu2 | m00 m01 m02 m11 m12 m22 | pad
+
+__device__ __forceinline__ void neumaier(float& s, float& c, float t) {
+    const float u = s + t;
+    c += (fabsf(s) >= fabsf(t)) ? ((s - u) + t) : ((t - u) + s);
+    s = u;
+}
+
+// One term of Eq. (DTPL), c^ - c - c log(c^/c) = c (u - log(1 + u)) with
+// u = (c^ - c) / c; a series is used for small |u| (cancellation), c = 0 gives c^.
+__device__ __forceinline__ float dtpl_term(float chat, float c) {
+    if (!(c > 0.0f)) return chat;
+    const float u = (chat - c) / c;
+    if (fabsf(u) < 0.0625f) {
+        const float p = 0.5f - u * (1.0f / 3.0f - u * (0.25f - u * (0.2f - u * (1.0f / 6.0f - u * (1.0f / 7.0f - u * 0.125f)))));
+        return c * u * u * p;
+    }
+    return chat - c - c * logf(chat / c);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    return s;
+}
+
+__device__ __forceinline__ void load_mu_smem(const SpecD& S, float* sm) {
+    const int nE = S.n_energies;
+    for (int i = threadIdx.x; i < nE; i += blockDim.x) {
+        const float m0 = S.mu[i], m1 = S.mu[nE + i], m2 = S.mu[2 * nE + i];
+        float* q = sm + kSmemStride * i;
+        q[0] = m0; q[1] = m1; q[2] = m2;
+        q[3] = m0 * m0; q[4] = m0 * m1; q[5] = m0 * m2;
+        q[6] = m1 * m1; q[7] = m1 * m2; q[8] = m2 * m2;
+        q[9] = q[10] = q[11] = 0.f;
+    }
+}
+
+// softexp(x), softexp'(x), softexp''(x) (Sec. 2): exp below 0, x + 1 above.
+__device__ __forceinline__ void sexp3(float x, float& e0, float& e1, float& e2) {
+    if (x <= 0.0f) {
+        e0 = expf(x);
+        e1 = e0;
+        e2 = e0;
+    } else {
+        e0 = x + 1.0f;
+        e1 = 1.0f;
+        e2 = 0.0f;
+    }
+}
+
+template <class Visit>
+__device__ __forceinline__ void ray_pixels(const GeomC& C, const ExcTable& E, const float4& r0, float ex, float ey,
+                                           int l, Visit&& visit) {
+    for_each_candidate(r0, C.grid, C.margin_mm, [&](int ix, int iy) {
+        const float w = x_weight(r0, ex, ey, C.grid, E, l, ix, iy);
+        if (w != 0.0f) visit(iy * C.grid.n + ix, w);
+    });
+}
+
+template <class Visit>
+__device__ __forceinline__ void pixel_rays(const GeomC& C, const ExcTable& E, const RayRec* rec,
+                                           const ViewF* views, int ix, int iy, Visit&& visit) {
+    for (int v = 0; v < C.n_views; ++v) {
+        int blo, bhi;
+        pixel_bin_range(C, views[v], ix, iy, blo, bhi);
+        for (int b = blo; b <= bhi; ++b) {
+            const int l = v * C.n_bins + b;
+            const float4 r0 = __ldg(&rec[l].r0);
+            const float4 r1 = __ldg(&rec[l].r1);
+            const float w = x_weight(r0, r1.x, r1.y, C.grid, E, l, ix, iy);
+            if (w != 0.0f) visit(l, w, r1);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ plain projectors
+
+__global__ void k_forward4(GeomC C, ExcTable E, const RayRec* rec, const float4* x, float4* g, int L) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= L) return;
+    const float4 r0 = rec[l].r0, r1 = rec[l].r1;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) {
+        const float4 v = __ldg(x + k);
+        acc.x = fmaf(w, v.x, acc.x);
+        acc.y = fmaf(w, v.y, acc.y);
+        acc.z = fmaf(w, v.z, acc.z);
+        acc.w = fmaf(w, v.w, acc.w);
+    });
+    g[l] = acc;
+}
+
+__global__ void k_backproject4(GeomC C, ExcTable E, const RayRec* rec, const ViewF* views, const float4* rf,
+                               float4* img) {
+    const int ix = blockIdx.x * kBpTileX + threadIdx.x, iy = blockIdx.y * kBpTileY + threadIdx.y;
+    if (ix >= C.grid.n || iy >= C.grid.n) return;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    pixel_rays(C, E, rec, views, ix, iy, [&](int l, float w, const float4&) {
+        const float4 v = __ldg(rf + l);
+        acc.x = fmaf(w, v.x, acc.x);
+        acc.y = fmaf(w, v.y, acc.y);
+        acc.z = fmaf(w, v.z, acc.z);
+        acc.w = fmaf(w, v.w, acc.w);
+    });
+    img[iy * C.grid.n + ix] = acc;
+}
+
+// c^(f) (Eq. finalModel) for every ray; with c != nullptr also the D_TPL block partials.
+__global__ void __launch_bounds__(kFwdThreads) k_counts(GeomC C, ExcTable E, const RayRec* rec, SpecD S,
+                                                        const float4* f, float4* chat, const float4* c,
+                                                        double* part, int L) {
+    __shared__ float sm[kSmemStride * kMaxEnergies];
+    __shared__ double red[kFwdThreads / 32];
+    load_mu_smem(S, sm);
+    __syncthreads();
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    double dsum = 0.0;
+    if (l < L) {
+        const float4 r0 = rec[l].r0, r1 = rec[l].r1;
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) {
+            const float4 v = __ldg(f + k);
+            g0 = fmaf(w, v.x, g0);
+            g1 = fmaf(w, v.y, g1);
+            g2 = fmaf(w, v.z, g2);
+        });
+        const int b = l % C.n_bins, nb = C.n_bins;
+        float Ds[4] = {0.f, 0.f, 0.f, 0.f}, Dc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int i = 0; i < S.n_energies; ++i) {
+            const float* q = sm + kSmemStride * i;
+            const float p = fmaf(q[2], g2, fmaf(q[1], g1, q[0] * g0));
+            float e0, e1, e2;
+            sexp3(-p, e0, e1, e2);
+            const float4 s = __ldg(S.s4 + (size_t)i * nb + b);
+            neumaier(Ds[0], Dc[0], s.x * e0);
+            neumaier(Ds[1], Dc[1], s.y * e0);
+            neumaier(Ds[2], Dc[2], s.z * e0);
+            neumaier(Ds[3], Dc[3], s.w * e0);
+        }
+        const float4 N = __ldg(S.N4 + b);
+        const float4 ch = make_float4(N.x * (Ds[0] + Dc[0]), N.y * (Ds[1] + Dc[1]), N.z * (Ds[2] + Dc[2]),
+                                      N.w * (Ds[3] + Dc[3]));
+        if (chat) chat[l] = ch;
+        if (c) {
+            const float4 cc = c[l];
+            dsum = (double)dtpl_term(ch.x, cc.x) + (double)dtpl_term(ch.y, cc.y) + (double)dtpl_term(ch.z, cc.z) +
+                   (double)dtpl_term(ch.w, cc.w);
+        }
+    }
+    if (part) {
+        const double s = block_sum(dsum, red);
+        if (threadIdx.x == 0) part[blockIdx.x] = s;
+    }
+}
+
+// ------------------------------------------------------------------ FP64 3x3 / 4x4 algebra
+
+// Symmetric 3x3 stored as (00, 01, 02, 11, 12, 22).
+// Negative-curvature removal H+ = V max(Lambda, 0) V^T.  A positive-definite H
+// (Sylvester's criterion) is returned unchanged; otherwise cyclic Jacobi.
+__device__ void clip_psd3(double h[6]) {
+    const double m2 = h[0] * h[3] - h[1] * h[1];
+    const double det = h[0] * (h[3] * h[5] - h[4] * h[4]) - h[1] * (h[1] * h[5] - h[4] * h[2]) +
+                       h[2] * (h[1] * h[4] - h[3] * h[2]);
+    if (h[0] > 0.0 && m2 > 0.0 && det > 0.0) return;
+    double a[3][3] = {{h[0], h[1], h[2]}, {h[1], h[3], h[4]}, {h[2], h[4], h[5]}};
+    double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        const double dia = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+        if (off <= 1e-34 * dia || off == 0.0) break;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int p = t == 2 ? 1 : 0, q = t == 0 ? 1 : 2, r = 3 - p - q;
+            const double apq = a[p][q];
+            if (apq == 0.0) continue;
+            const double tau = (a[q][q] - a[p][p]) / (2.0 * apq);
+            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            const double c = rsqrt(1.0 + tt * tt), s = tt * c;
+            a[p][p] -= tt * apq;
+            a[q][q] += tt * apq;
+            a[p][q] = a[q][p] = 0.0;
+            const double arp = a[r][p], arq = a[r][q];
+            a[r][p] = a[p][r] = c * arp - s * arq;
+            a[r][q] = a[q][r] = s * arp + c * arq;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double vp = V[i][p], vq = V[i][q];
+                V[i][p] = c * vp - s * vq;
+                V[i][q] = s * vp + c * vq;
+            }
+        }
+    }
+    const double l0 = fmax(a[0][0], 0.0), l1 = fmax(a[1][1], 0.0), l2 = fmax(a[2][2], 0.0);
+    const int idx[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+        const int i = idx[e][0], j = idx[e][1];
+        h[e] = l0 * V[i][0] * V[j][0] + l1 * V[i][1] * V[j][1] + l2 * V[i][2] * V[j][2];
+    }
+}
+
+// Inverse of a symmetric 3x3 (adjugate / determinant); returns false if singular.
+__device__ __forceinline__ bool inv_sym3(const double a[6], double o[6]) {
+    const double c00 = a[3] * a[5] - a[4] * a[4];
+    const double c01 = a[2] * a[4] - a[1] * a[5];
+    const double c02 = a[1] * a[4] - a[2] * a[3];
+    const double c11 = a[0] * a[5] - a[2] * a[2];
+    const double c12 = a[1] * a[2] - a[0] * a[4];
+    const double c22 = a[0] * a[3] - a[1] * a[1];
+    const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    if (!(det != 0.0) || !isfinite(det)) return false;
+    const double id = 1.0 / det;
+    o[0] = c00 * id; o[1] = c01 * id; o[2] = c02 * id;
+    o[3] = c11 * id; o[4] = c12 * id; o[5] = c22 * id;
+    return true;
+}
+
+// Entry (i, j) of a symmetric 3x3 packed as (00, 01, 02, 11, 12, 22).
+__device__ __forceinline__ double sym3(const double a[6], int i, int j) {
+    const int r = i < j ? i : j, c = i < j ? j : i;
+    return a[r == 0 ? c : (r == 1 ? 2 + c : 5)];
+}
+
+// Dual step of one ray (see the file header).  Returns y' in yo.
+__device__ void ray_dual(const double al[4][3], const double cw[4], const double rw[4], const double invD[4],
+                         const float Gm[4][6], double X1, float lambda, int model, const double y[4],
+                         double yo[4]) {
+    if (!(X1 > 0.0)) {
+#pragma unroll
+        for (int w = 0; w < 4; ++w) yo[w] = y[w];
+        return;
+    }
+    double sig[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const double nw = sqrt(al[w][0] * al[w][0] + al[w][1] * al[w][1] + al[w][2] * al[w][2]);
+        sig[w] = 1.0 / ((double)lambda * nw * X1);
+    }
+    if (model == 1) {
+#pragma unroll
+        for (int w = 0; w < 4; ++w) yo[w] = rw[w];
+        return;
+    }
+    // H = sum_w c_w alpha_w alpha_w^T - sum_w (r_w / D_w) Gamma_w, Gamma_w = sum_i s_wi e''_i mu_i mu_i^T
+    double H[6];
+    {
+        const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+            double acc = 0.0;
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                acc += cw[w] * al[w][ij[e][0]] * al[w][ij[e][1]] - rw[w] * invD[w] * (double)Gm[w][e];
+            H[e] = acc;
+        }
+    }
+    clip_psd3(H);
+    // G = (alpha^T alpha)^-1 alpha^T  (3 x 4);  W = G^T H+ G  (4 x 4)
+    double A[6];
+    A[0] = A[1] = A[2] = A[3] = A[4] = A[5] = 0.0;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        A[0] += al[w][0] * al[w][0]; A[1] += al[w][0] * al[w][1]; A[2] += al[w][0] * al[w][2];
+        A[3] += al[w][1] * al[w][1]; A[4] += al[w][1] * al[w][2]; A[5] += al[w][2] * al[w][2];
+    }
+    double Ai[6];
+    double M[4][4];
+    if (inv_sym3(A, Ai)) {
+        double G[3][4], HG[3][4];
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                G[m][w] = sym3(Ai, m, 0) * al[w][0] + sym3(Ai, m, 1) * al[w][1] + sym3(Ai, m, 2) * al[w][2];
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                HG[m][w] = sym3(H, m, 0) * G[0][w] + sym3(H, m, 1) * G[1][w] + sym3(H, m, 2) * G[2][w];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) M[i][j] = G[0][i] * HG[0][j] + G[1][i] * HG[1][j] + G[2][i] * HG[2][j];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) M[i][j] = 0.0;
+    }
+#pragma unroll
+    for (int w = 0; w < 4; ++w) M[w][w] += sig[w];
+    // Cholesky of the SPD W + Sigma, then (W + Sigma) u = y - r
+    double Lm[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        double d = M[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= Lm[j][k] * Lm[j][k];
+        d = sqrt(fmax(d, 1e-300));
+        Lm[j][j] = d;
+        const double id = 1.0 / d;
+#pragma unroll
+        for (int i = j + 1; i < 4; ++i) {
+            double s = M[i][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= Lm[i][k] * Lm[j][k];
+            Lm[i][j] = s * id;
+        }
+    }
+    double z[4], u[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        double s = y[i] - rw[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) s -= Lm[i][k] * z[k];
+        z[i] = s / Lm[i][i];
+    }
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+        double s = z[i];
+#pragma unroll
+        for (int k = i + 1; k < 4; ++k) s -= Lm[k][i] * u[k];
+        u[i] = s / Lm[i][i];
+    }
+#pragma unroll
+    for (int w = 0; w < 4; ++w) yo[w] = y[w] - sig[w] * u[w];
+}
+
+// ------------------------------------------------------------------ fused MOCCA kernels
+
+__global__ void __launch_bounds__(kFwdThreads) k_mocca_fwd(GeomC C, ExcTable E, RayRec* rec, SpecD S, StepParams P,
+                                                           SolveD D, int L) {
+    __shared__ float sm[kSmemStride * kMaxEnergies];
+    __shared__ double red[kFwdThreads / 32];
+    load_mu_smem(S, sm);
+    __syncthreads();
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    double dsum = 0.0;
+    if (l < L) {
+        const float4 r0 = rec[l].r0, r1 = rec[l].r1;
+        // a1: line integrals of the three maps at the expansion point xbar
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) {
+            const float4 v = __ldg(D.xbar + k);
+            g0 = fmaf(w, v.x, g0);
+            g1 = fmaf(w, v.y, g1);
+            g2 = fmaf(w, v.z, g2);
+        });
+        // a2/a3: counts model and its first/second-order pieces, summed over energies
+        const int b = l % C.n_bins, nb = C.n_bins;
+        float Ds[4] = {0.f, 0.f, 0.f, 0.f}, Dc[4] = {0.f, 0.f, 0.f, 0.f};
+        float An[4][3], Gm[4][6];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+#pragma unroll
+            for (int m = 0; m < 3; ++m) An[w][m] = 0.f;
+#pragma unroll
+            for (int e = 0; e < 6; ++e) Gm[w][e] = 0.f;
+        }
+        for (int i = 0; i < S.n_energies; ++i) {
+            const float4 qa = *reinterpret_cast<const float4*>(sm + kSmemStride * i);
+            const float4 qb = *reinterpret_cast<const float4*>(sm + kSmemStride * i + 4);
+            const float4 qc = *reinterpret_cast<const float4*>(sm + kSmemStride * i + 8);
+            const float p = fmaf(qa.z, g2, fmaf(qa.y, g1, qa.x * g0));
+            float e0, e1, e2;
+            sexp3(-p, e0, e1, e2);
+            const float4 s4 = __ldg(S.s4 + (size_t)i * nb + b);
+            const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+            const float mm[6] = {qa.w, qb.x, qb.y, qb.z, qb.w, qc.x};
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                neumaier(Ds[w], Dc[w], sv[w] * e0);
+                const float a = sv[w] * e1;
+                An[w][0] = fmaf(a, qa.x, An[w][0]);
+                An[w][1] = fmaf(a, qa.y, An[w][1]);
+                An[w][2] = fmaf(a, qa.z, An[w][2]);
+                const float gq = sv[w] * e2;
+#pragma unroll
+                for (int e = 0; e < 6; ++e) Gm[w][e] = fmaf(gq, mm[e], Gm[w][e]);
+            }
+        }
+        const float4 N = __ldg(S.N4 + b);
+        const float4 cc = D.c[l];
+        const float4 yy = D.y[l];
+        const float Nv[4] = {N.x, N.y, N.z, N.w}, cv[4] = {cc.x, cc.y, cc.z, cc.w};
+        double al[4][3], cw[4], rw[4], invD[4], y[4] = {yy.x, yy.y, yy.z, yy.w}, yo[4];
+        float dt = 0.f;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const double Dw = (double)Ds[w] + (double)Dc[w];
+            invD[w] = 1.0 / Dw;
+            const double chat = (double)Nv[w] * Dw;
+            cw[w] = (double)cv[w];
+            rw[w] = cw[w] - chat;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) al[w][m] = (double)An[w][m] * invD[w];
+            dt += dtpl_term((float)chat, cv[w]);
+        }
+        dsum = (double)dt;
+        // a4/a5: per-ray curvature with negative-curvature removal and the dual step
+        ray_dual(al, cw, rw, invD, Gm, (double)__ldg(D.chord + l), P.lambda, P.model, y, yo);
+        D.y[l] = make_float4((float)yo[0], (float)yo[1], (float)yo[2], (float)yo[3]);
+        // b = alpha^T y',  S = sum_w alpha_w alpha_w^T / |alpha_w|
+        double bb[3] = {0.0, 0.0, 0.0}, Sm[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const double nw = sqrt(al[w][0] * al[w][0] + al[w][1] * al[w][1] + al[w][2] * al[w][2]);
+            const double inw = nw > 0.0 ? 1.0 / nw : 0.0;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) bb[m] += al[w][m] * yo[w];
+            Sm[0] += al[w][0] * al[w][0] * inw; Sm[1] += al[w][0] * al[w][1] * inw;
+            Sm[2] += al[w][0] * al[w][2] * inw; Sm[3] += al[w][1] * al[w][1] * inw;
+            Sm[4] += al[w][1] * al[w][2] * inw; Sm[5] += al[w][2] * al[w][2] * inw;
+        }
+        rec[l].r1 = make_float4(r1.x, r1.y, (float)bb[0], (float)bb[1]);
+        rec[l].r2 = make_float4((float)bb[2], (float)Sm[0], (float)Sm[1], (float)Sm[2]);
+        rec[l].r3 = make_float4((float)Sm[3], (float)Sm[4], (float)Sm[5], 0.f);
+    }
+    const double s = block_sum(dsum, red);
+    if (threadIdx.x == 0) D.dtpl_part[blockIdx.x] = s;
+}
+
+// Box-constrained primal step: argmin over lo <= x <= hi of 1/2 (x - t)^T Q (x - t),
+// by trying every active set and keeping the feasible candidate of least objective.
+__device__ void box_prox3(const double Q[3][3], const double t[3], const float lo[3], const float hi[3],
+                          double xo[3]) {
+    double best = 1e308;
+    xo[0] = fmin(fmax(t[0], (double)lo[0]), (double)hi[0]);
+    xo[1] = fmin(fmax(t[1], (double)lo[1]), (double)hi[1]);
+    xo[2] = fmin(fmax(t[2], (double)lo[2]), (double)hi[2]);
+    for (int code = 0; code < 27; ++code) {
+        const int st[3] = {code % 3, (code / 3) % 3, code / 9};
+        double xc[3];
+        int fr[3], nf = 0;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            if (st[m] == 1) xc[m] = lo[m];
+            else if (st[m] == 2) xc[m] = hi[m];
+            else fr[nf++] = m;
+        }
+        bool ok = true;
+        if (nf > 0) {
+            double Mf[3][3], rhs[3];
+            for (int a = 0; a < nf; ++a) {
+                double acc = 0.0;
+                for (int m = 0; m < 3; ++m)
+                    if (st[m] != 0) acc -= Q[fr[a]][m] * (xc[m] - t[m]);
+                rhs[a] = acc;
+                for (int c2 = 0; c2 < nf; ++c2) Mf[a][c2] = Q[fr[a]][fr[c2]];
+            }
+            // Gaussian elimination (nf <= 3, SPD sub-block)
+            for (int c2 = 0; c2 < nf && ok; ++c2) {
+                if (!(Mf[c2][c2] > 0.0)) { ok = false; break; }
+                for (int r2 = c2 + 1; r2 < nf; ++r2) {
+                    const double f = Mf[r2][c2] / Mf[c2][c2];
+                    for (int k = c2; k < nf; ++k) Mf[r2][k] -= f * Mf[c2][k];
+                    rhs[r2] -= f * rhs[c2];
+                }
+            }
+            if (!ok) continue;
+            double sol[3];
+            for (int r2 = nf - 1; r2 >= 0; --r2) {
+                double acc = rhs[r2];
+                for (int k = r2 + 1; k < nf; ++k) acc -= Mf[r2][k] * sol[k];
+                sol[r2] = acc / Mf[r2][r2];
+            }
+            for (int a = 0; a < nf; ++a) {
+                const int m = fr[a];
+                const double val = t[m] + sol[a];
+                const double tol = 1e-12 * (1.0 + fabs((double)hi[m] - (double)lo[m]));
+                if (val < lo[m] - tol || val > hi[m] + tol) ok = false;
+                xc[m] = fmin(fmax(val, (double)lo[m]), (double)hi[m]);
+            }
+            if (!ok) continue;
+        }
+        double obj = 0.0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) obj += 0.5 * (xc[i] - t[i]) * Q[i][j] * (xc[j] - t[j]);
+        if (obj < best) {
+            best = obj;
+            xo[0] = xc[0]; xo[1] = xc[1]; xo[2] = xc[2];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBpTileX * kBpTileY) k_mocca_bp(GeomC C, ExcTable E, const RayRec* rec,
+                                                                 const ViewF* views, StepParams P, SolveD D) {
+    const int ix = blockIdx.x * kBpTileX + threadIdx.x, iy = blockIdx.y * kBpTileY + threadIdx.y;
+    if (ix >= C.grid.n || iy >= C.grid.n) return;
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+    float p00 = 0.f, p01 = 0.f, p02 = 0.f, p11 = 0.f, p12 = 0.f, p22 = 0.f;
+    pixel_rays(C, E, rec, views, ix, iy, [&](int l, float w, const float4& r1) {
+        const float4 r2 = __ldg(&rec[l].r2), r3 = __ldg(&rec[l].r3);
+        v0 = fmaf(w, r1.z, v0);
+        v1 = fmaf(w, r1.w, v1);
+        v2 = fmaf(w, r2.x, v2);
+        p00 = fmaf(w, r2.y, p00);
+        p01 = fmaf(w, r2.z, p01);
+        p02 = fmaf(w, r2.w, p02);
+        p11 = fmaf(w, r3.x, p11);
+        p12 = fmaf(w, r3.y, p12);
+        p22 = fmaf(w, r3.z, p22);
+    });
+    const int k = iy * C.grid.n + ix;
+    const float4 x = D.x[k];
+    const double il = 1.0 / (double)P.lambda;
+    double T[6] = {p00 * il, p01 * il, p02 * il, p11 * il, p12 * il, p22 * il};
+    const double tr = T[0] + T[3] + T[5];
+    if (!(tr > 0.0)) {
+        D.xbar[k] = x;
+        return;
+    }
+    T[0] += 1e-12 * tr;
+    T[3] += 1e-12 * tr;
+    T[5] += 1e-12 * tr;
+    double Ti[6];
+    double t[3] = {(double)x.x, (double)x.y, (double)x.z};
+    if (inv_sym3(T, Ti)) {
+        const double vv[3] = {(double)v0, (double)v1, (double)v2};
+        t[0] -= Ti[0] * vv[0] + Ti[1] * vv[1] + Ti[2] * vv[2];
+        t[1] -= Ti[1] * vv[0] + Ti[3] * vv[1] + Ti[4] * vv[2];
+        t[2] -= Ti[2] * vv[0] + Ti[4] * vv[1] + Ti[5] * vv[2];
+    }
+    if (P.use_box &&
+        (t[0] < P.lo[0] || t[0] > P.hi[0] || t[1] < P.lo[1] || t[1] > P.hi[1] || t[2] < P.lo[2] || t[2] > P.hi[2])) {
+        const double Q[3][3] = {{T[0], T[1], T[2]}, {T[1], T[3], T[4]}, {T[2], T[4], T[5]}};
+        double xo[3];
+        box_prox3(Q, t, P.lo, P.hi, xo);
+        t[0] = xo[0]; t[1] = xo[1]; t[2] = xo[2];
+    }
+    const float4 xn = make_float4((float)t[0], (float)t[1], (float)t[2], 0.f);
+    D.x[k] = xn;
+    D.xbar[k] = make_float4(2.f * xn.x - x.x, 2.f * xn.y - x.y, 2.f * xn.z - x.z, 0.f);
+}
+
+__global__ void k_dtpl_reduce(const double* part, int n, double* out) {
+    __shared__ double red[256 / 32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    const double t = block_sum(s, red);
+    if (threadIdx.x == 0) *out = t;
+}
+
+inline int blocks(int n, int t) { return (n + t - 1) / t; }
+
+}  // namespace
+
+cudaError_t launch_forward4(const GeomC& C, const ExcTable& E, const RayRec* rec, const float4* x, float4* g,
+                            cudaStream_t st) {
+    const int L = C.n_views * C.n_bins;
+    k_forward4<<<blocks(L, kFwdThreads), kFwdThreads, 0, st>>>(C, E, rec, x, g, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backproject4(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
+                                const float4* rf, float4* img, cudaStream_t st) {
+    dim3 grid(blocks(C.grid.n, kBpTileX), blocks(C.grid.n, kBpTileY)), blk(kBpTileX, kBpTileY);
+    k_backproject4<<<grid, blk, 0, st>>>(C, E, rec, views, rf, img);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_counts(const GeomC& C, const ExcTable& E, const RayRec* rec, const SpecD& S, const float4* f,
+                          float4* chat, const float4* c, double* dtpl_part, cudaStream_t st) {
+    const int L = C.n_views * C.n_bins;
+    k_counts<<<blocks(L, kFwdThreads), kFwdThreads, 0, st>>>(C, E, rec, S, f, chat, c, dtpl_part, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mocca_fwd(const GeomC& C, const ExcTable& E, RayRec* rec, const SpecD& S, const StepParams& P,
+                             const SolveD& D, cudaStream_t st) {
+    const int L = C.n_views * C.n_bins;
+    k_mocca_fwd<<<blocks(L, kFwdThreads), kFwdThreads, 0, st>>>(C, E, rec, S, P, D, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mocca_bp(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
+                            const StepParams& P, const SolveD& D, cudaStream_t st) {
+    dim3 grid(blocks(C.grid.n, kBpTileX), blocks(C.grid.n, kBpTileY)), blk(kBpTileX, kBpTileY);
+    k_mocca_bp<<<grid, blk, 0, st>>>(C, E, rec, views, P, D);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dtpl_reduce(const double* part, int n, double* out, cudaStream_t st) {
+    k_dtpl_reduce<<<1, 256, 0, st>>>(part, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace osscir

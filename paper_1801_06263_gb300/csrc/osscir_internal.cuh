@@ -1,0 +1,170 @@
+// Internal device-side definitions shared by the library's kernels.
+//
+// Projector X (Eq. fullModel's X_{l,k}): X_{l,k} is the length of ray l inside
+// pixel k.  Both the ray-driven forward projection and the pixel-driven
+// back-projection evaluate the SAME function x_weight(ray, ix, iy) on the SAME
+// per-ray FP32 record, so the two kernels use bit-identical weights and are
+// exact adjoints up to summation order.  Membership of (l, k) in the footprint
+// is decided in FP32 when the FP32 chord is farther than a rigorous per-ray
+// error bound from zero, and otherwise read from a per-geometry exception
+// table that a setup kernel fills in FP64 (chord > 1e-9 pixel), so the
+// footprint equals the FP64 definition exactly.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace osscir {
+
+constexpr int NW = 4;  // energy windows
+constexpr int NM = 3;  // basis materials
+
+// Pixel grid: n x n pixels of side h, planes at x0 + i h (i = 0..n), x0 = -n h / 2.
+struct GridF {
+    int n;
+    float h, x0;
+};
+
+__device__ __forceinline__ float grid_plane(const GridF& G, int i) {
+    return __fmaf_rn(static_cast<float>(i), G.h, G.x0);
+}
+
+// Per-ray record, 4 x float4 = 64 bytes, one per ray l = v * n_bins + b.
+//   r0 = (bx, by, idx, idy)  foot point of the ray line nearest the origin and
+//                            the reciprocal unit-direction components (inf if 0)
+//   r1 = (ex, ey, b0, b1)    FP32 error bounds on t for x- and y-planes; b = alpha^T y'
+//   r2 = (b2, S00, S01, S02) b and the block step matrix S = sum_w alpha_w alpha_w^T / |alpha_w|
+//   r3 = (S11, S12, S22, -)
+// r0 and r1.xy are written once per geometry; the rest once per MOCCA iteration.
+struct __align__(16) RayRec {
+    float4 r0, r1, r2, r3;
+};
+
+// t(X) for the x-plane X along the unit direction from the foot point (mm).
+__device__ __forceinline__ float t_plane(float X, float b, float inv_d) {
+    return __fmul_rn(__fsub_rn(X, b), inv_d);
+}
+
+// FP32 chord of pixel (ix, iy) on the ray and the error bound that applies to it.
+__device__ __forceinline__ void chord32(const float4& r0, float ex, float ey, const GridF& G, int ix,
+                                        int iy, float& w, float& eb) {
+    const float tx0 = t_plane(grid_plane(G, ix), r0.x, r0.z);
+    const float tx1 = t_plane(grid_plane(G, ix + 1), r0.x, r0.z);
+    const float ty0 = t_plane(grid_plane(G, iy), r0.y, r0.w);
+    const float ty1 = t_plane(grid_plane(G, iy + 1), r0.y, r0.w);
+    const float txl = fminf(tx0, tx1), txh = fmaxf(tx0, tx1);
+    const float tyl = fminf(ty0, ty1), tyh = fmaxf(ty0, ty1);
+    const float lo = fmaxf(txl, tyl), hi = fminf(txh, tyh);
+    w = __fsub_rn(hi, lo);
+    const float elo = txl > tyl ? ex : (tyl > txl ? ey : fmaxf(ex, ey));
+    const float ehi = txh < tyh ? ex : (tyh < txh ? ey : fmaxf(ex, ey));
+    eb = __fadd_rn(elo, ehi);
+}
+
+// Footprint exception table (CSR over rays): entries (pixel k, weight bits).
+struct ExcTable {
+    const int* off;    // [L + 1]
+    const int2* ent;   // [off[L]]
+};
+
+__device__ __forceinline__ float exc_lookup(const ExcTable& E, int l, int k) {
+    const int a = __ldg(E.off + l), b = __ldg(E.off + l + 1);
+    for (int j = a; j < b; ++j) {
+        const int2 e = __ldg(E.ent + j);
+        if (e.x == k) return __int_as_float(e.y);
+    }
+    return 0.0f;
+}
+
+// X_{l,k}: the weight both projectors use.
+__device__ __forceinline__ float x_weight(const float4& r0, float ex, float ey, const GridF& G,
+                                          const ExcTable& E, int l, int ix, int iy) {
+    float w, eb;
+    chord32(r0, ex, ey, G, ix, iy, w, eb);
+    if (w > eb) return w;
+    if (w < -eb) return 0.0f;
+    return exc_lookup(E, l, iy * G.n + ix);   // also reached by NaN (axis-parallel rays)
+}
+
+// float -> int with saturation (huge or infinite coordinates stay in range).
+__device__ __forceinline__ int sat_floor(float v) {
+    return static_cast<int>(floorf(fminf(fmaxf(v, -1.0e9f), 1.0e9f)));
+}
+
+// Candidate enumeration of a ray's pixels: slabs along the dominant axis,
+// within each slab the minor-axis cells the ray can touch (with a margin that
+// exceeds the FP32 error of the crossing points).  Calls visit(ix, iy) for a
+// superset of the footprint; the visitor applies x_weight.
+template <class Visit>
+__device__ __forceinline__ void for_each_candidate(const float4& r0, const GridF& G, float margin,
+                                                   Visit&& visit) {
+    // r0.zw = (1/dx, 1/dy): the ray is row-major (|dy| >= |dx|) iff |1/dy| <= |1/dx|
+    const bool rows = fabsf(r0.w) <= fabsf(r0.z);
+    // major axis coordinate / minor axis coordinate of the ray
+    const float bM = rows ? r0.y : r0.x, bm = rows ? r0.x : r0.y;
+    const float iM = rows ? r0.w : r0.z, im = rows ? r0.z : r0.w;
+    const float slope = iM / im;   // d_minor / d_major, |slope| <= 1 (0 for axis-parallel rays)
+    const float xlo = G.x0, xhi = grid_plane(G, G.n);
+    // major-axis range where the minor coordinate lies inside the image (with margin)
+    int jlo = 0, jhi = G.n - 1;
+    if (slope != 0.0f) {
+        const float ya = bM + (xlo - margin - bm) / slope;
+        const float yb = bM + (xhi + margin - bm) / slope;
+        const float ymin = fminf(ya, yb), ymax = fmaxf(ya, yb);
+        jlo = max(jlo, sat_floor((ymin - G.x0) / G.h) - 1);
+        jhi = min(jhi, sat_floor((ymax - G.x0) / G.h) + 1);
+    } else if (bm < xlo - margin || bm > xhi + margin) {
+        return;
+    }
+    const float inv_h = 1.0f / G.h;
+    for (int j = jlo; j <= jhi; ++j) {
+        const float pa = grid_plane(G, j) - bM, pb = grid_plane(G, j + 1) - bM;
+        const float ma = fmaf(slope, pa, bm), mb = fmaf(slope, pb, bm);
+        const float mn = fminf(ma, mb) - margin, mx = fmaxf(ma, mb) + margin;
+        int ilo = sat_floor((mn - G.x0) * inv_h);
+        int ihi = sat_floor((mx - G.x0) * inv_h);
+        ilo = max(ilo, 0);
+        ihi = min(ihi, G.n - 1);
+        for (int i = ilo; i <= ihi; ++i) {
+            if (rows) visit(i, j);
+            else visit(j, i);
+        }
+    }
+}
+
+// Per-view constants for the pixel-driven back-projection: the detector bin
+// coordinate of a point q is beta(q) = scale * (q . e_u) / (sid - q . e) + mid
+// with e = (cos th, sin th), e_u = (-sin th, cos th).
+struct ViewF {
+    float c, s;   // cos th, sin th
+};
+
+// Library geometry constants shared by all kernels of one context.
+struct GeomC {
+    GridF grid;
+    int n_views, n_bins;
+    float sid, scale, mid;   // scale = sdd / bin_mm, mid = (n_bins - 1) / 2
+    float margin_mm;         // candidate margin for the ray-driven enumeration
+    float margin_bins;       // candidate margin for the pixel-driven enumeration
+};
+
+// Candidate bin range of pixel (ix, iy) in a view: bins whose centre ray can
+// cross the pixel square (FP32 shadow of the four corners, with a margin).
+__device__ __forceinline__ void pixel_bin_range(const GeomC& C, const ViewF& V, int ix, int iy, int& blo,
+                                                int& bhi) {
+    const float X0 = grid_plane(C.grid, ix), X1 = grid_plane(C.grid, ix + 1);
+    const float Y0 = grid_plane(C.grid, iy), Y1 = grid_plane(C.grid, iy + 1);
+    float bmin = 3.0e38f, bmax = -3.0e38f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float X = (q & 1) ? X1 : X0, Y = (q & 2) ? Y1 : Y0;
+        const float num = -V.s * X + V.c * Y;
+        const float den = C.sid - (V.c * X + V.s * Y);
+        const float beta = C.scale * num / den + C.mid;
+        bmin = fminf(bmin, beta);
+        bmax = fmaxf(bmax, beta);
+    }
+    blo = max(0, -sat_floor(-(bmin - C.margin_bins)));
+    bhi = min(C.n_bins - 1, sat_floor(bmax + C.margin_bins));
+}
+
+}  // namespace osscir

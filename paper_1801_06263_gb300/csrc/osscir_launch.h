@@ -1,0 +1,76 @@
+// Host-side declarations of the kernel launchers (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "osscir_internal.cuh"
+
+namespace osscir {
+
+// FP64 ray: foot point (x, y) nearest the origin and unit direction (z, w).
+struct __align__(32) Ray64 {
+    double x, y, z, w;
+};
+
+// FP64 geometry as given at creation (planes at x0 + i h, x0 = -n h / 2).
+struct GeomD {
+    int n;
+    double h, x0;
+    int n_views, n_bins;
+    double arc_deg, start_deg, bin_mm, sid, sdd;
+    double thr;   // footprint threshold: 1e-9 h
+};
+
+// Spectral tables on the device.
+struct SpecD {
+    int n_energies;
+    const float4* s4;   // [nE][n_bins]: (s_{1..4,b,i})
+    const float4* N4;   // [n_bins]
+    const float* mu;    // [3][nE]
+};
+
+// MOCCA per-solve parameters.
+struct StepParams {
+    float lambda;
+    int model;       // 0: eigen-clipped Hessian, 1: W = 0
+    int use_box;
+    float lo[3], hi[3];
+};
+
+// MOCCA per-solve device state.
+struct SolveD {
+    const float4* c;    // [L] measured counts
+    float4* y;          // [L] dual
+    float4* x;          // [P] x_n
+    float4* xbar;       // [P] 2 x_n - x_{n-1}
+    const float* chord; // [L] (X 1)_l
+    double* dtpl_part;  // [fwd blocks]
+};
+
+constexpr int kFwdThreads = 128;
+constexpr int kBpTileX = 16, kBpTileY = 8;
+
+cudaError_t launch_ray_setup(const GeomD& G, double r_img, RayRec* rec, Ray64* r64, ViewF* views,
+                             cudaStream_t st);
+cudaError_t launch_exc_pass(const GeomC& C, const GeomD& G, const RayRec* rec, const Ray64* r64, int* count,
+                            const int* off, int2* ent, cudaStream_t st);
+cudaError_t launch_chord(const GeomC& C, const ExcTable& E, const RayRec* rec, float* chord, cudaStream_t st);
+cudaError_t launch_footprint_rays(const GeomC& C, const ExcTable& E, const RayRec* rec, int l0, int n, int cap,
+                                  int* cnt, int* pix, float* wt, cudaStream_t st);
+cudaError_t launch_footprint_pixels(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
+                                    int k0, int n, int cap, int* cnt, int* ray, float* wt, cudaStream_t st);
+
+cudaError_t launch_forward4(const GeomC& C, const ExcTable& E, const RayRec* rec, const float4* x, float4* g,
+                            cudaStream_t st);
+cudaError_t launch_backproject4(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
+                                const float4* rf, float4* img, cudaStream_t st);
+cudaError_t launch_counts(const GeomC& C, const ExcTable& E, const RayRec* rec, const SpecD& S, const float4* f,
+                          float4* chat, const float4* c, double* dtpl_part, cudaStream_t st);
+cudaError_t launch_mocca_fwd(const GeomC& C, const ExcTable& E, RayRec* rec, const SpecD& S, const StepParams& P,
+                             const SolveD& D, cudaStream_t st);
+cudaError_t launch_mocca_bp(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
+                            const StepParams& P, const SolveD& D, cudaStream_t st);
+cudaError_t launch_dtpl_reduce(const double* part, int n, double* out, cudaStream_t st);
+
+inline int fwd_blocks(int L) { return (L + kFwdThreads - 1) / kFwdThreads; }
+
+}  // namespace osscir

@@ -1,0 +1,83 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it builds for sm_103a,
+loads, exports every entry point include/osscir.h declares, and rejects invalid
+arguments before touching the device."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1801_06263_gb300 import _lib, inputs
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "osscir.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(osscir_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return _lib.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(_lib.EXPORTS)
+
+
+def test_status_strings(lib):
+    assert _lib.load().osscir_status_string(0) == b"ok"
+    assert _lib.load().osscir_status_string(-1) == b"invalid argument"
+
+
+def _args():
+    g = inputs.make_geometry(8, 0.5, 4, 6)
+    sp = inputs.make_spectra(g.n_bins, 1e4)
+    return g, sp
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda g, sp: (g.__class__(**{**g.__dict__, "n": 0}), sp),
+    lambda g, sp: (g.__class__(**{**g.__dict__, "sid_mm": 1.0}), sp),
+    lambda g, sp: (g.__class__(**{**g.__dict__, "sdd_mm": 400.0}), sp),
+    lambda g, sp: (g.__class__(**{**g.__dict__, "bin_mm": float("nan")}), sp),
+    lambda g, sp: (g, inputs.Spectra(sp.energies, sp.s * 1.01, sp.N, sp.mu)),
+    lambda g, sp: (g, inputs.Spectra(sp.energies, sp.s, -sp.N, sp.mu)),
+    lambda g, sp: (g, inputs.Spectra(sp.energies, sp.s, sp.N, -sp.mu)),
+])
+def test_create_rejects_invalid_inputs(lib, mutate):
+    g, sp = mutate(*_args())
+    with pytest.raises(_lib.OsscirError) as e:
+        _lib.osscir_create(g, sp.s, sp.N, sp.mu, 1e-6)
+    assert e.value.status == _lib.OSSCIR_E_INVALID
+
+
+@pytest.mark.parametrize("lam", [0.0, -1.0, float("inf"), float("nan")])
+def test_create_rejects_bad_lambda(lib, lam):
+    g, sp = _args()
+    with pytest.raises(_lib.OsscirError) as e:
+        _lib.osscir_create(g, sp.s, sp.N, sp.mu, lam)
+    assert e.value.status == _lib.OSSCIR_E_INVALID
+
+
+def test_create_rejects_bad_box_and_model(lib):
+    g, sp = _args()
+    with pytest.raises(_lib.OsscirError):
+        _lib.osscir_create(g, sp.s, sp.N, sp.mu, 1e-6, box=((0, 0, 1), (1, 1, 0)))
+    with pytest.raises(_lib.OsscirError):
+        _lib.osscir_create(g, sp.s, sp.N, sp.mu, 1e-6, model=7)
+
+
+def test_null_handle_calls_are_rejected(lib):
+    null = ct.c_void_p(0)
+    assert lib.osscir_mocca_step(null, 1, None) == _lib.OSSCIR_E_INVALID
+    assert lib.osscir_forward(null, None, None, None) == _lib.OSSCIR_E_INVALID
+    out = ct.c_double()
+    assert lib.osscir_dtpl(null, 0, ct.byref(out), None) == _lib.OSSCIR_E_INVALID
+    assert lib.osscir_destroy(null) == _lib.OSSCIR_OK
