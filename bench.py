@@ -1,0 +1,309 @@
+#!/usr/bin/env python
+"""Benchmark: MOCCA iterations/s for 256x256 three-material spectral CT on GB300.
+
+Workload (medium_256): 256 x 256 pixels of 0.5 mm, 512 views over 360 deg x 512
+detector bins (flat detector, source 500 mm / detector 1000 mm), 4 overlapping
+energy windows, 101 energy bins (20-120 keV), PMMA / Al / Gd basis, seeded
+ellipse phantom with 4 Al and 6 Gd inserts, Poisson counts at 1e5 photons per
+ray.  One step is one MOCCA iteration (forward projection + spectral model +
+per-ray curvature and dual step, back-projection + block step-preconditioner +
+primal step, D_TPL reduction) of one solve; a reconstruction is 500 steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+The GPU arm times K iterations with CUDA events (L2 flushed between steps),
+reports per-kernel device time from events captured in the iteration graph,
+the end-to-end rate through the host-buffer C-ABI call, the FP64 oracle on the
+host cores as the CPU baseline, clocks sampled during the timed region, and
+one JSON line on rank 0.  --impl reference times the FP64 oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("MOCCA iters/sec & recon/s at 256² (served vs plain, 1 GB300) at 1e-4 rel L2; p50/p99")
+WORKLOAD = "medium_256"
+WORKLOAD_DESC = ("256x256 (0.5 mm), 512 views x 512 bins, 4 windows, 101 energies, 3 materials "
+                 "(PMMA/Al/Gd), ellipse phantom 4 Al + 6 Gd, Poisson 1e5 photons/ray")
+LAMBDA = 3e-8
+SOLVE_ITERS = 500
+# FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes per launch from an ncu capture of the dominant kernel; valid only for the
+# kernel source it was taken on (see profiles/), otherwise reported as null.
+TRAFFIC = {"k_mocca_fwd": {"bytes_per_launch": 29231360 + 1792, "source_sha": "5056569922572533"},
+           "k_mocca_bp": {"bytes_per_launch": 16076544, "source_sha": "5056569922572533"}}
+
+
+def _source_sha() -> str:
+    p = os.path.join(ROOT, "paper_1801_06263_gb300", "csrc", "mocca.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        busy = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- CPU oracle legs
+
+def _oracle_problem():
+    import numpy as np
+
+    import oracle
+    from paper_1801_06263_gb300 import inputs
+    w = inputs.workload(WORKLOAD)
+    cbar = oracle.counts(w.geom, w.spectra, w.f_true)
+    c = inputs.poisson_counts(cbar, w.noise_seed)
+    return w, np.ascontiguousarray(c)
+
+
+def cpu_oracle_rate(n_iters: int):
+    """FP64 oracle MOCCA iterations/s on the host cores for n_iters iterations."""
+    import oracle
+    w, c = _oracle_problem()
+    t0 = time.perf_counter()
+    oracle.mocca(w.geom, w.spectra, c, n_iters, LAMBDA)
+    dt = time.perf_counter() - t0
+    return n_iters / dt, oracle.max_threads(), dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    w, c = _oracle_problem()
+    st = None
+    for _ in range(min(args.warmup, 1)):
+        st, _ = oracle.mocca(w.geom, w.spectra, c, 1, LAMBDA, st)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, _ = oracle.mocca(w.geom, w.spectra, c, 1, LAMBDA, st)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "lambda": LAMBDA},
+        "cpu_baseline": {"value": v, "unit": "iter/s", "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": f"{args.steps} full MOCCA iterations of {WORKLOAD} (FP64 C oracle)"},
+        "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    from paper_1801_06263_gb300 import Reconstructor, _lib, inputs, osscir_footprint_rays
+
+    w = inputs.workload(WORKLOAD)
+    R = Reconstructor(w.geom, w.spectra, LAMBDA)
+    f4 = torch.zeros((w.geom.n_pixels, 4), dtype=torch.float32, device="cuda")
+    f4[:, :3] = torch.tensor(w.f_true, dtype=torch.float32, device="cuda")
+    chat = R.simulate(f4)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(w.noise_seed + rank)
+    c = torch.poisson(chat, generator=gen).contiguous()
+    R.set_counts(c)
+    # footprint size: number of (ray, pixel) pairs, the unit of the projector work
+    cnt = torch.zeros(w.geom.n_rays, dtype=torch.int32, device="cuda")
+    osscir_footprint_rays(R.handle, 0, w.geom.n_rays, 0, cnt, None, None)
+    nnz = int(cnt.sum().item())
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for i in range(args.warmup):
+        flush.fill_(i & 0xFF)
+        R.step(1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    fwd_ms, bp_ms = [], []
+    _barrier(ws)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.fill_((k + 1) & 0xFF)          # L2 flush between steps, outside the timed events
+            ev[k][0].record(stream)
+            R.step(1)
+            ev[k][1].record(stream)
+            a, b = _lib.osscir_last_kernel_ms(R.handle)   # synchronises the stream
+            fwd_ms.append(a)
+            bp_ms.append(b)
+        torch.cuda.synchronize()
+    _barrier(ws)
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    total_s = _max_over_ranks(ws, sum(step_ms) / 1e3)
+    value = ws * args.steps / total_s
+    d_last = R.dtpl(1)
+
+    # end to end: full reconstructions through the host-buffer C-ABI call
+    e2e_steps = max(1, args.e2e)
+    c_host = c.cpu().pin_memory()
+    maps_host = torch.empty((w.geom.n_pixels, 4), dtype=torch.float32).pin_memory()
+    _lib.osscir_reconstruct(R.handle, c_host, 5, maps_host)          # warm-up
+    _barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        _lib.osscir_reconstruct(R.handle, c_host, SOLVE_ITERS, maps_host)
+    e2e_s = _max_over_ranks(ws, time.perf_counter() - t0)
+    e2e_rate = ws * e2e_steps * SOLVE_ITERS / e2e_s
+    finite = bool(torch.isfinite(maps_host).all().item())
+
+    if rank != 0:
+        return 0
+    fwd_mean = statistics.mean(fwd_ms)
+    bp_mean = statistics.mean(bp_ms)
+    L, nE = w.geom.n_rays, w.spectra.n_energies
+    kern = {
+        # k_mocca_bp: 9 FMA per footprint pair (K^T y' and the 6-channel block SPC)
+        "k_mocca_bp": {"ms": bp_mean, "flop": 18.0 * nnz},
+        # k_mocca_fwd: 3 FMA per footprint pair + 43 FMA per (ray, energy) of the spectral sums
+        "k_mocca_fwd": {"ms": fwd_mean, "flop": 6.0 * nnz + 86.0 * L * nE},
+    }
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    achieved = kern[dom]["flop"] / (kern[dom]["ms"] * 1e-3) / 1e12
+    tr = TRAFFIC.get(dom)
+    traffic = tr["bytes_per_launch"] if tr and tr.get("source_sha") == _source_sha() else None
+    cpu = None
+    if ws == 1 and args.cpu_iters > 0:
+        rate, cores, dt = cpu_oracle_rate(args.cpu_iters)
+        cpu = {"value": rate, "unit": "iter/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_iters} full MOCCA iterations of {WORKLOAD} (FP64 C oracle, {dt:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "solve_iterations": SOLVE_ITERS,
+                   "lambda": LAMBDA, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "independent solves per GPU" if ws > 1 else "single solve"},
+        "recon_per_s": value / SOLVE_ITERS,
+        "kernel_ms": {"k_mocca_fwd": fwd_mean, "k_mocca_bp": bp_mean},
+        "footprint_pairs": nnz,
+        "intersections_per_s": 2.0 * nnz / (total_s / args.steps) * ws,
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and max clock)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_rate, "unit": "iter/s", "h2d_bytes_per_step": int(c_host.numel() * 4),
+                "d2h_bytes_per_step": int(maps_host.numel() * 4),
+                "step": f"one {SOLVE_ITERS}-iteration reconstruction via osscir_reconstruct (pinned host buffers)",
+                "recon_per_s": e2e_rate / SOLVE_ITERS},
+        "clocks": clk.summary(),
+        "gpu_launches": 3 * args.steps,
+        "dtpl_last": d_last,
+        "maps_finite": finite,
+    }
+    print(json.dumps(line), flush=True)
+    R.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--e2e", type=int, default=3, help="full reconstructions for the end-to-end rate")
+    ap.add_argument("--cpu-iters", type=int, default=3, help="oracle iterations for the CPU baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

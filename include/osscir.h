@@ -132,6 +132,20 @@ osscir_status osscir_set_counts(osscir_t h, const float *c, void *stream);
  * Sigma and T).  Library-owned state; asynchronous on the stream. */
 osscir_status osscir_mocca_step(osscir_t h, int n_iters, void *stream);
 
+/* End-to-end reconstruction with host buffers: copies the counts c (host
+ * float[L][4], c >= 0; pinned memory makes the copy asynchronous DMA) to the
+ * device, resets the state as osscir_set_counts does, runs n_iters MOCCA
+ * iterations and copies the maps x_n to maps_out (host float[P][4]).
+ * Synchronises the stream before returning. */
+osscir_status osscir_reconstruct(osscir_t h, const float *c_host, int n_iters, float *maps_out_host,
+                                 void *stream);
+
+/* Device time of the last MOCCA iteration's two main kernels, measured with
+ * CUDA events recorded inside the iteration's graph: fwd_ms for the
+ * ray-driven forward/spectral/dual kernel, bp_ms for the pixel-driven
+ * back-projection/primal kernel (host floats).  Synchronises the stream. */
+osscir_status osscir_last_kernel_ms(osscir_t h, float *fwd_ms, float *bp_ms, void *stream);
+
 /* Copy the current material maps x_n to x_out: device float[P][4]. */
 osscir_status osscir_get_maps(osscir_t h, float *x_out, void *stream);
 
@@ -152,7 +166,8 @@ osscir_status osscir_dtpl(osscir_t h, int which, double *out, void *stream);
 /* Footprint dumps for verification: for rays [l0, l0+n) (or pixels [k0, k0+n))
  * the pixels (rays) with nonzero X_{l,k} as the forward (back-)projection uses
  * them, and their weights.  cnt: device int[n]; idx: device int[n][cap];
- * wt: device float[n][cap]; entries beyond cap are counted but not stored. */
+ * wt: device float[n][cap]; entries beyond cap are counted but not stored
+ * (with cap = 0 only the counts are written and idx, wt may be NULL). */
 osscir_status osscir_footprint_rays(osscir_t h, int l0, int n, int cap, int *cnt, int *idx, float *wt,
                                     void *stream);
 osscir_status osscir_footprint_pixels(osscir_t h, int k0, int n, int cap, int *cnt, int *idx, float *wt,

@@ -28,7 +28,7 @@ EXPORTS = (
     "osscir_status_string", "osscir_create", "osscir_destroy", "osscir_info", "osscir_forward",
     "osscir_backproject", "osscir_simulate", "osscir_set_counts", "osscir_mocca_step", "osscir_get_maps",
     "osscir_get_state", "osscir_set_state", "osscir_dtpl", "osscir_footprint_rays",
-    "osscir_footprint_pixels",
+    "osscir_footprint_pixels", "osscir_reconstruct", "osscir_last_kernel_ms",
 )
 
 
@@ -88,6 +88,8 @@ def load(build_if_missing: bool = True):
         "osscir_dtpl": ([vp, ct.c_int, dp, vp], ct.c_int),
         "osscir_footprint_rays": ([vp, ct.c_int, ct.c_int, ct.c_int, vp, vp, vp, vp], ct.c_int),
         "osscir_footprint_pixels": ([vp, ct.c_int, ct.c_int, ct.c_int, vp, vp, vp, vp], ct.c_int),
+        "osscir_reconstruct": ([vp, vp, ct.c_int, vp, vp], ct.c_int),
+        "osscir_last_kernel_ms": ([vp, ct.POINTER(ct.c_float), ct.POINTER(ct.c_float), vp], ct.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -211,3 +213,18 @@ def osscir_footprint_rays(h, l0, n, cap, cnt, idx, wt, stream=None):
 def osscir_footprint_pixels(h, k0, n, cap, cnt, idx, wt, stream=None):
     _check("osscir_footprint_pixels", load().osscir_footprint_pixels(
         ct.c_void_p(h), int(k0), int(n), int(cap), _ptr(cnt), _ptr(idx), _ptr(wt), _stream(stream)))
+
+
+def osscir_reconstruct(h, c_host, n_iters, maps_out_host, stream=None):
+    """c_host [L, 4] and maps_out_host [P, 4]: contiguous float32 CPU tensors (pinned for DMA)."""
+    if c_host.is_cuda or maps_out_host.is_cuda:
+        raise ValueError("osscir_reconstruct takes host buffers")
+    _check("osscir_reconstruct", load().osscir_reconstruct(ct.c_void_p(h), _ptr(c_host), int(n_iters),
+                                                           _ptr(maps_out_host), _stream(stream)))
+
+
+def osscir_last_kernel_ms(h, stream=None):
+    a, b = ct.c_float(), ct.c_float()
+    _check("osscir_last_kernel_ms", load().osscir_last_kernel_ms(ct.c_void_p(h), ct.byref(a), ct.byref(b),
+                                                                 _stream(stream)))
+    return a.value, b.value

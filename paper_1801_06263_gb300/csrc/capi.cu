@@ -42,6 +42,7 @@ struct osscir_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // recorded around the kernels inside the graph
 
     ExcTable exc() const { return ExcTable{exc_off, exc_ent}; }
     SpecD spec() const { return SpecD{nE, s4, N4, mu}; }
@@ -75,6 +76,8 @@ void free_ctx(osscir_ctx* h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
     void* ptrs[] = {h->rec, h->r64, h->views, h->chord, h->exc_off, h->exc_ent, h->s4, h->N4, h->mu,
                     h->c, h->y, h->x, h->xbar, h->dtpl_part, h->dtpl_out};
     for (void* p : ptrs)
@@ -173,6 +176,7 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     CK(dalloc(&h->dtpl_part, h->n_part));
     CK(dalloc(&h->dtpl_out, 2));
     CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : h->ev) CK(cudaEventCreate(&e));
     cudaStream_t st = h->cap_stream;
 
     // spectral tables: s reordered to [nE][n_bins] float4 so consecutive rays read consecutive entries
@@ -216,9 +220,15 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
 
 // One MOCCA iteration as launches on a stream (captured into a graph once).
 cudaError_t enqueue_iteration(osscir_ctx* h, cudaStream_t st) {
-    cudaError_t e = launch_mocca_fwd(h->gc, h->exc(), h->rec, h->spec(), h->params, h->solve(), st);
+    cudaError_t e = cudaEventRecordWithFlags(h->ev[0], st, cudaEventRecordExternal);
+    if (e != cudaSuccess) return e;
+    e = launch_mocca_fwd(h->gc, h->exc(), h->rec, h->spec(), h->params, h->solve(), st);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecordWithFlags(h->ev[1], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
     e = launch_mocca_bp(h->gc, h->exc(), h->rec, h->views, h->params, h->solve(), st);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecordWithFlags(h->ev[2], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
     return launch_dtpl_reduce(h->dtpl_part, h->n_part, h->dtpl_out + 1, st);
 }
@@ -329,6 +339,31 @@ osscir_status osscir_mocca_step(osscir_t h, int n_iters, void* stream) {
     return OSSCIR_OK;
 }
 
+osscir_status osscir_reconstruct(osscir_t h, const float* c_host, int n_iters, float* maps_out_host,
+                                 void* stream) {
+    if (!h || !c_host || !maps_out_host || n_iters < 0) return OSSCIR_E_INVALID;
+    cudaStream_t st = as_stream(stream);
+    CK(cudaMemcpyAsync(h->c, c_host, sizeof(float4) * h->L, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(h->y, 0, sizeof(float4) * h->L, st));
+    CK(cudaMemsetAsync(h->x, 0, sizeof(float4) * h->P, st));
+    CK(cudaMemsetAsync(h->xbar, 0, sizeof(float4) * h->P, st));
+    h->iter = 0;
+    const osscir_status s = osscir_mocca_step(h, n_iters, stream);
+    if (s != OSSCIR_OK) return s;
+    CK(cudaMemcpyAsync(maps_out_host, h->x, sizeof(float4) * h->P, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return OSSCIR_OK;
+}
+
+osscir_status osscir_last_kernel_ms(osscir_t h, float* fwd_ms, float* bp_ms, void* stream) {
+    if (!h || !fwd_ms || !bp_ms) return OSSCIR_E_INVALID;
+    if (!h->gexec) return OSSCIR_E_INVALID;
+    CK(cudaStreamSynchronize(as_stream(stream)));
+    CK(cudaEventElapsedTime(fwd_ms, h->ev[0], h->ev[1]));
+    CK(cudaEventElapsedTime(bp_ms, h->ev[1], h->ev[2]));
+    return OSSCIR_OK;
+}
+
 osscir_status osscir_get_maps(osscir_t h, float* x_out, void* stream) {
     if (!h || !x_out) return OSSCIR_E_INVALID;
     CK(cudaMemcpyAsync(x_out, h->x, sizeof(float4) * h->P, cudaMemcpyDeviceToDevice, as_stream(stream)));
@@ -371,7 +406,8 @@ osscir_status osscir_dtpl(osscir_t h, int which, double* out, void* stream) {
 
 osscir_status osscir_footprint_rays(osscir_t h, int l0, int n, int cap, int* cnt, int* idx, float* wt,
                                     void* stream) {
-    if (!h || !cnt || !idx || !wt || l0 < 0 || n < 0 || cap < 0 || l0 + n > h->L) return OSSCIR_E_INVALID;
+    if (!h || !cnt || (cap > 0 && (!idx || !wt)) || l0 < 0 || n < 0 || cap < 0 || l0 + n > h->L)
+        return OSSCIR_E_INVALID;
     if (n == 0) return OSSCIR_OK;
     CK(launch_footprint_rays(h->gc, h->exc(), h->rec, l0, n, cap, cnt, idx, wt, as_stream(stream)));
     return OSSCIR_OK;
@@ -379,7 +415,8 @@ osscir_status osscir_footprint_rays(osscir_t h, int l0, int n, int cap, int* cnt
 
 osscir_status osscir_footprint_pixels(osscir_t h, int k0, int n, int cap, int* cnt, int* idx, float* wt,
                                       void* stream) {
-    if (!h || !cnt || !idx || !wt || k0 < 0 || n < 0 || cap < 0 || k0 + n > h->P) return OSSCIR_E_INVALID;
+    if (!h || !cnt || (cap > 0 && (!idx || !wt)) || k0 < 0 || n < 0 || cap < 0 || k0 + n > h->P)
+        return OSSCIR_E_INVALID;
     if (n == 0) return OSSCIR_OK;
     CK(launch_footprint_pixels(h->gc, h->exc(), h->rec, h->views, k0, n, cap, cnt, idx, wt, as_stream(stream)));
     return OSSCIR_OK;

@@ -1,0 +1,181 @@
+"""GPU parity of the MOCCA iteration (Sec. 2, m-block-diagonal SPC) against the FP64 oracle.
+
+Tolerance: the GPU projects and sums the spectral model in FP32 and does the
+3x3 / 4x4 algebra in FP64; after many iterations the material maps must agree
+with the FP64 oracle within 1e-4 relative L2 per material (the Gd map, whose
+values are 100x smaller, is reported separately and held to the same bar).
+Inputs are the library's FP32 copies of the spectra and counts, given to both.
+"""
+import numpy as np
+import pytest
+
+from paper_1801_06263_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-4
+
+
+def _sp32(sp):
+    return inputs.Spectra(sp.energies, sp.s.astype(np.float32).astype(np.float64),
+                          sp.N.astype(np.float32).astype(np.float64),
+                          sp.mu.astype(np.float32).astype(np.float64))
+
+
+def _rel(a, b):
+    return [float(np.linalg.norm(a[:, m] - b[:, m]) / np.linalg.norm(b[:, m])) for m in range(3)]
+
+
+@pytest.fixture(scope="module")
+def small(orc):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = inputs.workload("small_64")
+    s32 = _sp32(w.spectra)
+    c = inputs.poisson_counts(orc.counts(w.geom, s32, w.f_true), w.noise_seed).astype(np.float32)
+    return w, s32, c
+
+
+def _recon(w, lam, **kw):
+    from paper_1801_06263_gb300 import Reconstructor
+    return Reconstructor(w.geom, w.spectra, lam, **kw)
+
+
+def test_one_iteration_from_random_state(orc):
+    geom = inputs.make_geometry(20, 0.6, 24, 30)
+    sp = inputs.make_spectra(geom.n_bins, 5e4)
+    s32 = _sp32(sp)
+    f = inputs.disk_phantom(geom, radius_mm=5.0, insert_mm=1.0)
+    c = inputs.poisson_counts(orc.counts(geom, s32, f), 3).astype(np.float32)
+    rng = np.random.default_rng(4)
+    x = (f + rng.normal(scale=0.05, size=f.shape) * np.array([1.0, 0.3, 0.003])).astype(np.float32)
+    xbar = (x + rng.normal(scale=0.02, size=f.shape) * np.array([1.0, 0.3, 0.003])).astype(np.float32)
+    y = rng.normal(scale=300.0, size=(geom.n_rays, 4)).astype(np.float32)
+    lam = 3e-7
+    from paper_1801_06263_gb300 import Reconstructor
+    R = Reconstructor(geom, sp, lam)
+    pad = lambda a: torch.tensor(np.concatenate([a, np.zeros((a.shape[0], 1), np.float32)], 1), device="cuda")
+    R.set_counts(torch.tensor(c, device="cuda"))
+    R.set_state(pad(x), pad(xbar), torch.tensor(y, device="cuda"), 0)
+    R.step(1)
+    gx, gxb, gy, it = R.get_state()
+    torch.cuda.synchronize()
+    st = orc.State(geom)
+    st.x[:], st.xbar[:], st.y[:] = x, xbar, y
+    st, hist = orc.mocca(geom, s32, c.astype(np.float64), 1, lam, st)
+    gy = gy.cpu().double().numpy()
+    np.testing.assert_allclose(gy, st.y, rtol=0, atol=2e-5 * np.abs(st.y).max())
+    gx = gx.cpu().double().numpy()[:, :3]
+    for m in range(3):
+        np.testing.assert_allclose(gx[:, m], st.x[:, m], rtol=0, atol=2e-5 * np.abs(st.x[:, m]).max())
+    assert abs(R.dtpl(1) - hist[0]) <= 1e-5 * hist[0]
+    assert it == 1
+    R.close()
+
+
+@pytest.mark.parametrize("model", ["hessian", "gradient"])
+def test_small_64_iterates_match_oracle(orc, small, model):
+    w, s32, c = small
+    # the zero-curvature variant takes larger dual steps and needs a smaller step ratio
+    lam, n_it = (1e-7, 200) if model == "hessian" else (3e-8, 60)
+    R = _recon(w, lam, model=0 if model == "hessian" else 1)
+    R.set_counts(torch.tensor(c, device="cuda"))
+    R.step(n_it)
+    x = R.maps().cpu().double().numpy()[:, :3]
+    d_gpu = R.dtpl(1)
+    R.close()
+    st, hist = orc.mocca(w.geom, s32, c.astype(np.float64), n_it, lam, model=model)
+    errs = _rel(x, st.x)
+    print(f"{model}: rel L2 after {n_it} iterations PMMA {errs[0]:.2e} Al {errs[1]:.2e} Gd {errs[2]:.2e}")
+    assert max(errs) < REL_L2, errs
+    assert abs(d_gpu - hist[-1]) <= 1e-5 * hist[-1]
+
+
+def test_box_constrained_iterates(orc, small):
+    w, s32, c = small
+    lo, hi = (0.0, 0.0, 0.0), (1.05, 1.05, 0.012)
+    lam, n_it = 1e-7, 60
+    R = _recon(w, lam, box=(lo, hi))
+    R.set_counts(torch.tensor(c, device="cuda"))
+    R.step(n_it)
+    x = R.maps().cpu().double().numpy()[:, :3]
+    R.close()
+    assert (x >= np.array(lo, np.float32)).all() and (x <= np.array(hi, np.float32)).all()
+    st, _ = orc.mocca(w.geom, s32, c.astype(np.float64), n_it, lam, box=(lo, hi))
+    assert max(_rel(x, st.x)) < REL_L2
+
+
+def test_dtpl_at_current_maps(orc, small):
+    w, s32, c = small
+    R = _recon(w, 1e-7)
+    R.set_counts(torch.tensor(c, device="cuda"))
+    R.step(15)
+    x = R.maps().cpu().double().numpy()[:, :3]
+    d = R.dtpl(0)
+    R.close()
+    ref = orc.objective(w.geom, s32, c.astype(np.float64), x.astype(np.float32).astype(np.float64),
+                        with_grad=False)
+    assert abs(d - ref) <= 1e-5 * ref
+
+
+def test_checkpoint_resume_is_bit_identical(small):
+    w, _, c = small
+    ct_ = torch.tensor(c, device="cuda")
+    A = _recon(w, 1e-7)
+    A.set_counts(ct_)
+    A.step(30)
+    xa = A.maps().cpu().numpy()
+    B = _recon(w, 1e-7)
+    B.set_counts(ct_)
+    B.step(15)
+    x, xbar, y, it = B.get_state()
+    B.close()
+    C = _recon(w, 1e-7)
+    C.set_counts(ct_)
+    C.set_state(x, xbar, y, it)
+    C.step(15)
+    xc = C.maps().cpu().numpy()
+    assert np.array_equal(xa, xc)
+    # and two runs are deterministic (no atomics anywhere)
+    A.set_counts(ct_)
+    A.step(30)
+    assert np.array_equal(A.maps().cpu().numpy(), xa)
+    A.close()
+    C.close()
+
+
+def test_medium_256_full_size(orc):
+    """The 256 x 256, 512-view workload in the benchmark's launch configuration:
+    three iterations against the oracle over all pixels, plus footprints of a
+    sample of rays."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = inputs.workload("medium_256")
+    s32 = _sp32(w.spectra)
+    c = inputs.poisson_counts(orc.counts(w.geom, s32, w.f_true), w.noise_seed).astype(np.float32)
+    lam, n_it = 3e-8, 3
+    R = _recon(w, lam)
+    R.set_counts(torch.tensor(c, device="cuda"))
+    R.step(n_it)
+    x = R.maps().cpu().double().numpy()[:, :3]
+    d_gpu = R.dtpl(1)
+    # sampled footprints
+    rng = np.random.default_rng(0)
+    rays = rng.choice(w.geom.n_rays, size=400, replace=False)
+    from paper_1801_06263_gb300 import osscir_footprint_rays
+    cap = 2 * w.geom.n + 4
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    idx = torch.zeros((1, cap), dtype=torch.int32, device="cuda")
+    wt = torch.zeros((1, cap), dtype=torch.float32, device="cuda")
+    for l in rays:
+        osscir_footprint_rays(R.handle, int(l), 1, cap, cnt, idx, wt)
+        n = int(cnt.item())
+        pix, _ = orc.siddon(w.geom, int(l) // w.geom.n_bins, int(l) % w.geom.n_bins)
+        assert np.array_equal(np.sort(idx[0, :n].cpu().numpy()), np.sort(pix))
+    R.close()
+    st, hist = orc.mocca(w.geom, s32, c.astype(np.float64), n_it, lam)
+    errs = _rel(x, st.x)
+    print(f"medium_256 after {n_it}: PMMA {errs[0]:.2e} Al {errs[1]:.2e} Gd {errs[2]:.2e}")
+    assert max(errs) < REL_L2
+    assert abs(d_gpu - hist[-1]) <= 1e-5 * hist[-1]
