@@ -173,6 +173,25 @@ osscir_status osscir_footprint_rays(osscir_t h, int l0, int n, int cap, int *cnt
 osscir_status osscir_footprint_pixels(osscir_t h, int k0, int n, int cap, int *cnt, int *idx, float *wt,
                                       void *stream);
 
+/* D_TPL (Eq. DTPL form) of expected counts chat and measured counts c, computed
+ * without allocating any memory and without a context.  The paper has no
+ * counterpart: this serves callers that must not call cudaMalloc after
+ * start-up, for example a server whose memory arena claims the device at
+ * launch, or a latency-bound loop that cannot accept the synchronisation an
+ * allocation may cause; osscir_dtpl needs a context, and creating one allocates.
+ *   chat, c: device float[n_rays][4];  out: device double (written on the stream).
+ *   n_rays: 1 .. 4,194,304 (larger values return OSSCIR_E_INVALID).
+ * Scratch: a fixed 128 KiB array of per-block partial sums inside the library's
+ * device memory, held by every GPU that loads the library until the process
+ * exits.  The first call on a device looks up that array's device address (with
+ * the device current); make that first call before any stream capture.  Every
+ * call overwrites the partials it reads, so nothing carries over between calls,
+ * but all calls share the one array: calls that overlap on the GPU (different
+ * streams, or different host threads on the same device) race and give wrong
+ * results; serialise them on one stream. */
+osscir_status osscir_dtpl_counts_static(const float *chat, const float *c, int n_rays, double *out,
+                                        void *stream);
+
 #ifdef __cplusplus
 }
 #endif

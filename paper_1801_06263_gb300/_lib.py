@@ -28,7 +28,7 @@ EXPORTS = (
     "osscir_status_string", "osscir_create", "osscir_destroy", "osscir_info", "osscir_forward",
     "osscir_backproject", "osscir_simulate", "osscir_set_counts", "osscir_mocca_step", "osscir_get_maps",
     "osscir_get_state", "osscir_set_state", "osscir_dtpl", "osscir_footprint_rays",
-    "osscir_footprint_pixels", "osscir_reconstruct", "osscir_last_kernel_ms",
+    "osscir_footprint_pixels", "osscir_reconstruct", "osscir_last_kernel_ms", "osscir_dtpl_counts_static",
 )
 
 
@@ -90,6 +90,7 @@ def load(build_if_missing: bool = True):
         "osscir_footprint_pixels": ([vp, ct.c_int, ct.c_int, ct.c_int, vp, vp, vp, vp], ct.c_int),
         "osscir_reconstruct": ([vp, vp, ct.c_int, vp, vp], ct.c_int),
         "osscir_last_kernel_ms": ([vp, ct.POINTER(ct.c_float), ct.POINTER(ct.c_float), vp], ct.c_int),
+        "osscir_dtpl_counts_static": ([vp, vp, ct.c_int, vp, vp], ct.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -228,3 +229,10 @@ def osscir_last_kernel_ms(h, stream=None):
     _check("osscir_last_kernel_ms", load().osscir_last_kernel_ms(ct.c_void_p(h), ct.byref(a), ct.byref(b),
                                                                  _stream(stream)))
     return a.value, b.value
+
+
+def osscir_dtpl_counts_static(chat, c, out, stream=None):
+    """D_TPL of expected counts chat and measured counts c (device float32 [L, 4])
+    into out (device float64 [1]) without allocating memory; see include/osscir.h."""
+    _check("osscir_dtpl_counts_static", load().osscir_dtpl_counts_static(
+        _ptr(chat), _ptr(c), int(chat.shape[0]), _ptr(out), _stream(stream)))
