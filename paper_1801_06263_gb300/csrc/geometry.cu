@@ -93,9 +93,7 @@ __global__ void k_exc_pass(GeomC C, GeomD G, const RayRec* rec, const Ray64* r64
     const Ray64 R = r64[l];
     int cnt = 0;
     const int base = count ? 0 : off[l];
-    for_each_candidate(r0, C.grid, C.margin_mm, [&](int ix, int iy) {
-        float w, eb;
-        chord32(r0, ex, ey, C.grid, ix, iy, w, eb);
+    ray_chords(r0, ex, ey, C.grid, C.margin_mm, [&](int ix, int iy, float w, float eb) {
         if (w > eb || w < -eb) return;
         const double c64 = chord64(R, G, ix, iy);
         if (c64 > G.thr) {
@@ -113,8 +111,7 @@ __global__ void k_chord(GeomC C, ExcTable E, const RayRec* rec, float* chord, in
     const float4 r0 = rec[l].r0;
     const float ex = rec[l].r1.x, ey = rec[l].r1.y;
     float acc = 0.f;
-    for_each_candidate(r0, C.grid, C.margin_mm,
-                       [&](int ix, int iy) { acc += x_weight(r0, ex, ey, C.grid, E, l, ix, iy); });
+    ray_weights(r0, ex, ey, C.grid, C.margin_mm, E, l, [&](int, float w) { acc += w; });
     chord[l] = acc;
 }
 
@@ -127,15 +124,12 @@ __global__ void k_footprint_rays(GeomC C, ExcTable E, const RayRec* rec, int l0,
     const float4 r0 = rec[l].r0;
     const float ex = rec[l].r1.x, ey = rec[l].r1.y;
     int c = 0;
-    for_each_candidate(r0, C.grid, C.margin_mm, [&](int ix, int iy) {
-        const float w = x_weight(r0, ex, ey, C.grid, E, l, ix, iy);
-        if (w != 0.f) {
-            if (c < cap) {
-                pix[(size_t)j * cap + c] = iy * C.grid.n + ix;
-                wt[(size_t)j * cap + c] = w;
-            }
-            ++c;
+    ray_weights(r0, ex, ey, C.grid, C.margin_mm, E, l, [&](int k, float w) {
+        if (c < cap) {
+            pix[(size_t)j * cap + c] = k;
+            wt[(size_t)j * cap + c] = w;
         }
+        ++c;
     });
     cnt[j] = c;
 }

@@ -52,6 +52,22 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return s;
 }
 
+__device__ __forceinline__ void warp_partial(double v, double* part) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0)
+        part[(blockIdx.y * gridDim.x + blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)] = v;
+}
+
+// Ray of this thread in the ray-driven kernels: a block covers 32 consecutive
+// detector bins (one per lane) of 4 consecutive views (one per warp), so the
+// block's slice of the energy-major spectral table is shared by its warps.
+__device__ __forceinline__ int ray_of_thread(const GeomC& C) {
+    const int b = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int v = blockIdx.y * (kFwdThreads / 32) + (threadIdx.x >> 5);
+    return (b < C.n_bins && v < C.n_views) ? v * C.n_bins + b : -1;
+}
+
 __device__ __forceinline__ void load_mu_smem(const SpecD& S, float* sm) {
     const int nE = S.n_energies;
     for (int i = threadIdx.x; i < nE; i += blockDim.x) {
@@ -80,10 +96,7 @@ __device__ __forceinline__ void sexp3(float x, float& e0, float& e1, float& e2) 
 template <class Visit>
 __device__ __forceinline__ void ray_pixels(const GeomC& C, const ExcTable& E, const float4& r0, float ex, float ey,
                                            int l, Visit&& visit) {
-    for_each_candidate(r0, C.grid, C.margin_mm, [&](int ix, int iy) {
-        const float w = x_weight(r0, ex, ey, C.grid, E, l, ix, iy);
-        if (w != 0.0f) visit(iy * C.grid.n + ix, w);
-    });
+    ray_weights(r0, ex, ey, C.grid, C.margin_mm, E, l, visit);
 }
 
 template <class Visit>
@@ -104,9 +117,10 @@ __device__ __forceinline__ void pixel_rays(const GeomC& C, const ExcTable& E, co
 
 // ------------------------------------------------------------------ plain projectors
 
-__global__ void k_forward4(GeomC C, ExcTable E, const RayRec* rec, const float4* x, float4* g, int L) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= L) return;
+__global__ void __launch_bounds__(kFwdThreads) k_forward4(GeomC C, ExcTable E, const RayRec* rec, const float4* x,
+                                                          float4* g) {
+    const int l = ray_of_thread(C);
+    if (l < 0) return;
     const float4 r0 = rec[l].r0, r1 = rec[l].r1;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) {
@@ -137,14 +151,13 @@ __global__ void k_backproject4(GeomC C, ExcTable E, const RayRec* rec, const Vie
 // c^(f) (Eq. finalModel) for every ray; with c != nullptr also the D_TPL block partials.
 __global__ void __launch_bounds__(kFwdThreads) k_counts(GeomC C, ExcTable E, const RayRec* rec, SpecD S,
                                                         const float4* f, float4* chat, const float4* c,
-                                                        double* part, int L) {
+                                                        double* part) {
     __shared__ float sm[kSmemStride * kMaxEnergies];
-    __shared__ double red[kFwdThreads / 32];
     load_mu_smem(S, sm);
     __syncthreads();
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = ray_of_thread(C);
     double dsum = 0.0;
-    if (l < L) {
+    if (l >= 0) {
         const float4 r0 = rec[l].r0, r1 = rec[l].r1;
         float g0 = 0.f, g1 = 0.f, g2 = 0.f;
         ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) {
@@ -176,28 +189,44 @@ __global__ void __launch_bounds__(kFwdThreads) k_counts(GeomC C, ExcTable E, con
                    (double)dtpl_term(ch.w, cc.w);
         }
     }
-    if (part) {
-        const double s = block_sum(dsum, red);
-        if (threadIdx.x == 0) part[blockIdx.x] = s;
-    }
+    if (part) warp_partial(dsum, part);
 }
 
 // ------------------------------------------------------------------ FP64 3x3 / 4x4 algebra
 
 // Symmetric 3x3 stored as (00, 01, 02, 11, 12, 22).
-// Negative-curvature removal H+ = V max(Lambda, 0) V^T.  A positive-definite H
-// (Sylvester's criterion) is returned unchanged; otherwise cyclic Jacobi.
-__device__ void clip_psd3(double h[6]) {
-    const double m2 = h[0] * h[3] - h[1] * h[1];
-    const double det = h[0] * (h[3] * h[5] - h[4] * h[4]) - h[1] * (h[1] * h[5] - h[4] * h[2]) +
-                       h[2] * (h[1] * h[4] - h[3] * h[2]);
-    if (h[0] > 0.0 && m2 > 0.0 && det > 0.0) return;
+
+// Unit eigenvector of H for the simple eigenvalue lam: the largest cross
+// product of two rows of H - lam I.  Returns false if all are (near) zero.
+__device__ __forceinline__ bool eigvec3(const double h[6], double lam, double v[3]) {
+    const double a00 = h[0] - lam, a11 = h[3] - lam, a22 = h[5] - lam;
+    // rows r0 = (a00, h1, h2), r1 = (h1, a11, h4), r2 = (h2, h4, a22)
+    const double c0x = h[1] * h[4] - h[2] * a11, c0y = h[2] * h[1] - a00 * h[4], c0z = a00 * a11 - h[1] * h[1];
+    const double c1x = h[1] * a22 - h[2] * h[4], c1y = h[2] * h[2] - a00 * a22, c1z = a00 * h[4] - h[1] * h[2];
+    const double c2x = a11 * a22 - h[4] * h[4], c2y = h[4] * h[2] - h[1] * a22, c2z = h[1] * h[4] - a11 * h[2];
+    const double n0 = c0x * c0x + c0y * c0y + c0z * c0z;
+    const double n1 = c1x * c1x + c1y * c1y + c1z * c1z;
+    const double n2 = c2x * c2x + c2y * c2y + c2z * c2z;
+    double bx = c0x, by = c0y, bz = c0z, best = n0;
+    if (n1 > best) { bx = c1x; by = c1y; bz = c1z; best = n1; }
+    if (n2 > best) { bx = c2x; by = c2y; bz = c2z; best = n2; }
+    const double sc = fabs(h[0]) + fabs(h[3]) + fabs(h[5]) + fabs(h[1]) + fabs(h[2]) + fabs(h[4]) + fabs(lam);
+    if (!(best > 1e-60 * sc * sc * sc * sc)) return false;
+    const double in = rsqrt(best);
+    v[0] = bx * in;
+    v[1] = by * in;
+    v[2] = bz * in;
+    return true;
+}
+
+// Cyclic Jacobi, used only when the closed form meets a (near) repeated root.
+__device__ void clip_psd3_jacobi(double h[6]) {
     double a[3][3] = {{h[0], h[1], h[2]}, {h[1], h[3], h[4]}, {h[2], h[4], h[5]}};
     double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-    for (int sweep = 0; sweep < 12; ++sweep) {
+    for (int sweep = 0; sweep < 10; ++sweep) {
         const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
         const double dia = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
-        if (off <= 1e-34 * dia || off == 0.0) break;
+        if (!(off > 1e-30 * dia)) break;
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
             const int p = t == 2 ? 1 : 0, q = t == 0 ? 1 : 2, r = 3 - p - q;
@@ -229,6 +258,58 @@ __device__ void clip_psd3(double h[6]) {
     }
 }
 
+// Negative-curvature removal H+ = V max(Lambda, 0) V^T.  A positive-definite H
+// (Sylvester's criterion) is returned unchanged.  Otherwise the eigenvalues
+// come from the closed form of Smith (1961) for symmetric 3x3 matrices
+// (trace, deviatoric part, arccos of half the normalised determinant) and the
+// eigenvectors of the eigenvalues to remove (or to keep) from cross products.
+__device__ void clip_psd3(double h[6]) {
+    const double m2 = h[0] * h[3] - h[1] * h[1];
+    const double det = h[0] * (h[3] * h[5] - h[4] * h[4]) - h[1] * (h[1] * h[5] - h[4] * h[2]) +
+                       h[2] * (h[1] * h[4] - h[3] * h[2]);
+    if (h[0] > 0.0 && m2 > 0.0 && det > 0.0) return;
+    const double p1 = h[1] * h[1] + h[2] * h[2] + h[4] * h[4];
+    if (p1 == 0.0) {   // diagonal
+        h[0] = fmax(h[0], 0.0);
+        h[3] = fmax(h[3], 0.0);
+        h[5] = fmax(h[5], 0.0);
+        return;
+    }
+    const double q = (h[0] + h[3] + h[5]) / 3.0;
+    const double a0 = h[0] - q, a3 = h[3] - q, a5 = h[5] - q;
+    const double p = sqrt((a0 * a0 + a3 * a3 + a5 * a5 + 2.0 * p1) / 6.0);
+    const double ip = 1.0 / p;
+    const double b0 = a0 * ip, b1 = h[1] * ip, b2 = h[2] * ip, b3 = a3 * ip, b4 = h[4] * ip, b5 = a5 * ip;
+    double r = 0.5 * (b0 * (b3 * b5 - b4 * b4) - b1 * (b1 * b5 - b4 * b2) + b2 * (b1 * b4 - b3 * b2));
+    r = fmin(fmax(r, -1.0), 1.0);
+    const double phi = acos(r) / 3.0;
+    const double lhi = q + 2.0 * p * cos(phi);
+    const double llo = q + 2.0 * p * cos(phi + 2.0943951023931954923);   // + 2 pi / 3
+    const double lmid = 3.0 * q - lhi - llo;
+    const int neg = (lhi < 0.0) + (lmid < 0.0) + (llo < 0.0);
+    if (neg == 0) return;
+    if (neg == 3) {
+        h[0] = h[1] = h[2] = h[3] = h[4] = h[5] = 0.0;
+        return;
+    }
+    double v[3];
+    if (neg == 1) {   // H+ = H - llo v v^T
+        if (!eigvec3(h, llo, v)) {
+            clip_psd3_jacobi(h);
+            return;
+        }
+        h[0] -= llo * v[0] * v[0]; h[1] -= llo * v[0] * v[1]; h[2] -= llo * v[0] * v[2];
+        h[3] -= llo * v[1] * v[1]; h[4] -= llo * v[1] * v[2]; h[5] -= llo * v[2] * v[2];
+    } else {          // H+ = lhi u u^T
+        if (!eigvec3(h, lhi, v)) {
+            clip_psd3_jacobi(h);
+            return;
+        }
+        h[0] = lhi * v[0] * v[0]; h[1] = lhi * v[0] * v[1]; h[2] = lhi * v[0] * v[2];
+        h[3] = lhi * v[1] * v[1]; h[4] = lhi * v[1] * v[2]; h[5] = lhi * v[2] * v[2];
+    }
+}
+
 // Inverse of a symmetric 3x3 (adjugate / determinant); returns false if singular.
 __device__ __forceinline__ bool inv_sym3(const double a[6], double o[6]) {
     const double c00 = a[3] * a[5] - a[4] * a[4];
@@ -251,122 +332,96 @@ __device__ __forceinline__ double sym3(const double a[6], int i, int j) {
     return a[r == 0 ? c : (r == 1 ? 2 + c : 5)];
 }
 
-// Dual step of one ray (see the file header).  Returns y' in yo.
-__device__ void ray_dual(const double al[4][3], const double cw[4], const double rw[4], const double invD[4],
-                         const float Gm[4][6], double X1, float lambda, int model, const double y[4],
-                         double yo[4]) {
-    if (!(X1 > 0.0)) {
+// Dual step of one ray that meets the image (see the file header).
+//   al: window-effective attenuations alpha (FP32), sig: Sigma (FP32),
+//   cw: counts, rw: residuals, Bt: sum_i beta_i mu_i mu_i^T with
+//   beta_i = softexp''_i sum_w r_w s_wi / D_w (FP32, packed), y: dual.
+// The Hessian, its clip, G = (alpha^T alpha)^-1 alpha^T, W = G^T H+ G and the
+// Cholesky solve of (W + Sigma) u = y - r are FP64.  Returns y' in yo.
+__device__ void ray_dual(const float al[4][3], const float sig[4], const double cw[4], const double rw[4],
+                         const float Bt[6], const double y[4], double yo[4]) {
+    double a[4][3];
 #pragma unroll
-        for (int w = 0; w < 4; ++w) yo[w] = y[w];
-        return;
-    }
-    double sig[4];
+    for (int w = 0; w < 4; ++w)
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        const double nw = sqrt(al[w][0] * al[w][0] + al[w][1] * al[w][1] + al[w][2] * al[w][2]);
-        sig[w] = 1.0 / ((double)lambda * nw * X1);
-    }
-    if (model == 1) {
-#pragma unroll
-        for (int w = 0; w < 4; ++w) yo[w] = rw[w];
-        return;
-    }
-    // H = sum_w c_w alpha_w alpha_w^T - sum_w (r_w / D_w) Gamma_w, Gamma_w = sum_i s_wi e''_i mu_i mu_i^T
+        for (int m = 0; m < 3; ++m) a[w][m] = (double)al[w][m];
     double H[6];
     {
         const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
 #pragma unroll
         for (int e = 0; e < 6; ++e) {
-            double acc = 0.0;
+            double acc = -(double)Bt[e];
 #pragma unroll
-            for (int w = 0; w < 4; ++w)
-                acc += cw[w] * al[w][ij[e][0]] * al[w][ij[e][1]] - rw[w] * invD[w] * (double)Gm[w][e];
+            for (int w = 0; w < 4; ++w) acc += cw[w] * a[w][ij[e][0]] * a[w][ij[e][1]];
             H[e] = acc;
         }
     }
     clip_psd3(H);
-    // G = (alpha^T alpha)^-1 alpha^T  (3 x 4);  W = G^T H+ G  (4 x 4)
-    double A[6];
-    A[0] = A[1] = A[2] = A[3] = A[4] = A[5] = 0.0;
+    double A[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        A[0] += al[w][0] * al[w][0]; A[1] += al[w][0] * al[w][1]; A[2] += al[w][0] * al[w][2];
-        A[3] += al[w][1] * al[w][1]; A[4] += al[w][1] * al[w][2]; A[5] += al[w][2] * al[w][2];
+        A[0] += a[w][0] * a[w][0]; A[1] += a[w][0] * a[w][1]; A[2] += a[w][0] * a[w][2];
+        A[3] += a[w][1] * a[w][1]; A[4] += a[w][1] * a[w][2]; A[5] += a[w][2] * a[w][2];
     }
     double Ai[6];
-    double M[4][4];
+    double M[10];   // packed upper triangle of W + Sigma: 00 01 02 03 11 12 13 22 23 33
     if (inv_sym3(A, Ai)) {
         double G[3][4], HG[3][4];
 #pragma unroll
         for (int m = 0; m < 3; ++m)
 #pragma unroll
             for (int w = 0; w < 4; ++w)
-                G[m][w] = sym3(Ai, m, 0) * al[w][0] + sym3(Ai, m, 1) * al[w][1] + sym3(Ai, m, 2) * al[w][2];
+                G[m][w] = sym3(Ai, m, 0) * a[w][0] + sym3(Ai, m, 1) * a[w][1] + sym3(Ai, m, 2) * a[w][2];
 #pragma unroll
         for (int m = 0; m < 3; ++m)
 #pragma unroll
             for (int w = 0; w < 4; ++w)
                 HG[m][w] = sym3(H, m, 0) * G[0][w] + sym3(H, m, 1) * G[1][w] + sym3(H, m, 2) * G[2][w];
+        int t = 0;
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) M[i][j] = G[0][i] * HG[0][j] + G[1][i] * HG[1][j] + G[2][i] * HG[2][j];
+            for (int j = i; j < 4; ++j) M[t++] = G[0][i] * HG[0][j] + G[1][i] * HG[1][j] + G[2][i] * HG[2][j];
     } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) M[i][j] = 0.0;
+        for (int t = 0; t < 10; ++t) M[t] = 0.0;
     }
-#pragma unroll
-    for (int w = 0; w < 4; ++w) M[w][w] += sig[w];
-    // Cholesky of the SPD W + Sigma, then (W + Sigma) u = y - r
-    double Lm[4][4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        double d = M[j][j];
-#pragma unroll
-        for (int k = 0; k < j; ++k) d -= Lm[j][k] * Lm[j][k];
-        d = sqrt(fmax(d, 1e-300));
-        Lm[j][j] = d;
-        const double id = 1.0 / d;
-#pragma unroll
-        for (int i = j + 1; i < 4; ++i) {
-            double s = M[i][j];
-#pragma unroll
-            for (int k = 0; k < j; ++k) s -= Lm[i][k] * Lm[j][k];
-            Lm[i][j] = s * id;
-        }
-    }
-    double z[4], u[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        double s = y[i] - rw[i];
-#pragma unroll
-        for (int k = 0; k < i; ++k) s -= Lm[i][k] * z[k];
-        z[i] = s / Lm[i][i];
-    }
-#pragma unroll
-    for (int i = 3; i >= 0; --i) {
-        double s = z[i];
-#pragma unroll
-        for (int k = i + 1; k < 4; ++k) s -= Lm[k][i] * u[k];
-        u[i] = s / Lm[i][i];
-    }
-#pragma unroll
-    for (int w = 0; w < 4; ++w) yo[w] = y[w] - sig[w] * u[w];
+    M[0] += (double)sig[0];
+    M[4] += (double)sig[1];
+    M[7] += (double)sig[2];
+    M[9] += (double)sig[3];
+    // W + Sigma = L D L^T (SPD: Sigma > 0, W >= 0; unit lower L), then L D L^T u = y - r
+    const double d0 = M[0], i0 = 1.0 / d0;
+    const double l10 = M[1] * i0, l20 = M[2] * i0, l30 = M[3] * i0;
+    const double d1 = fmax(M[4] - l10 * l10 * d0, 1e-300 * d0), i1 = 1.0 / d1;
+    const double l21 = (M[5] - l20 * l10 * d0) * i1, l31 = (M[6] - l30 * l10 * d0) * i1;
+    const double d2 = fmax(M[7] - l20 * l20 * d0 - l21 * l21 * d1, 1e-300 * d0), i2 = 1.0 / d2;
+    const double l32 = (M[8] - l30 * l20 * d0 - l31 * l21 * d1) * i2;
+    const double d3 = fmax(M[9] - l30 * l30 * d0 - l31 * l31 * d1 - l32 * l32 * d2, 1e-300 * d0), i3 = 1.0 / d3;
+    const double z0 = y[0] - rw[0];
+    const double z1 = y[1] - rw[1] - l10 * z0;
+    const double z2 = y[2] - rw[2] - l20 * z0 - l21 * z1;
+    const double z3 = y[3] - rw[3] - l30 * z0 - l31 * z1 - l32 * z2;
+    const double u3 = z3 * i3;
+    const double u2 = z2 * i2 - l32 * u3;
+    const double u1 = z1 * i1 - l21 * u2 - l31 * u3;
+    const double u0 = z0 * i0 - l10 * u1 - l20 * u2 - l30 * u3;
+    yo[0] = y[0] - (double)sig[0] * u0;
+    yo[1] = y[1] - (double)sig[1] * u1;
+    yo[2] = y[2] - (double)sig[2] * u2;
+    yo[3] = y[3] - (double)sig[3] * u3;
 }
 
 // ------------------------------------------------------------------ fused MOCCA kernels
 
-__global__ void __launch_bounds__(kFwdThreads) k_mocca_fwd(GeomC C, ExcTable E, RayRec* rec, SpecD S, StepParams P,
-                                                           SolveD D, int L) {
+__global__ void __launch_bounds__(kFwdThreads, 5) k_mocca_fwd(GeomC C, ExcTable E, RayRec* rec, SpecD S,
+                                                              StepParams P, SolveD D) {
     __shared__ float sm[kSmemStride * kMaxEnergies];
-    __shared__ double red[kFwdThreads / 32];
     load_mu_smem(S, sm);
     __syncthreads();
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int l = ray_of_thread(C);
     double dsum = 0.0;
-    if (l < L) {
+    if (l >= 0) {
         const float4 r0 = rec[l].r0, r1 = rec[l].r1;
         // a1: line integrals of the three maps at the expansion point xbar
         float g0 = 0.f, g1 = 0.f, g2 = 0.f;
@@ -376,27 +431,18 @@ __global__ void __launch_bounds__(kFwdThreads) k_mocca_fwd(GeomC C, ExcTable E, 
             g1 = fmaf(w, v.y, g1);
             g2 = fmaf(w, v.z, g2);
         });
-        // a2/a3: counts model and its first/second-order pieces, summed over energies
-        const int b = l % C.n_bins, nb = C.n_bins;
-        float Ds[4] = {0.f, 0.f, 0.f, 0.f}, Dc[4] = {0.f, 0.f, 0.f, 0.f};
-        float An[4][3], Gm[4][6];
+        // a2/a3, first pass over energies: D_w (compensated) and alpha_w numerators
+        const int b = l % C.n_bins, nb = C.n_bins, nE = S.n_energies;
+        float Ds[4] = {0.f, 0.f, 0.f, 0.f}, Dc[4] = {0.f, 0.f, 0.f, 0.f}, An[4][3];
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-#pragma unroll
-            for (int m = 0; m < 3; ++m) An[w][m] = 0.f;
-#pragma unroll
-            for (int e = 0; e < 6; ++e) Gm[w][e] = 0.f;
-        }
-        for (int i = 0; i < S.n_energies; ++i) {
+        for (int w = 0; w < 4; ++w) An[w][0] = An[w][1] = An[w][2] = 0.f;
+        for (int i = 0; i < nE; ++i) {
             const float4 qa = *reinterpret_cast<const float4*>(sm + kSmemStride * i);
-            const float4 qb = *reinterpret_cast<const float4*>(sm + kSmemStride * i + 4);
-            const float4 qc = *reinterpret_cast<const float4*>(sm + kSmemStride * i + 8);
             const float p = fmaf(qa.z, g2, fmaf(qa.y, g1, qa.x * g0));
             float e0, e1, e2;
             sexp3(-p, e0, e1, e2);
             const float4 s4 = __ldg(S.s4 + (size_t)i * nb + b);
             const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
-            const float mm[6] = {qa.w, qb.x, qb.y, qb.z, qb.w, qc.x};
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 neumaier(Ds[w], Dc[w], sv[w] * e0);
@@ -404,50 +450,81 @@ __global__ void __launch_bounds__(kFwdThreads) k_mocca_fwd(GeomC C, ExcTable E, 
                 An[w][0] = fmaf(a, qa.x, An[w][0]);
                 An[w][1] = fmaf(a, qa.y, An[w][1]);
                 An[w][2] = fmaf(a, qa.z, An[w][2]);
-                const float gq = sv[w] * e2;
-#pragma unroll
-                for (int e = 0; e < 6; ++e) Gm[w][e] = fmaf(gq, mm[e], Gm[w][e]);
             }
         }
         const float4 N = __ldg(S.N4 + b);
         const float4 cc = D.c[l];
         const float4 yy = D.y[l];
         const float Nv[4] = {N.x, N.y, N.z, N.w}, cv[4] = {cc.x, cc.y, cc.z, cc.w};
-        double al[4][3], cw[4], rw[4], invD[4], y[4] = {yy.x, yy.y, yy.z, yy.w}, yo[4];
+        float al[4][3], qw[4], nw[4];
+        double cw[4], rw[4];
         float dt = 0.f;
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
-            const double Dw = (double)Ds[w] + (double)Dc[w];
-            invD[w] = 1.0 / Dw;
-            const double chat = (double)Nv[w] * Dw;
+            const float Dw = Ds[w] + Dc[w];
+            const float invD = 1.0f / Dw;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) al[w][m] = An[w][m] * invD;
+            nw[w] = sqrtf(al[w][0] * al[w][0] + al[w][1] * al[w][1] + al[w][2] * al[w][2]);
+            const double chat = (double)Nv[w] * (double)Dw;
             cw[w] = (double)cv[w];
             rw[w] = cw[w] - chat;
-#pragma unroll
-            for (int m = 0; m < 3; ++m) al[w][m] = (double)An[w][m] * invD[w];
+            qw[w] = (float)rw[w] * invD;
             dt += dtpl_term((float)chat, cv[w]);
         }
         dsum = (double)dt;
-        // a4/a5: per-ray curvature with negative-curvature removal and the dual step
-        ray_dual(al, cw, rw, invD, Gm, (double)__ldg(D.chord + l), P.lambda, P.model, y, yo);
-        D.y[l] = make_float4((float)yo[0], (float)yo[1], (float)yo[2], (float)yo[3]);
+        const float X1 = __ldg(D.chord + l);
+        double y[4] = {yy.x, yy.y, yy.z, yy.w}, yo[4];
+        if (!(X1 > 0.f)) {   // the ray misses the image: Sigma^-1 = 0, the dual is kept
+#pragma unroll
+            for (int w = 0; w < 4; ++w) yo[w] = y[w];
+        } else if (P.model == 1) {   // W = 0: y' = y - Sigma Sigma^-1 (y - r) = r
+#pragma unroll
+            for (int w = 0; w < 4; ++w) yo[w] = rw[w];
+        } else {
+            // second pass: sum_i beta_i mu_i mu_i^T, beta_i = softexp''(-p_i) sum_w (r_w / D_w) s_wi
+            float Bt[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int i = 0; i < nE; ++i) {
+                const float4 qa = *reinterpret_cast<const float4*>(sm + kSmemStride * i);
+                const float p = fmaf(qa.z, g2, fmaf(qa.y, g1, qa.x * g0));
+                if (p < 0.0f) continue;   // softexp'' = 0 where -p > 0
+                const float e2 = expf(-p);
+                const float4 s4 = __ldg(S.s4 + (size_t)i * nb + b);
+                const float beta = e2 * fmaf(qw[3], s4.w, fmaf(qw[2], s4.z, fmaf(qw[1], s4.y, qw[0] * s4.x)));
+                const float4 qb = *reinterpret_cast<const float4*>(sm + kSmemStride * i + 4);
+                const float4 qc = *reinterpret_cast<const float4*>(sm + kSmemStride * i + 8);
+                Bt[0] = fmaf(beta, qa.w, Bt[0]);
+                Bt[1] = fmaf(beta, qb.x, Bt[1]);
+                Bt[2] = fmaf(beta, qb.y, Bt[2]);
+                Bt[3] = fmaf(beta, qb.z, Bt[3]);
+                Bt[4] = fmaf(beta, qb.w, Bt[4]);
+                Bt[5] = fmaf(beta, qc.x, Bt[5]);
+            }
+            // a5: m-block SPC dual step length Sigma_w = 1 / (lambda |alpha_w| (X 1)_l)
+            float sig[4];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) sig[w] = 1.0f / (P.lambda * nw[w] * X1);
+            ray_dual(al, sig, cw, rw, Bt, y, yo);
+        }
+        const float yf[4] = {(float)yo[0], (float)yo[1], (float)yo[2], (float)yo[3]};
+        D.y[l] = make_float4(yf[0], yf[1], yf[2], yf[3]);
         // b = alpha^T y',  S = sum_w alpha_w alpha_w^T / |alpha_w|
-        double bb[3] = {0.0, 0.0, 0.0}, Sm[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        float bb[3] = {0.f, 0.f, 0.f}, Sm[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
-            const double nw = sqrt(al[w][0] * al[w][0] + al[w][1] * al[w][1] + al[w][2] * al[w][2]);
-            const double inw = nw > 0.0 ? 1.0 / nw : 0.0;
+            const float inw = nw[w] > 0.f ? 1.0f / nw[w] : 0.f;
 #pragma unroll
-            for (int m = 0; m < 3; ++m) bb[m] += al[w][m] * yo[w];
-            Sm[0] += al[w][0] * al[w][0] * inw; Sm[1] += al[w][0] * al[w][1] * inw;
-            Sm[2] += al[w][0] * al[w][2] * inw; Sm[3] += al[w][1] * al[w][1] * inw;
-            Sm[4] += al[w][1] * al[w][2] * inw; Sm[5] += al[w][2] * al[w][2] * inw;
+            for (int m = 0; m < 3; ++m) bb[m] = fmaf(al[w][m], yf[w], bb[m]);
+            const float a0 = al[w][0] * inw, a1 = al[w][1] * inw, a2 = al[w][2] * inw;
+            Sm[0] = fmaf(a0, al[w][0], Sm[0]); Sm[1] = fmaf(a0, al[w][1], Sm[1]);
+            Sm[2] = fmaf(a0, al[w][2], Sm[2]); Sm[3] = fmaf(a1, al[w][1], Sm[3]);
+            Sm[4] = fmaf(a1, al[w][2], Sm[4]); Sm[5] = fmaf(a2, al[w][2], Sm[5]);
         }
-        rec[l].r1 = make_float4(r1.x, r1.y, (float)bb[0], (float)bb[1]);
-        rec[l].r2 = make_float4((float)bb[2], (float)Sm[0], (float)Sm[1], (float)Sm[2]);
-        rec[l].r3 = make_float4((float)Sm[3], (float)Sm[4], (float)Sm[5], 0.f);
+        rec[l].r1 = make_float4(r1.x, r1.y, bb[0], bb[1]);
+        rec[l].r2 = make_float4(bb[2], Sm[0], Sm[1], Sm[2]);
+        rec[l].r3 = make_float4(Sm[3], Sm[4], Sm[5], 0.f);
     }
-    const double s = block_sum(dsum, red);
-    if (threadIdx.x == 0) D.dtpl_part[blockIdx.x] = s;
+    warp_partial(dsum, D.dtpl_part);
 }
 
 // Box-constrained primal step: argmin over lo <= x <= hi of 1/2 (x - t)^T Q (x - t),
@@ -513,28 +590,55 @@ __device__ void box_prox3(const double Q[3][3], const double t[3], const float l
     }
 }
 
-__global__ void __launch_bounds__(kBpTileX * kBpTileY) k_mocca_bp(GeomC C, ExcTable E, const RayRec* rec,
-                                                                 const ViewF* views, StepParams P, SolveD D) {
-    const int ix = blockIdx.x * kBpTileX + threadIdx.x, iy = blockIdx.y * kBpTileY + threadIdx.y;
-    if (ix >= C.grid.n || iy >= C.grid.n) return;
-    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-    float p00 = 0.f, p01 = 0.f, p02 = 0.f, p11 = 0.f, p12 = 0.f, p22 = 0.f;
-    pixel_rays(C, E, rec, views, ix, iy, [&](int l, float w, const float4& r1) {
-        const float4 r2 = __ldg(&rec[l].r2), r3 = __ldg(&rec[l].r3);
-        v0 = fmaf(w, r1.z, v0);
-        v1 = fmaf(w, r1.w, v1);
-        v2 = fmaf(w, r2.x, v2);
-        p00 = fmaf(w, r2.y, p00);
-        p01 = fmaf(w, r2.z, p01);
-        p02 = fmaf(w, r2.w, p02);
-        p11 = fmaf(w, r3.x, p11);
-        p12 = fmaf(w, r3.y, p12);
-        p22 = fmaf(w, r3.z, p22);
-    });
+// Pixel-driven back-projection with the views split over blockDim.z thread
+// groups per pixel (contiguous view ranges); the groups' partial sums are
+// added in a fixed order in shared memory, so results are deterministic.
+__global__ void __launch_bounds__(kBpMaxThreads) k_mocca_bp(GeomC C, ExcTable E, const RayRec* rec,
+                                                           const ViewF* views, StepParams P, SolveD D) {
+    extern __shared__ float red[];   // [blockDim.z - 1][9][kBpPix]
+    const int G = blockDim.z, g = threadIdx.z;
+    const int ix = blockIdx.x * kBpPixX + threadIdx.x, iy = blockIdx.y * kBpPixY + threadIdx.y;
+    const int pix = threadIdx.y * kBpPixX + threadIdx.x;
+    const bool valid = ix < C.grid.n && iy < C.grid.n;
+    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+        const int per = (C.n_views + G - 1) / G;
+        const int v0 = g * per, v1 = min(C.n_views, v0 + per);
+        for (int v = v0; v < v1; ++v) {
+            int blo, bhi;
+            pixel_bin_range(C, views[v], ix, iy, blo, bhi);
+            for (int b = blo; b <= bhi; ++b) {
+                const int l = v * C.n_bins + b;
+                const float4 r0 = __ldg(&rec[l].r0);
+                const float4 r1 = __ldg(&rec[l].r1);
+                const float w = x_weight(r0, r1.x, r1.y, C.grid, E, l, ix, iy);
+                if (w == 0.0f) continue;
+                const float4 r2 = __ldg(&rec[l].r2), r3 = __ldg(&rec[l].r3);
+                acc[0] = fmaf(w, r1.z, acc[0]);
+                acc[1] = fmaf(w, r1.w, acc[1]);
+                acc[2] = fmaf(w, r2.x, acc[2]);
+                acc[3] = fmaf(w, r2.y, acc[3]);
+                acc[4] = fmaf(w, r2.z, acc[4]);
+                acc[5] = fmaf(w, r2.w, acc[5]);
+                acc[6] = fmaf(w, r3.x, acc[6]);
+                acc[7] = fmaf(w, r3.y, acc[7]);
+                acc[8] = fmaf(w, r3.z, acc[8]);
+            }
+        }
+    }
+    if (g > 0) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) red[((g - 1) * 9 + c) * kBpPix + pix] = acc[c];
+    }
+    __syncthreads();
+    if (g != 0 || !valid) return;
+    for (int gg = 1; gg < G; ++gg)
+#pragma unroll
+        for (int c = 0; c < 9; ++c) acc[c] += red[((gg - 1) * 9 + c) * kBpPix + pix];
     const int k = iy * C.grid.n + ix;
     const float4 x = D.x[k];
     const double il = 1.0 / (double)P.lambda;
-    double T[6] = {p00 * il, p01 * il, p02 * il, p11 * il, p12 * il, p22 * il};
+    double T[6] = {acc[3] * il, acc[4] * il, acc[5] * il, acc[6] * il, acc[7] * il, acc[8] * il};
     const double tr = T[0] + T[3] + T[5];
     if (!(tr > 0.0)) {
         D.xbar[k] = x;
@@ -546,7 +650,7 @@ __global__ void __launch_bounds__(kBpTileX * kBpTileY) k_mocca_bp(GeomC C, ExcTa
     double Ti[6];
     double t[3] = {(double)x.x, (double)x.y, (double)x.z};
     if (inv_sym3(T, Ti)) {
-        const double vv[3] = {(double)v0, (double)v1, (double)v2};
+        const double vv[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
         t[0] -= Ti[0] * vv[0] + Ti[1] * vv[1] + Ti[2] * vv[2];
         t[1] -= Ti[1] * vv[0] + Ti[3] * vv[1] + Ti[4] * vv[2];
         t[2] -= Ti[2] * vv[0] + Ti[4] * vv[1] + Ti[5] * vv[2];
@@ -577,8 +681,7 @@ inline int blocks(int n, int t) { return (n + t - 1) / t; }
 
 cudaError_t launch_forward4(const GeomC& C, const ExcTable& E, const RayRec* rec, const float4* x, float4* g,
                             cudaStream_t st) {
-    const int L = C.n_views * C.n_bins;
-    k_forward4<<<blocks(L, kFwdThreads), kFwdThreads, 0, st>>>(C, E, rec, x, g, L);
+    k_forward4<<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, E, rec, x, g);
     return cudaGetLastError();
 }
 
@@ -591,22 +694,22 @@ cudaError_t launch_backproject4(const GeomC& C, const ExcTable& E, const RayRec*
 
 cudaError_t launch_counts(const GeomC& C, const ExcTable& E, const RayRec* rec, const SpecD& S, const float4* f,
                           float4* chat, const float4* c, double* dtpl_part, cudaStream_t st) {
-    const int L = C.n_views * C.n_bins;
-    k_counts<<<blocks(L, kFwdThreads), kFwdThreads, 0, st>>>(C, E, rec, S, f, chat, c, dtpl_part, L);
+    k_counts<<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, E, rec, S, f, chat, c, dtpl_part);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mocca_fwd(const GeomC& C, const ExcTable& E, RayRec* rec, const SpecD& S, const StepParams& P,
                              const SolveD& D, cudaStream_t st) {
-    const int L = C.n_views * C.n_bins;
-    k_mocca_fwd<<<blocks(L, kFwdThreads), kFwdThreads, 0, st>>>(C, E, rec, S, P, D, L);
+    k_mocca_fwd<<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, E, rec, S, P, D);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mocca_bp(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
                             const StepParams& P, const SolveD& D, cudaStream_t st) {
-    dim3 grid(blocks(C.grid.n, kBpTileX), blocks(C.grid.n, kBpTileY)), blk(kBpTileX, kBpTileY);
-    k_mocca_bp<<<grid, blk, 0, st>>>(C, E, rec, views, P, D);
+    const int G = bp_view_groups(C.grid.n * C.grid.n, C.n_views);
+    dim3 grid(blocks(C.grid.n, kBpPixX), blocks(C.grid.n, kBpPixY)), blk(kBpPixX, kBpPixY, G);
+    const size_t smem = sizeof(float) * (size_t)(G - 1) * 9 * kBpPix;
+    k_mocca_bp<<<grid, blk, smem, st>>>(C, E, rec, views, P, D);
     return cudaGetLastError();
 }
 

@@ -44,20 +44,28 @@ __device__ __forceinline__ float t_plane(float X, float b, float inv_d) {
     return __fmul_rn(__fsub_rn(X, b), inv_d);
 }
 
-// FP32 chord of pixel (ix, iy) on the ray and the error bound that applies to it.
-__device__ __forceinline__ void chord32(const float4& r0, float ex, float ey, const GridF& G, int ix,
-                                        int iy, float& w, float& eb) {
-    const float tx0 = t_plane(grid_plane(G, ix), r0.x, r0.z);
-    const float tx1 = t_plane(grid_plane(G, ix + 1), r0.x, r0.z);
-    const float ty0 = t_plane(grid_plane(G, iy), r0.y, r0.w);
-    const float ty1 = t_plane(grid_plane(G, iy + 1), r0.y, r0.w);
-    const float txl = fminf(tx0, tx1), txh = fmaxf(tx0, tx1);
-    const float tyl = fminf(ty0, ty1), tyh = fmaxf(ty0, ty1);
+// The chord of a pixel from the ray parameters of its four planes: the ray is
+// inside the pixel for max(entry planes) < t < min(exit planes).  The planes of
+// each axis are ordered by the sign of the reciprocal direction (t is monotone
+// in the plane position), which equals fminf/fmaxf on these values.  The error
+// bound is the one of the plane that decides each end.
+__device__ __forceinline__ void chord_from_planes(float tx0, float tx1, float ty0, float ty1, float idx, float idy,
+                                                  float ex, float ey, float& w, float& eb) {
+    const float txl = idx >= 0.0f ? tx0 : tx1, txh = idx >= 0.0f ? tx1 : tx0;
+    const float tyl = idy >= 0.0f ? ty0 : ty1, tyh = idy >= 0.0f ? ty1 : ty0;
     const float lo = fmaxf(txl, tyl), hi = fminf(txh, tyh);
     w = __fsub_rn(hi, lo);
     const float elo = txl > tyl ? ex : (tyl > txl ? ey : fmaxf(ex, ey));
     const float ehi = txh < tyh ? ex : (tyh < txh ? ey : fmaxf(ex, ey));
     eb = __fadd_rn(elo, ehi);
+}
+
+// FP32 chord of pixel (ix, iy) on the ray and the error bound that applies to it.
+__device__ __forceinline__ void chord32(const float4& r0, float ex, float ey, const GridF& G, int ix,
+                                        int iy, float& w, float& eb) {
+    chord_from_planes(t_plane(grid_plane(G, ix), r0.x, r0.z), t_plane(grid_plane(G, ix + 1), r0.x, r0.z),
+                      t_plane(grid_plane(G, iy), r0.y, r0.w), t_plane(grid_plane(G, iy + 1), r0.y, r0.w), r0.z,
+                      r0.w, ex, ey, w, eb);
 }
 
 // Footprint exception table (CSR over rays): entries (pixel k, weight bits).
@@ -90,45 +98,74 @@ __device__ __forceinline__ int sat_floor(float v) {
     return static_cast<int>(floorf(fminf(fmaxf(v, -1.0e9f), 1.0e9f)));
 }
 
-// Candidate enumeration of a ray's pixels: slabs along the dominant axis,
-// within each slab the minor-axis cells the ray can touch (with a margin that
-// exceeds the FP32 error of the crossing points).  Calls visit(ix, iy) for a
-// superset of the footprint; the visitor applies x_weight.
-template <class Visit>
-__device__ __forceinline__ void for_each_candidate(const float4& r0, const GridF& G, float margin,
-                                                   Visit&& visit) {
-    // r0.zw = (1/dx, 1/dy): the ray is row-major (|dy| >= |dx|) iff |1/dy| <= |1/dx|
-    const bool rows = fabsf(r0.w) <= fabsf(r0.z);
-    // major axis coordinate / minor axis coordinate of the ray
-    const float bM = rows ? r0.y : r0.x, bm = rows ? r0.x : r0.y;
-    const float iM = rows ? r0.w : r0.z, im = rows ? r0.z : r0.w;
+// Candidate enumeration of a ray's pixels with their chords: slabs along the
+// dominant axis (ROWS: y), within each slab the minor-axis cells the ray can
+// touch (with a margin that exceeds the FP32 error of the crossing points).
+// Every plane parameter is computed once and shared by the neighbouring
+// cells; the chord and bound equal chord32's bit for bit.  Calls
+// visit(ix, iy, w, eb) for a superset of the footprint.
+template <bool ROWS, class Visit>
+__device__ __forceinline__ void ray_chords_dir(const float4& r0, float ex, float ey, const GridF& G, float margin,
+                                               Visit&& visit) {
+    const float bM = ROWS ? r0.y : r0.x, bm = ROWS ? r0.x : r0.y;
+    const float iM = ROWS ? r0.w : r0.z, im = ROWS ? r0.z : r0.w;
     const float slope = iM / im;   // d_minor / d_major, |slope| <= 1 (0 for axis-parallel rays)
     const float xlo = G.x0, xhi = grid_plane(G, G.n);
-    // major-axis range where the minor coordinate lies inside the image (with margin)
     int jlo = 0, jhi = G.n - 1;
     if (slope != 0.0f) {
         const float ya = bM + (xlo - margin - bm) / slope;
         const float yb = bM + (xhi + margin - bm) / slope;
-        const float ymin = fminf(ya, yb), ymax = fmaxf(ya, yb);
-        jlo = max(jlo, sat_floor((ymin - G.x0) / G.h) - 1);
-        jhi = min(jhi, sat_floor((ymax - G.x0) / G.h) + 1);
+        jlo = max(jlo, sat_floor((fminf(ya, yb) - G.x0) / G.h) - 1);
+        jhi = min(jhi, sat_floor((fmaxf(ya, yb) - G.x0) / G.h) + 1);
     } else if (bm < xlo - margin || bm > xhi + margin) {
         return;
     }
     const float inv_h = 1.0f / G.h;
+    float pM0 = grid_plane(G, jlo);
+    float tM0 = t_plane(pM0, bM, iM);
     for (int j = jlo; j <= jhi; ++j) {
-        const float pa = grid_plane(G, j) - bM, pb = grid_plane(G, j + 1) - bM;
-        const float ma = fmaf(slope, pa, bm), mb = fmaf(slope, pb, bm);
-        const float mn = fminf(ma, mb) - margin, mx = fmaxf(ma, mb) + margin;
-        int ilo = sat_floor((mn - G.x0) * inv_h);
-        int ihi = sat_floor((mx - G.x0) * inv_h);
-        ilo = max(ilo, 0);
-        ihi = min(ihi, G.n - 1);
-        for (int i = ilo; i <= ihi; ++i) {
-            if (rows) visit(i, j);
-            else visit(j, i);
+        const float pM1 = grid_plane(G, j + 1);
+        const float tM1 = t_plane(pM1, bM, iM);
+        const float ma = fmaf(slope, pM0 - bM, bm), mb = fmaf(slope, pM1 - bM, bm);
+        const int ilo = max(sat_floor((fminf(ma, mb) - margin - G.x0) * inv_h), 0);
+        const int ihi = min(sat_floor((fmaxf(ma, mb) + margin - G.x0) * inv_h), G.n - 1);
+        if (ilo <= ihi) {
+            float tm0 = t_plane(grid_plane(G, ilo), bm, im);
+            for (int i = ilo; i <= ihi; ++i) {
+                const float tm1 = t_plane(grid_plane(G, i + 1), bm, im);
+                float w, eb;
+                if (ROWS) {
+                    chord_from_planes(tm0, tm1, tM0, tM1, r0.z, r0.w, ex, ey, w, eb);
+                    visit(i, j, w, eb);
+                } else {
+                    chord_from_planes(tM0, tM1, tm0, tm1, r0.z, r0.w, ex, ey, w, eb);
+                    visit(j, i, w, eb);
+                }
+                tm0 = tm1;
+            }
         }
+        pM0 = pM1;
+        tM0 = tM1;
     }
+}
+
+template <class Visit>
+__device__ __forceinline__ void ray_chords(const float4& r0, float ex, float ey, const GridF& G, float margin,
+                                           Visit&& visit) {
+    // r0.zw = (1/dx, 1/dy): the ray is row-major (|dy| >= |dx|) iff |1/dy| <= |1/dx|
+    if (fabsf(r0.w) <= fabsf(r0.z)) ray_chords_dir<true>(r0, ex, ey, G, margin, visit);
+    else ray_chords_dir<false>(r0, ex, ey, G, margin, visit);
+}
+
+// X_{l,k} for every pixel of ray l with a nonzero weight: visit(k, w).
+template <class Visit>
+__device__ __forceinline__ void ray_weights(const float4& r0, float ex, float ey, const GridF& G, float margin,
+                                            const ExcTable& E, int l, Visit&& visit) {
+    ray_chords(r0, ex, ey, G, margin, [&](int ix, int iy, float w, float eb) {
+        if (w < -eb) return;
+        const float x = w > eb ? w : exc_lookup(E, l, iy * G.n + ix);   // also reached by NaN
+        if (x != 0.0f) visit(iy * G.n + ix, x);
+    });
 }
 
 // Per-view constants for the pixel-driven back-projection: the detector bin
@@ -159,7 +196,7 @@ __device__ __forceinline__ void pixel_bin_range(const GeomC& C, const ViewF& V, 
         const float X = (q & 1) ? X1 : X0, Y = (q & 2) ? Y1 : Y0;
         const float num = -V.s * X + V.c * Y;
         const float den = C.sid - (V.c * X + V.s * Y);
-        const float beta = C.scale * num / den + C.mid;
+        const float beta = C.scale * __fdividef(num, den) + C.mid;   // 2-ulp division; the margin covers it
         bmin = fminf(bmin, beta);
         bmax = fmaxf(bmax, beta);
     }

@@ -47,7 +47,18 @@ struct SolveD {
 };
 
 constexpr int kFwdThreads = 128;
-constexpr int kBpTileX = 16, kBpTileY = 8;
+constexpr int kBpTileX = 16, kBpTileY = 8;            // plain back-projection tile
+constexpr int kBpPixX = 8, kBpPixY = 8;               // MOCCA back-projection pixel tile
+constexpr int kBpPix = kBpPixX * kBpPixY;
+constexpr int kBpMaxThreads = 512;                    // kBpPix x up to 8 view groups
+
+// View groups per pixel for the MOCCA back-projection: enough threads to fill
+// the GPU several times over, at most 8, and at least one view per group.
+inline int bp_view_groups(int n_pixels, int n_views) {
+    int G = n_pixels <= 131072 ? 8 : (n_pixels <= 524288 ? 4 : 2);
+    while (G > 1 && G > n_views) G >>= 1;
+    return G;
+}
 
 cudaError_t launch_ray_setup(const GeomD& G, double r_img, RayRec* rec, Ray64* r64, ViewF* views,
                              cudaStream_t st);
@@ -71,6 +82,14 @@ cudaError_t launch_mocca_bp(const GeomC& C, const ExcTable& E, const RayRec* rec
                             const StepParams& P, const SolveD& D, cudaStream_t st);
 cudaError_t launch_dtpl_reduce(const double* part, int n, double* out, cudaStream_t st);
 
-inline int fwd_blocks(int L) { return (L + kFwdThreads - 1) / kFwdThreads; }
+// Ray-driven kernels: blocks of 32 bins x (kFwdThreads / 32) views.
+inline dim3 fwd_grid(int n_bins, int n_views) {
+    return dim3((n_bins + 31) / 32, (n_views + kFwdThreads / 32 - 1) / (kFwdThreads / 32));
+}
+// D_TPL partial sums: one per warp of the ray-driven kernels.
+inline int dtpl_partials(int n_bins, int n_views) {
+    const dim3 g = fwd_grid(n_bins, n_views);
+    return (int)(g.x * g.y) * (kFwdThreads / 32);
+}
 
 }  // namespace osscir
