@@ -36,7 +36,7 @@ METRIC = ("MOCCA iters/sec & recon/s at 256² (served vs plain, 1 GB300) at 1e-4
 WORKLOAD = "medium_256"
 WORKLOAD_DESC = ("256x256 (0.5 mm), 512 views x 512 bins, 4 windows, 101 energies, 3 materials "
                  "(PMMA/Al/Gd), ellipse phantom 4 Al + 6 Gd, Poisson 1e5 photons/ray")
-LAMBDA = 3e-8
+LAMBDA = 10.0 ** -7.5   # tuned with the oracle: tests/golden/lambda_sweeps.json
 SOLVE_ITERS = 500
 # FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -242,6 +242,8 @@ def run_gpu(args):
     e2e_rate = ws * e2e_steps * SOLVE_ITERS / e2e_s
     finite = bool(torch.isfinite(maps_host).all().item())
 
+    served = run_served(args, w, R, chat, rank) if args.served > 0 else None
+
     if rank != 0:
         return 0
     fwd_mean = statistics.mean(fwd_ms)
@@ -281,6 +283,8 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(maps_host.numel() * 4),
                 "step": f"one {SOLVE_ITERS}-iteration reconstruction via osscir_reconstruct (pinned host buffers)",
                 "recon_per_s": e2e_rate / SOLVE_ITERS},
+        "plain_recon_per_s": e2e_rate / SOLVE_ITERS,
+        "served": served,
         "clocks": clk.summary(),
         "gpu_launches": 3 * args.steps,
         "dtpl_last": d_last,
@@ -291,6 +295,51 @@ def run_gpu(args):
     return 0
 
 
+def run_served(args, w, R, chat, rank):
+    """Served form: args.served requests of the same workload (each its own
+    seeded Poisson counts, SOLVE_ITERS iterations) submitted with seeded
+    Poisson arrivals at args.rate requests/s to a server with a 150 GB budget."""
+    import numpy as np
+    import torch
+
+    from paper_1801_06263_gb300 import _lib
+    counts = []
+    for k in range(args.served):
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(3000 + 17 * rank + k)
+        counts.append(torch.poisson(chat, generator=gen).cpu().numpy())
+    rng = np.random.default_rng(3000 + rank)
+    gaps = rng.exponential(1.0 / args.rate, size=args.served)
+    sp = w.spectra
+    srv = _lib.osscir_server_create(150 << 30, args.slots)
+    try:
+        # warm the server's context cache with one short request
+        t = _lib.osscir_submit(srv, w.geom, sp.s, sp.N, sp.mu, LAMBDA, counts[0], 5)
+        _lib.osscir_poll(srv, t, -1)
+        t0 = time.perf_counter()
+        tickets = []
+        for k in range(args.served):
+            target = t0 + float(np.sum(gaps[:k]))
+            while time.perf_counter() < target:
+                time.sleep(min(0.001, max(0.0, target - time.perf_counter())))
+            tickets.append(_lib.osscir_submit(srv, w.geom, sp.s, sp.N, sp.mu, LAMBDA, counts[k], SOLVE_ITERS))
+        lat, gpu, status = [], [], []
+        for t in tickets:
+            rc, st = _lib.osscir_poll(srv, t, -1)
+            status.append(rc)
+            lat.append(st.latency_ms)
+            gpu.append(st.gpu_ms)
+        wall = time.perf_counter() - t0
+    finally:
+        _lib.osscir_server_destroy(srv)
+    lat = np.array(lat)
+    return {"recon_per_s": args.served / wall, "iters_per_s": args.served * SOLVE_ITERS / wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "requests": args.served, "slots": args.slots, "arrival_rate_per_s": args.rate,
+            "all_ok": all(r == 0 for r in status),
+            "note": "Poisson arrivals, 150 GB budget, one stream per admitted request"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -299,6 +348,9 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--e2e", type=int, default=3, help="full reconstructions for the end-to-end rate")
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle iterations for the CPU baseline")
+    ap.add_argument("--served", type=int, default=16, help="requests for the served measurement (0: skip)")
+    ap.add_argument("--slots", type=int, default=8, help="server slots")
+    ap.add_argument("--rate", type=float, default=4.0, help="request arrival rate, requests/s")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -173,6 +173,60 @@ osscir_status osscir_footprint_rays(osscir_t h, int l0, int n, int cap, int *cnt
 osscir_status osscir_footprint_pixels(osscir_t h, int k0, int n, int cap, int *cnt, int *idx, float *wt,
                                       void *stream);
 
+/* ------------------------------------------------------------------ served form
+ * A server owns a worker thread on the device that is current when it is
+ * created.  Requests (complete reconstruction problems with host data) are
+ * queued by osscir_submit and admitted while a slot is free and the device
+ * memory of all cached contexts stays within the budget; admitted requests run
+ * concurrently on their own streams (continuous batching: new requests join
+ * while others are on the GPU).  Contexts of finished requests stay cached and
+ * are reused by later requests with the same geometry, spectra, mu and
+ * parameters; the least recently used idle ones are released when memory is
+ * needed.  A request's result does not depend on what else runs. */
+typedef struct osscir_server *osscir_server_t;
+
+typedef struct {
+    osscir_geometry geom;
+    osscir_spectra spectra; /* host arrays, copied at submit */
+    const float *mu;        /* host float[3][n_energies], copied at submit */
+    osscir_params params;
+    const float *counts;    /* host float[L][4], measured counts c >= 0, copied at submit */
+    int n_iters;            /* MOCCA iterations from x_0 = 0 */
+} osscir_request;
+
+typedef struct {
+    osscir_status status; /* OSSCIR_OK, OSSCIR_E_DIVERGED (non-finite D_TPL) or an error */
+    int iterations;
+    double dtpl;          /* D_TPL at the last expansion point */
+    double latency_ms;    /* submit to result ready (host clock) */
+    double queue_ms;      /* submit to work enqueued on the GPU */
+    double gpu_ms;        /* device time of the solve (events on its stream) */
+} osscir_stats;
+
+/* Create a server.  hbm_budget_bytes: device memory the server's contexts may
+ * hold; max_slots: requests running at once (1 .. 256). */
+osscir_status osscir_server_create(size_t hbm_budget_bytes, int max_slots, osscir_server_t *out);
+
+/* Stop the server: queued requests are dropped, running ones finish, every
+ * resource is released (synchronises). NULL is a no-op. */
+osscir_status osscir_server_destroy(osscir_server_t s);
+
+/* Queue a request; *ticket identifies it.  Errors: OSSCIR_E_INVALID (as
+ * osscir_create, or counts < 0 / non-finite, n_iters < 0), OSSCIR_E_BUSY (the
+ * request alone needs more device memory than the budget). */
+osscir_status osscir_submit(osscir_server_t s, const osscir_request *req, uint64_t *ticket);
+
+/* Wait up to timeout_ms (< 0: no limit) for a request.  When done, copies the
+ * maps x_n to maps_out (host float[P][4], may be NULL), fills stats (may be
+ * NULL), forgets the ticket and returns the request's status.  Returns
+ * OSSCIR_E_TIMEOUT if it is still queued or running (the ticket stays valid)
+ * and OSSCIR_E_NOTFOUND for an unknown ticket. */
+osscir_status osscir_poll(osscir_server_t s, uint64_t ticket, int timeout_ms, float *maps_out, osscir_stats *stats);
+
+/* Requests running and queued, and device bytes held by the server's contexts
+ * (any pointer may be NULL). */
+osscir_status osscir_server_info(osscir_server_t s, int *running, int *queued, size_t *bytes_in_use);
+
 /* D_TPL (Eq. DTPL form) of expected counts chat and measured counts c, computed
  * without allocating any memory and without a context.  The paper has no
  * counterpart: this serves callers that must not call cudaMalloc after

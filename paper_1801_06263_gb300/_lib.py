@@ -29,6 +29,7 @@ EXPORTS = (
     "osscir_backproject", "osscir_simulate", "osscir_set_counts", "osscir_mocca_step", "osscir_get_maps",
     "osscir_get_state", "osscir_set_state", "osscir_dtpl", "osscir_footprint_rays",
     "osscir_footprint_pixels", "osscir_reconstruct", "osscir_last_kernel_ms", "osscir_dtpl_counts_static",
+    "osscir_server_create", "osscir_server_destroy", "osscir_submit", "osscir_poll", "osscir_server_info",
 )
 
 
@@ -51,6 +52,16 @@ class Spectra(ct.Structure):
 class Params(ct.Structure):
     _fields_ = [("lambda_", ct.c_double), ("model", ct.c_int), ("use_box", ct.c_int),
                 ("lo", ct.c_float * 3), ("hi", ct.c_float * 3)]
+
+
+class Request(ct.Structure):
+    _fields_ = [("geom", Geometry), ("spectra", Spectra), ("mu", ct.POINTER(ct.c_float)), ("params", Params),
+                ("counts", ct.POINTER(ct.c_float)), ("n_iters", ct.c_int)]
+
+
+class Stats(ct.Structure):
+    _fields_ = [("status", ct.c_int), ("iterations", ct.c_int), ("dtpl", ct.c_double),
+                ("latency_ms", ct.c_double), ("queue_ms", ct.c_double), ("gpu_ms", ct.c_double)]
 
 
 _lib = None
@@ -91,6 +102,11 @@ def load(build_if_missing: bool = True):
         "osscir_reconstruct": ([vp, vp, ct.c_int, vp, vp], ct.c_int),
         "osscir_last_kernel_ms": ([vp, ct.POINTER(ct.c_float), ct.POINTER(ct.c_float), vp], ct.c_int),
         "osscir_dtpl_counts_static": ([vp, vp, ct.c_int, vp, vp], ct.c_int),
+        "osscir_server_create": ([ct.c_size_t, ct.c_int, ct.POINTER(ct.c_void_p)], ct.c_int),
+        "osscir_server_destroy": ([vp], ct.c_int),
+        "osscir_submit": ([vp, ct.POINTER(Request), ct.POINTER(ct.c_uint64)], ct.c_int),
+        "osscir_poll": ([vp, ct.c_uint64, ct.c_int, vp, ct.POINTER(Stats)], ct.c_int),
+        "osscir_server_info": ([vp, ip, ip, ct.POINTER(ct.c_size_t)], ct.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -132,6 +148,17 @@ def _stream(stream):
 
 # --------------------------------------------------------------------------- C-ABI mirrors
 
+def _geometry(geom):
+    return Geometry(int(geom.n), float(geom.pixel_mm), int(geom.n_views), float(geom.arc_deg),
+                    float(geom.start_deg), int(geom.n_bins), float(geom.bin_mm), float(geom.sid_mm),
+                    float(geom.sdd_mm))
+
+
+def _params(lam, model=0, box=None):
+    lo, hi = (box if box is not None else ((0.0,) * 3, (0.0,) * 3))
+    return Params(float(lam), int(model), int(box is not None), (ct.c_float * 3)(*lo), (ct.c_float * 3)(*hi))
+
+
 def osscir_create(geom, s, N, mu, lam, model=0, box=None):
     """geom: object with the osscir_geometry fields; s [n_bins, nE, 4], N [n_bins, 4],
     mu [3, nE] host arrays (copied).  Returns the handle (int)."""
@@ -139,13 +166,10 @@ def osscir_create(geom, s, N, mu, lam, model=0, box=None):
     s32 = np.ascontiguousarray(s, dtype=np.float32)
     N32 = np.ascontiguousarray(N, dtype=np.float32)
     mu32 = np.ascontiguousarray(mu, dtype=np.float32)
-    g = Geometry(int(geom.n), float(geom.pixel_mm), int(geom.n_views), float(geom.arc_deg),
-                 float(geom.start_deg), int(geom.n_bins), float(geom.bin_mm), float(geom.sid_mm),
-                 float(geom.sdd_mm))
+    g = _geometry(geom)
     sp = Spectra(int(s32.shape[1]), s32.ctypes.data_as(ct.POINTER(ct.c_float)),
                  N32.ctypes.data_as(ct.POINTER(ct.c_float)))
-    lo, hi = (box if box is not None else ((0.0,) * 3, (0.0,) * 3))
-    p = Params(float(lam), int(model), int(box is not None), (ct.c_float * 3)(*lo), (ct.c_float * 3)(*hi))
+    p = _params(lam, model, box)
     h = ct.c_void_p()
     _check("osscir_create", L.osscir_create(ct.byref(g), ct.byref(sp),
                                             mu32.ctypes.data_as(ct.POINTER(ct.c_float)), ct.byref(p),
@@ -236,3 +260,45 @@ def osscir_dtpl_counts_static(chat, c, out, stream=None):
     into out (device float64 [1]) without allocating memory; see include/osscir.h."""
     _check("osscir_dtpl_counts_static", load().osscir_dtpl_counts_static(
         _ptr(chat), _ptr(c), int(chat.shape[0]), _ptr(out), _stream(stream)))
+
+
+# --------------------------------------------------------------------------- served form
+
+def osscir_server_create(hbm_budget_bytes, max_slots):
+    h = ct.c_void_p()
+    _check("osscir_server_create", load().osscir_server_create(int(hbm_budget_bytes), int(max_slots), ct.byref(h)))
+    return h.value
+
+
+def osscir_server_destroy(server):
+    _check("osscir_server_destroy", load().osscir_server_destroy(ct.c_void_p(server)))
+
+
+def osscir_submit(server, geom, s, N, mu, lam, counts, n_iters, model=0, box=None):
+    """Host numpy arrays (copied by the call): s [n_bins, nE, 4], N [n_bins, 4], mu [3, nE],
+    counts [L, 4].  Returns the ticket."""
+    s32 = np.ascontiguousarray(s, dtype=np.float32)
+    N32 = np.ascontiguousarray(N, dtype=np.float32)
+    mu32 = np.ascontiguousarray(mu, dtype=np.float32)
+    c32 = np.ascontiguousarray(counts, dtype=np.float32)
+    fptr = lambda a: a.ctypes.data_as(ct.POINTER(ct.c_float))
+    req = Request(_geometry(geom), Spectra(int(s32.shape[1]), fptr(s32), fptr(N32)), fptr(mu32),
+                  _params(lam, model, box), fptr(c32), int(n_iters))
+    t = ct.c_uint64()
+    _check("osscir_submit", load().osscir_submit(ct.c_void_p(server), ct.byref(req), ct.byref(t)))
+    return t.value
+
+
+def osscir_poll(server, ticket, timeout_ms, maps_out=None):
+    """maps_out: contiguous float32 numpy array [P, 4] or None.  Returns (status, Stats)."""
+    st = Stats()
+    ptr = None if maps_out is None else maps_out.ctypes.data_as(ct.c_void_p)
+    rc = load().osscir_poll(ct.c_void_p(server), ct.c_uint64(ticket), int(timeout_ms), ptr, ct.byref(st))
+    return rc, st
+
+
+def osscir_server_info(server):
+    r, q, b = ct.c_int(), ct.c_int(), ct.c_size_t()
+    _check("osscir_server_info", load().osscir_server_info(ct.c_void_p(server), ct.byref(r), ct.byref(q),
+                                                           ct.byref(b)))
+    return r.value, q.value, b.value

@@ -6,54 +6,21 @@
 #include <new>
 #include <vector>
 
-#include "../../include/osscir.h"
-#include "osscir_launch.h"
+#include "osscir_ctx.h"
 
 using namespace osscir;
 
-struct osscir_ctx {
-    int device = 0;
-    GeomD g64{};
-    GeomC gc{};
-    int P = 0, L = 0, nE = 0;
-    StepParams params{};
-    // per-geometry tables
-    RayRec* rec = nullptr;
-    Ray64* r64 = nullptr;
-    ViewF* views = nullptr;
-    float* chord = nullptr;
-    int* exc_off = nullptr;
-    int2* exc_ent = nullptr;
-    int exc_n = 0;
-    // spectral tables
-    float4* s4 = nullptr;
-    float4* N4 = nullptr;
-    float* mu = nullptr;
-    // solver state
-    float4* c = nullptr;
-    float4* y = nullptr;
-    float4* x = nullptr;
-    float4* xbar = nullptr;
-    double* dtpl_part = nullptr;
-    double* dtpl_out = nullptr;   // [0]: at x (on request), [1]: at the last expansion point
-    int n_part = 0;
-    int iter = 0;
-    // per-iteration graph
-    cudaStream_t cap_stream = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // recorded around the kernels inside the graph
-
-    ExcTable exc() const { return ExcTable{exc_off, exc_ent}; }
-    SpecD spec() const { return SpecD{nE, s4, N4, mu}; }
-    SolveD solve() const { return SolveD{c, y, x, xbar, chord, dtpl_part}; }
-};
-
 namespace {
+
+thread_local size_t g_dalloc_bytes_sink = 0;
+thread_local size_t* g_dalloc_bytes = &g_dalloc_bytes_sink;
 
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
-    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1));
+    const size_t bytes = sizeof(T) * (count ? count : 1);
+    const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (e == cudaSuccess) *g_dalloc_bytes += bytes;
+    return e;
 }
 
 osscir_status from_cuda(cudaError_t e) {
@@ -124,6 +91,7 @@ osscir_status validate(const osscir_geometry* g, const osscir_spectra* sp, const
 
 osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectra* sp, const float* mu,
                     const osscir_params* pa) {
+    g_dalloc_bytes = &h->bytes;
     CK(cudaGetDevice(&h->device));
     const int n = g->n;
     h->P = n * n;
@@ -251,6 +219,36 @@ osscir_status ensure_graph(osscir_ctx* h) {
 
 }  // namespace
 
+namespace osscir {
+
+osscir_status ctx_create(const osscir_geometry* geom, const osscir_spectra* spectra, const float* mu,
+                         const osscir_params* params, osscir_ctx** out) {
+    *out = nullptr;
+    const osscir_status v = validate(geom, spectra, mu, params);
+    if (v != OSSCIR_OK) return v;
+    osscir_ctx* h = new (std::nothrow) osscir_ctx();
+    if (!h) return OSSCIR_E_NOMEM;
+    const osscir_status s = build(h, geom, spectra, mu, params);
+    g_dalloc_bytes = &g_dalloc_bytes_sink;
+    if (s != OSSCIR_OK) {
+        free_ctx(h);
+        return s;
+    }
+    *out = h;
+    return OSSCIR_OK;
+}
+
+void ctx_destroy(osscir_ctx* h) { free_ctx(h); }
+
+osscir_status ctx_validate(const osscir_geometry* geom, const osscir_spectra* spectra, const float* mu,
+                           const osscir_params* params) {
+    return validate(geom, spectra, mu, params);
+}
+
+osscir_status ctx_ensure_graph(osscir_ctx* h) { return ensure_graph(h); }
+
+}  // namespace osscir
+
 extern "C" {
 
 const char* osscir_status_string(osscir_status s) {
@@ -270,18 +268,7 @@ const char* osscir_status_string(osscir_status s) {
 osscir_status osscir_create(const osscir_geometry* geom, const osscir_spectra* spectra, const float* mu,
                             const osscir_params* params, osscir_t* out) {
     if (!out) return OSSCIR_E_INVALID;
-    *out = nullptr;
-    const osscir_status v = validate(geom, spectra, mu, params);
-    if (v != OSSCIR_OK) return v;
-    osscir_ctx* h = new (std::nothrow) osscir_ctx();
-    if (!h) return OSSCIR_E_NOMEM;
-    const osscir_status s = build(h, geom, spectra, mu, params);
-    if (s != OSSCIR_OK) {
-        free_ctx(h);
-        return s;
-    }
-    *out = h;
-    return OSSCIR_OK;
+    return osscir::ctx_create(geom, spectra, mu, params, out);
 }
 
 osscir_status osscir_destroy(osscir_t h) {

@@ -1,0 +1,61 @@
+// The reconstruction context behind osscir_t (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+#include "../../include/osscir.h"
+#include "osscir_launch.h"
+
+struct osscir_ctx {
+    int device = 0;
+    size_t bytes = 0;   // device bytes allocated by this context
+    osscir::GeomD g64{};
+    osscir::GeomC gc{};
+    int P = 0, L = 0, nE = 0;
+    osscir::StepParams params{};
+    // per-geometry tables
+    osscir::RayRec* rec = nullptr;
+    osscir::Ray64* r64 = nullptr;
+    osscir::ViewF* views = nullptr;
+    float* chord = nullptr;
+    int* exc_off = nullptr;
+    int2* exc_ent = nullptr;
+    int exc_n = 0;
+    // spectral tables
+    float4* s4 = nullptr;
+    float4* N4 = nullptr;
+    float* mu = nullptr;
+    // solver state
+    float4* c = nullptr;
+    float4* y = nullptr;
+    float4* x = nullptr;
+    float4* xbar = nullptr;
+    double* dtpl_part = nullptr;
+    double* dtpl_out = nullptr;   // [0]: at x (on request), [1]: at the last expansion point
+    int n_part = 0;
+    int iter = 0;
+    // per-iteration graph
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // recorded around the kernels inside the graph
+
+    osscir::ExcTable exc() const { return osscir::ExcTable{exc_off, exc_ent}; }
+    osscir::SpecD spec() const { return osscir::SpecD{nE, s4, N4, mu}; }
+    osscir::SolveD solve() const { return osscir::SolveD{c, y, x, xbar, chord, dtpl_part}; }
+};
+
+namespace osscir {
+
+// Validate the inputs, allocate the device state and build the per-geometry
+// tables on the current device (synchronises).  On error *out is null.
+osscir_status ctx_create(const osscir_geometry* geom, const osscir_spectra* spectra, const float* mu,
+                         const osscir_params* params, osscir_ctx** out);
+void ctx_destroy(osscir_ctx* h);
+osscir_status ctx_validate(const osscir_geometry* geom, const osscir_spectra* spectra, const float* mu,
+                           const osscir_params* params);
+// Capture the per-iteration graph once.
+osscir_status ctx_ensure_graph(osscir_ctx* h);
+
+}  // namespace osscir
