@@ -8,6 +8,7 @@
 #include <condition_variable>
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <deque>
 #include <list>
 #include <mutex>
@@ -70,6 +71,9 @@ struct Ticket {
     float gpu_ms = 0.f;
 };
 
+constexpr int kChunk = 4;      // MOCCA iterations per enqueued chunk
+constexpr int kInFlight = 2;   // chunks queued per stream at a time
+
 struct Slot {
     osscir_ctx* ctx = nullptr;
     Config cfg;
@@ -79,7 +83,13 @@ struct Slot {
     float* h_maps = nullptr;     // pinned
     double* h_dtpl = nullptr;    // pinned
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t evc[kInFlight] = {nullptr, nullptr};
     Ticket* running = nullptr;
+    int enq = 0;        // iterations enqueued
+    int head = 0;       // oldest chunk event in flight
+    int in_flight = 0;  // chunks in flight
+    bool tail = false;  // results copy-back enqueued
+    bool failed = false;
     uint64_t last_used = 0;
     size_t bytes = 0;
 };
@@ -98,6 +108,8 @@ void release_slot(Slot* s) {
     if (s->stream) cudaStreamDestroy(s->stream);
     if (s->ev0) cudaEventDestroy(s->ev0);
     if (s->ev1) cudaEventDestroy(s->ev1);
+    for (cudaEvent_t e : s->evc)
+        if (e) cudaEventDestroy(e);
     if (s->h_counts) cudaFreeHost(s->h_counts);
     if (s->h_maps) cudaFreeHost(s->h_maps);
     if (s->h_dtpl) cudaFreeHost(s->h_dtpl);
@@ -123,8 +135,9 @@ struct osscir_server {
 
     void run();
     Slot* acquire(Ticket* t);   // with mu held
-    bool start(Slot* s, Ticket* t);
-    void finish(Slot* s);
+    bool begin(Slot* s);        // worker thread, no lock
+    bool advance(Slot* s);      // worker thread, no lock; true if anything happened
+    void finish(Slot* s);       // with mu held
 };
 
 // An idle cached context of the same configuration, or a new one once memory
@@ -150,6 +163,8 @@ Slot* osscir_server::acquire(Ticket* t) {
     const size_t L = (size_t)t->cfg.geom.n_views * t->cfg.geom.n_bins, P = (size_t)t->cfg.geom.n * t->cfg.geom.n;
     if (st == OSSCIR_OK && (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
                             cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess ||
+                            cudaEventCreateWithFlags(&s->evc[0], cudaEventDisableTiming) != cudaSuccess ||
+                            cudaEventCreateWithFlags(&s->evc[1], cudaEventDisableTiming) != cudaSuccess ||
                             cudaHostAlloc(&s->h_counts, L * 16, cudaHostAllocDefault) != cudaSuccess ||
                             cudaHostAlloc(&s->h_maps, P * 16, cudaHostAllocDefault) != cudaSuccess ||
                             cudaHostAlloc(&s->h_dtpl, sizeof(double), cudaHostAllocDefault) != cudaSuccess))
@@ -166,31 +181,73 @@ Slot* osscir_server::acquire(Ticket* t) {
     return s;
 }
 
-bool osscir_server::start(Slot* s, Ticket* t) {
+// Copy the counts in and reset the state (the iterations follow in chunks).
+bool osscir_server::begin(Slot* s) {
+    Ticket* t = s->running;
     osscir_ctx* h = s->ctx;
     std::memcpy(s->h_counts, t->counts.data(), t->counts.size() * sizeof(float));
     cudaStream_t st = s->stream;
-    bool ok = cudaEventRecord(s->ev0, st) == cudaSuccess &&
-              cudaMemcpyAsync(h->c, s->h_counts, sizeof(float4) * h->L, cudaMemcpyHostToDevice, st) == cudaSuccess &&
-              cudaMemsetAsync(h->y, 0, sizeof(float4) * h->L, st) == cudaSuccess &&
-              cudaMemsetAsync(h->x, 0, sizeof(float4) * h->P, st) == cudaSuccess &&
-              cudaMemsetAsync(h->xbar, 0, sizeof(float4) * h->P, st) == cudaSuccess &&
-              cudaMemsetAsync(h->dtpl_out, 0, sizeof(double) * 2, st) == cudaSuccess;
-    for (int i = 0; ok && i < t->n_iters; ++i) ok = cudaGraphLaunch(h->gexec, st) == cudaSuccess;
-    ok = ok && cudaMemcpyAsync(s->h_maps, h->x, sizeof(float4) * h->P, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
-         cudaMemcpyAsync(s->h_dtpl, h->dtpl_out + 1, sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
-         cudaEventRecord(s->ev1, st) == cudaSuccess;
-    h->iter = t->n_iters;
-    t->t_start = clk::now();
-    s->running = t;
-    s->last_used = ++clock;
-    ++running;
-    return ok;
+    s->enq = s->head = s->in_flight = 0;
+    s->tail = s->failed = false;
+    h->iter = 0;
+    return cudaEventRecord(s->ev0, st) == cudaSuccess &&
+           cudaMemcpyAsync(h->c, s->h_counts, sizeof(float4) * h->L, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+           cudaMemsetAsync(h->y, 0, sizeof(float4) * h->L, st) == cudaSuccess &&
+           cudaMemsetAsync(h->x, 0, sizeof(float4) * h->P, st) == cudaSuccess &&
+           cudaMemsetAsync(h->xbar, 0, sizeof(float4) * h->P, st) == cudaSuccess &&
+           cudaMemsetAsync(h->dtpl_out, 0, sizeof(double) * 2, st) == cudaSuccess;
+}
+
+// Keep at most kInFlight chunks of kChunk iterations queued on the slot's
+// stream, then the copy-back of the results; returns true if it did anything.
+bool osscir_server::advance(Slot* s) {
+    Ticket* t = s->running;
+    osscir_ctx* h = s->ctx;
+    bool acted = false;
+    while (s->in_flight > 0) {
+        const cudaError_t q = cudaEventQuery(s->evc[s->head]);
+        if (q == cudaErrorNotReady) break;
+        if (q != cudaSuccess) s->failed = true;
+        s->head = (s->head + 1) % kInFlight;
+        --s->in_flight;
+        acted = true;
+    }
+    while (!s->tail && !s->failed && s->in_flight < kInFlight && s->enq < t->n_iters) {
+        const int k = std::min(kChunk, t->n_iters - s->enq);
+        bool ok = true;
+        for (int i = 0; ok && i < k; ++i) ok = cudaGraphLaunch(h->gexec, s->stream) == cudaSuccess;
+        ok = ok && cudaEventRecord(s->evc[(s->head + s->in_flight) % kInFlight], s->stream) == cudaSuccess;
+        if (!ok) s->failed = true;
+        ++s->in_flight;
+        s->enq += k;
+        acted = true;
+    }
+    if (!s->tail && (s->enq >= t->n_iters || s->failed)) {
+        const bool ok =
+            cudaMemcpyAsync(s->h_maps, h->x, sizeof(float4) * h->P, cudaMemcpyDeviceToHost, s->stream) == cudaSuccess &&
+            cudaMemcpyAsync(s->h_dtpl, h->dtpl_out + 1, sizeof(double), cudaMemcpyDeviceToHost, s->stream) ==
+                cudaSuccess &&
+            cudaEventRecord(s->ev1, s->stream) == cudaSuccess;
+        if (!ok) s->failed = true;
+        h->iter = s->enq;
+        s->tail = true;
+        acted = true;
+    }
+    return acted;
 }
 
 void osscir_server::finish(Slot* s) {
     Ticket* t = s->running;
     const osscir_ctx* h = s->ctx;
+    if (s->failed) {
+        cudaStreamSynchronize(s->stream);
+        t->status = OSSCIR_E_CUDA;
+        t->t_done = clk::now();
+        t->done = true;
+        s->running = nullptr;
+        --running;
+        return;
+    }
     t->maps.assign(s->h_maps, s->h_maps + (size_t)h->P * 4);
     t->dtpl = *s->h_dtpl;
     float ms = 0.f;
@@ -210,39 +267,56 @@ void osscir_server::finish(Slot* s) {
 
 void osscir_server::run() {
     cudaSetDevice(device);
-    std::unique_lock<std::mutex> lock(mu);
+    std::vector<Slot*> started;
     while (true) {
-        // completions
+        started.clear();
+        {
+            std::unique_lock<std::mutex> lock(mu);
+            if (stop && running == 0) break;
+            // admissions, first come first served, while a slot and the memory budget allow
+            while (!stop && !queue.empty() && running < max_slots) {
+                Ticket* t = queue.front();
+                Slot* s = acquire(t);
+                if (!s) break;   // wait for memory
+                queue.pop_front();
+                if (s == reinterpret_cast<Slot*>(-1)) {
+                    t->t_start = t->t_done = clk::now();
+                    t->done = true;
+                    cv_done.notify_all();
+                    continue;
+                }
+                s->running = t;
+                s->last_used = ++clock;
+                t->t_start = clk::now();
+                ++running;
+                started.push_back(s);
+            }
+        }
+        // CUDA work without the lock: the worker thread alone touches the slots' streams
+        bool acted = !started.empty();
+        for (Slot* s : started)
+            if (!begin(s)) s->failed = true;
+        std::vector<Slot*> done;
         for (Slot* s : slots) {
             if (!s->running) continue;
-            const cudaError_t q = cudaEventQuery(s->ev1);
-            if (q == cudaErrorNotReady) continue;
-            if (q != cudaSuccess) s->running->status = OSSCIR_E_CUDA;
-            finish(s);
+            if (advance(s)) acted = true;
+            if (s->tail) {
+                const cudaError_t q = cudaEventQuery(s->ev1);
+                if (q == cudaErrorNotReady) continue;
+                if (q != cudaSuccess) s->failed = true;
+                done.push_back(s);
+            }
+        }
+        std::unique_lock<std::mutex> lock(mu);
+        for (Slot* s : done) finish(s);
+        if (!done.empty()) {
             cv_done.notify_all();
+            acted = true;
         }
-        if (stop && running == 0) break;
-        // admissions, first come first served
-        while (!stop && !queue.empty() && running < max_slots) {
-            Ticket* t = queue.front();
-            Slot* s = acquire(t);
-            if (!s) break;   // wait for memory
-            queue.pop_front();
-            if (s == reinterpret_cast<Slot*>(-1)) {
-                t->t_start = t->t_done = clk::now();
-                t->done = true;
-                cv_done.notify_all();
-                continue;
-            }
-            if (!start(s, t)) {
-                cudaStreamSynchronize(s->stream);
-                finish(s);
-                t->status = OSSCIR_E_CUDA;
-                cv_done.notify_all();
-            }
+        if (!acted) {
+            if (running > 0) cv_work.wait_for(lock, std::chrono::microseconds(20));
+            else if (!stop && queue.empty()) cv_work.wait(lock);
         }
-        if (running > 0) cv_work.wait_for(lock, std::chrono::microseconds(50));
-        else if (!stop) cv_work.wait(lock);
     }
 }
 
