@@ -42,8 +42,7 @@ SOLVE_ITERS = 500
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch from an ncu capture of the dominant kernel; valid only for the
 # kernel source it was taken on (see profiles/), otherwise reported as null.
-TRAFFIC = {"k_mocca_fwd": {"bytes_per_launch": 29245952 + 7680, "source_sha": "dcf24ce94ded3de2"},
-           "k_mocca_bp": {"bytes_per_launch": 16076288 + 256, "source_sha": "dcf24ce94ded3de2"}}
+TRAFFIC = {}
 
 
 def _source_sha() -> str:
@@ -218,7 +217,7 @@ def run_gpu(args):
         R.step(1)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    fwd_ms, bp_ms = [], []
+    kms = []
     _barrier(ws)
     torch.cuda.synchronize()
     with Clocks(local) as clk:
@@ -227,9 +226,7 @@ def run_gpu(args):
             ev[k][0].record(stream)
             R.step(1)
             ev[k][1].record(stream)
-            a, b = _lib.osscir_last_kernel_ms(R.handle)   # synchronises the stream
-            fwd_ms.append(a)
-            bp_ms.append(b)
+            kms.append(_lib.osscir_last_kernel_ms(R.handle))   # synchronises the stream
         torch.cuda.synchronize()
     _barrier(ws)
     step_ms = [s.elapsed_time(e) for s, e in ev]
@@ -252,14 +249,16 @@ def run_gpu(args):
 
     if rank != 0:
         return 0
-    fwd_mean = statistics.mean(fwd_ms)
-    bp_mean = statistics.mean(bp_ms)
     L, nE = w.geom.n_rays, w.spectra.n_energies
+    mean = [statistics.mean(k[i] for k in kms) for i in range(3)]
     kern = {
+        # k_mocca_proj: 3 FMA per footprint pair (three materials)
+        "k_mocca_proj": {"ms": mean[0], "flop": 6.0 * nnz},
+        # k_mocca_ray: 29 FMA per (ray, energy): p_i (3), D_w (4), alpha numerators (12),
+        # beta_i (4) and sum_i beta_i mu_i mu_i^T (6); the FP64 per-ray algebra is not counted
+        "k_mocca_ray": {"ms": mean[1], "flop": 58.0 * L * nE},
         # k_mocca_bp: 9 FMA per footprint pair (K^T y' and the 6-channel block SPC)
-        "k_mocca_bp": {"ms": bp_mean, "flop": 18.0 * nnz},
-        # k_mocca_fwd: 3 FMA per footprint pair + 43 FMA per (ray, energy) of the spectral sums
-        "k_mocca_fwd": {"ms": fwd_mean, "flop": 6.0 * nnz + 86.0 * L * nE},
+        "k_mocca_bp": {"ms": mean[2], "flop": 18.0 * nnz},
     }
     dom = max(kern, key=lambda k: kern[k]["ms"])
     achieved = kern[dom]["flop"] / (kern[dom]["ms"] * 1e-3) / 1e12
@@ -278,7 +277,7 @@ def run_gpu(args):
                    "lambda": LAMBDA, "l2": "flushed between steps (256 MB write)",
                    "parallelism": "independent solves per GPU" if ws > 1 else "single solve"},
         "recon_per_s": value / SOLVE_ITERS,
-        "kernel_ms": {"k_mocca_fwd": fwd_mean, "k_mocca_bp": bp_mean},
+        "kernel_ms": {k: v["ms"] for k, v in kern.items()},
         "footprint_pairs": nnz,
         "intersections_per_s": 2.0 * nnz / (total_s / args.steps) * ws,
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
@@ -292,7 +291,7 @@ def run_gpu(args):
         "plain_recon_per_s": e2e_rate / SOLVE_ITERS,
         "served": served,
         "clocks": clk.summary(),
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 4 * args.steps,
         "dtpl_last": d_last,
         "maps_finite": finite,
     }

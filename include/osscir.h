@@ -140,11 +140,12 @@ osscir_status osscir_mocca_step(osscir_t h, int n_iters, void *stream);
 osscir_status osscir_reconstruct(osscir_t h, const float *c_host, int n_iters, float *maps_out_host,
                                  void *stream);
 
-/* Device time of the last MOCCA iteration's two main kernels, measured with
- * CUDA events recorded inside the iteration's graph: fwd_ms for the
- * ray-driven forward/spectral/dual kernel, bp_ms for the pixel-driven
- * back-projection/primal kernel (host floats).  Synchronises the stream. */
-osscir_status osscir_last_kernel_ms(osscir_t h, float *fwd_ms, float *bp_ms, void *stream);
+/* Device time of the last MOCCA iteration's three main kernels, measured with
+ * CUDA events recorded inside the iteration's graph (host float[3]): ms[0]
+ * the ray-driven forward projection, ms[1] the per-ray spectral model,
+ * curvature and dual step, ms[2] the pixel-driven back-projection, block
+ * step-preconditioner and primal step.  Synchronises the stream. */
+osscir_status osscir_last_kernel_ms(osscir_t h, float *ms, void *stream);
 
 /* Copy the current material maps x_n to x_out: device float[P][4]. */
 osscir_status osscir_get_maps(osscir_t h, float *x_out, void *stream);

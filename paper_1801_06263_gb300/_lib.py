@@ -100,7 +100,7 @@ def load(build_if_missing: bool = True):
         "osscir_footprint_rays": ([vp, ct.c_int, ct.c_int, ct.c_int, vp, vp, vp, vp], ct.c_int),
         "osscir_footprint_pixels": ([vp, ct.c_int, ct.c_int, ct.c_int, vp, vp, vp, vp], ct.c_int),
         "osscir_reconstruct": ([vp, vp, ct.c_int, vp, vp], ct.c_int),
-        "osscir_last_kernel_ms": ([vp, ct.POINTER(ct.c_float), ct.POINTER(ct.c_float), vp], ct.c_int),
+        "osscir_last_kernel_ms": ([vp, ct.POINTER(ct.c_float), vp], ct.c_int),
         "osscir_dtpl_counts_static": ([vp, vp, ct.c_int, vp, vp], ct.c_int),
         "osscir_server_create": ([ct.c_size_t, ct.c_int, ct.POINTER(ct.c_void_p)], ct.c_int),
         "osscir_server_destroy": ([vp], ct.c_int),
@@ -249,10 +249,10 @@ def osscir_reconstruct(h, c_host, n_iters, maps_out_host, stream=None):
 
 
 def osscir_last_kernel_ms(h, stream=None):
-    a, b = ct.c_float(), ct.c_float()
-    _check("osscir_last_kernel_ms", load().osscir_last_kernel_ms(ct.c_void_p(h), ct.byref(a), ct.byref(b),
-                                                                 _stream(stream)))
-    return a.value, b.value
+    """(projection, per-ray, back-projection) device ms of the last iteration."""
+    ms = (ct.c_float * 3)()
+    _check("osscir_last_kernel_ms", load().osscir_last_kernel_ms(ct.c_void_p(h), ms, _stream(stream)))
+    return tuple(ms)
 
 
 def osscir_dtpl_counts_static(chat, c, out, stream=None):

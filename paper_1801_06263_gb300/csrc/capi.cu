@@ -46,7 +46,7 @@ void free_ctx(osscir_ctx* h) {
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
     void* ptrs[] = {h->rec, h->r64, h->views, h->chord, h->exc_off, h->exc_ent, h->s4, h->N4, h->mu,
-                    h->c, h->y, h->x, h->xbar, h->dtpl_part, h->dtpl_out};
+                    h->g, h->c, h->y, h->x, h->xbar, h->dtpl_part, h->dtpl_out};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -137,6 +137,7 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     CK(dalloc(&h->s4, (size_t)nE * g->n_bins));
     CK(dalloc(&h->N4, g->n_bins));
     CK(dalloc(&h->mu, 3 * nE));
+    CK(dalloc(&h->g, L));
     CK(dalloc(&h->c, L));
     CK(dalloc(&h->y, L));
     CK(dalloc(&h->x, P));
@@ -190,13 +191,17 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
 cudaError_t enqueue_iteration(osscir_ctx* h, cudaStream_t st) {
     cudaError_t e = cudaEventRecordWithFlags(h->ev[0], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
-    e = launch_mocca_fwd(h->gc, h->exc(), h->rec, h->spec(), h->params, h->solve(), st);
+    e = launch_mocca_proj(h->gc, h->exc(), h->rec, h->solve(), st);
     if (e != cudaSuccess) return e;
     e = cudaEventRecordWithFlags(h->ev[1], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
-    e = launch_mocca_bp(h->gc, h->exc(), h->rec, h->views, h->params, h->solve(), st);
+    e = launch_mocca_ray(h->gc, h->rec, h->spec(), h->params, h->solve(), st);
     if (e != cudaSuccess) return e;
     e = cudaEventRecordWithFlags(h->ev[2], st, cudaEventRecordExternal);
+    if (e != cudaSuccess) return e;
+    e = launch_mocca_bp(h->gc, h->exc(), h->rec, h->views, h->params, h->solve(), st);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
     return launch_dtpl_reduce(h->dtpl_part, h->n_part, h->dtpl_out + 1, st);
 }
@@ -342,12 +347,11 @@ osscir_status osscir_reconstruct(osscir_t h, const float* c_host, int n_iters, f
     return OSSCIR_OK;
 }
 
-osscir_status osscir_last_kernel_ms(osscir_t h, float* fwd_ms, float* bp_ms, void* stream) {
-    if (!h || !fwd_ms || !bp_ms) return OSSCIR_E_INVALID;
+osscir_status osscir_last_kernel_ms(osscir_t h, float* ms, void* stream) {
+    if (!h || !ms) return OSSCIR_E_INVALID;
     if (!h->gexec) return OSSCIR_E_INVALID;
     CK(cudaStreamSynchronize(as_stream(stream)));
-    CK(cudaEventElapsedTime(fwd_ms, h->ev[0], h->ev[1]));
-    CK(cudaEventElapsedTime(bp_ms, h->ev[1], h->ev[2]));
+    for (int k = 0; k < 3; ++k) CK(cudaEventElapsedTime(ms + k, h->ev[k], h->ev[k + 1]));
     return OSSCIR_OK;
 }
 

@@ -1,8 +1,9 @@
 // Per-iteration kernels of MOCCA with the m-block-diagonal SPC (Sec. 2) and the
 // plain projectors behind osscir_forward / osscir_backproject / osscir_simulate.
 //
-// One iteration is two fused launches (plus a tiny deterministic reduction):
-//   k_mocca_fwd (ray-driven):   g = X xbar for the three maps, the counts model
+// One iteration is three launches (plus a tiny deterministic reduction):
+//   k_mocca_proj (ray-driven):  g = X xbar for the three maps;
+//   k_mocca_ray (per ray):      the counts model
 //       of Eq. (finalModel) summed over energies (compensated), D_TPL of
 //       Eq. (DTPL), alpha_w = sum_i A_wi mu_i (K = alpha X, Eq. aeq), the per-ray
 //       Hessian of Sec. 2 in g with its negative eigenvalues removed (FP64),
@@ -91,6 +92,18 @@ __device__ __forceinline__ void sexp3(float x, float& e0, float& e1, float& e2) 
         e1 = 1.0f;
         e2 = 0.0f;
     }
+}
+
+// Half of a ray record (32 bytes, 32-byte aligned) in one 256-bit load.
+struct RecHalf {
+    float4 a, b;
+};
+__device__ __forceinline__ RecHalf ldg_half(const float4* p) {
+    RecHalf r;
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(r.a.x), "=f"(r.a.y), "=f"(r.a.z), "=f"(r.a.w), "=f"(r.b.x), "=f"(r.b.y), "=f"(r.b.z), "=f"(r.b.w)
+        : "l"(p));
+    return r;
 }
 
 template <class Visit>
@@ -333,12 +346,15 @@ __device__ __forceinline__ double sym3(const double a[6], int i, int j) {
 }
 
 // Dual step of one ray that meets the image (see the file header).
-//   al: window-effective attenuations alpha (FP32), sig: Sigma (FP32),
+//   al: window-effective attenuations alpha (FP32), sinv: Sigma^-1 (FP32),
 //   cw: counts, rw: residuals, Bt: sum_i beta_i mu_i mu_i^T with
 //   beta_i = softexp''_i sum_w r_w s_wi / D_w (FP32, packed), y: dual.
-// The Hessian, its clip, G = (alpha^T alpha)^-1 alpha^T, W = G^T H+ G and the
-// Cholesky solve of (W + Sigma) u = y - r are FP64.  Returns y' in yo.
-__device__ void ray_dual(const float al[4][3], const float sig[4], const double cw[4], const double rw[4],
+// With G = (alpha^T alpha)^-1 alpha^T and W = G^T H+ G, the prox
+//   y' = y - Sigma (W + Sigma)^-1 (y - r)
+// equals r + G^T z with (I + H+ F) z = H+ G Sigma^-1 (y - r), F = G Sigma^-1 G^T
+// (push-through identity: the rank-3 update is solved in the 3-dim space of g).
+// The Hessian, its clip and this 3x3 algebra are FP64.  Returns y' in yo.
+__device__ void ray_dual(const float al[4][3], const float sinv[4], const double cw[4], const double rw[4],
                          const float Bt[6], const double y[4], double yo[4]) {
     double a[4][3];
 #pragma unroll
@@ -347,12 +363,17 @@ __device__ void ray_dual(const float al[4][3], const float sig[4], const double 
         for (int m = 0; m < 3; ++m) a[w][m] = (double)al[w][m];
     double H[6];
     {
+        double ca[4][3];   // c_w alpha_w
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) ca[w][m] = cw[w] * a[w][m];
         const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
 #pragma unroll
         for (int e = 0; e < 6; ++e) {
             double acc = -(double)Bt[e];
 #pragma unroll
-            for (int w = 0; w < 4; ++w) acc += cw[w] * a[w][ij[e][0]] * a[w][ij[e][1]];
+            for (int w = 0; w < 4; ++w) acc += ca[w][ij[e][0]] * a[w][ij[e][1]];
             H[e] = acc;
         }
     }
@@ -364,73 +385,87 @@ __device__ void ray_dual(const float al[4][3], const float sig[4], const double 
         A[3] += a[w][1] * a[w][1]; A[4] += a[w][1] * a[w][2]; A[5] += a[w][2] * a[w][2];
     }
     double Ai[6];
-    double M[10];   // packed upper triangle of W + Sigma: 00 01 02 03 11 12 13 22 23 33
-    if (inv_sym3(A, Ai)) {
-        double G[3][4], HG[3][4];
+    if (!inv_sym3(A, Ai)) {   // degenerate alpha: no curvature term, y' = r
 #pragma unroll
-        for (int m = 0; m < 3; ++m)
-#pragma unroll
-            for (int w = 0; w < 4; ++w)
-                G[m][w] = sym3(Ai, m, 0) * a[w][0] + sym3(Ai, m, 1) * a[w][1] + sym3(Ai, m, 2) * a[w][2];
-#pragma unroll
-        for (int m = 0; m < 3; ++m)
-#pragma unroll
-            for (int w = 0; w < 4; ++w)
-                HG[m][w] = sym3(H, m, 0) * G[0][w] + sym3(H, m, 1) * G[1][w] + sym3(H, m, 2) * G[2][w];
-        int t = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = i; j < 4; ++j) M[t++] = G[0][i] * HG[0][j] + G[1][i] * HG[1][j] + G[2][i] * HG[2][j];
-    } else {
-#pragma unroll
-        for (int t = 0; t < 10; ++t) M[t] = 0.0;
+        for (int w = 0; w < 4; ++w) yo[w] = rw[w];
+        return;
     }
-    M[0] += (double)sig[0];
-    M[4] += (double)sig[1];
-    M[7] += (double)sig[2];
-    M[9] += (double)sig[3];
-    // W + Sigma = L D L^T (SPD: Sigma > 0, W >= 0; unit lower L), then L D L^T u = y - r
-    const double d0 = M[0], i0 = 1.0 / d0;
-    const double l10 = M[1] * i0, l20 = M[2] * i0, l30 = M[3] * i0;
-    const double d1 = fmax(M[4] - l10 * l10 * d0, 1e-300 * d0), i1 = 1.0 / d1;
-    const double l21 = (M[5] - l20 * l10 * d0) * i1, l31 = (M[6] - l30 * l10 * d0) * i1;
-    const double d2 = fmax(M[7] - l20 * l20 * d0 - l21 * l21 * d1, 1e-300 * d0), i2 = 1.0 / d2;
-    const double l32 = (M[8] - l30 * l20 * d0 - l31 * l21 * d1) * i2;
-    const double d3 = fmax(M[9] - l30 * l30 * d0 - l31 * l31 * d1 - l32 * l32 * d2, 1e-300 * d0), i3 = 1.0 / d3;
-    const double z0 = y[0] - rw[0];
-    const double z1 = y[1] - rw[1] - l10 * z0;
-    const double z2 = y[2] - rw[2] - l20 * z0 - l21 * z1;
-    const double z3 = y[3] - rw[3] - l30 * z0 - l31 * z1 - l32 * z2;
-    const double u3 = z3 * i3;
-    const double u2 = z2 * i2 - l32 * u3;
-    const double u1 = z1 * i1 - l21 * u2 - l31 * u3;
-    const double u0 = z0 * i0 - l10 * u1 - l20 * u2 - l30 * u3;
-    yo[0] = y[0] - (double)sig[0] * u0;
-    yo[1] = y[1] - (double)sig[1] * u1;
-    yo[2] = y[2] - (double)sig[2] * u2;
-    yo[3] = y[3] - (double)sig[3] * u3;
+    double G[3][4], Gs[3][4];
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            G[m][w] = sym3(Ai, m, 0) * a[w][0] + sym3(Ai, m, 1) * a[w][1] + sym3(Ai, m, 2) * a[w][2];
+            Gs[m][w] = G[m][w] * (double)sinv[w];
+        }
+    double d[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) d[w] = y[w] - rw[w];
+    double F[6], phi[3];
+    {
+        const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+            const int m = ij[e][0], n = ij[e][1];
+            F[e] = Gs[m][0] * G[n][0] + Gs[m][1] * G[n][1] + Gs[m][2] * G[n][2] + Gs[m][3] * G[n][3];
+        }
+#pragma unroll
+        for (int m = 0; m < 3; ++m) phi[m] = Gs[m][0] * d[0] + Gs[m][1] * d[1] + Gs[m][2] * d[2] + Gs[m][3] * d[3];
+    }
+    // Mx = I + H+ F (3 x 3), rhs = H+ phi
+    double Mx[3][3], rhs[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            Mx[i][j] = (i == j ? 1.0 : 0.0) + sym3(H, i, 0) * sym3(F, 0, j) + sym3(H, i, 1) * sym3(F, 1, j) +
+                       sym3(H, i, 2) * sym3(F, 2, j);
+        rhs[i] = sym3(H, i, 0) * phi[0] + sym3(H, i, 1) * phi[1] + sym3(H, i, 2) * phi[2];
+    }
+    // z = Mx^-1 rhs (adjugate; the eigenvalues of Mx are >= 1)
+    const double c00 = Mx[1][1] * Mx[2][2] - Mx[1][2] * Mx[2][1];
+    const double c01 = Mx[1][2] * Mx[2][0] - Mx[1][0] * Mx[2][2];
+    const double c02 = Mx[1][0] * Mx[2][1] - Mx[1][1] * Mx[2][0];
+    const double idet = 1.0 / (Mx[0][0] * c00 + Mx[0][1] * c01 + Mx[0][2] * c02);
+    const double z0 = idet * (c00 * rhs[0] + (Mx[0][2] * Mx[2][1] - Mx[0][1] * Mx[2][2]) * rhs[1] +
+                              (Mx[0][1] * Mx[1][2] - Mx[0][2] * Mx[1][1]) * rhs[2]);
+    const double z1 = idet * (c01 * rhs[0] + (Mx[0][0] * Mx[2][2] - Mx[0][2] * Mx[2][0]) * rhs[1] +
+                              (Mx[0][2] * Mx[1][0] - Mx[0][0] * Mx[1][2]) * rhs[2]);
+    const double z2 = idet * (c02 * rhs[0] + (Mx[0][1] * Mx[2][0] - Mx[0][0] * Mx[2][1]) * rhs[1] +
+                              (Mx[0][0] * Mx[1][1] - Mx[0][1] * Mx[1][0]) * rhs[2]);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) yo[w] = rw[w] + G[0][w] * z0 + G[1][w] * z1 + G[2][w] * z2;
 }
 
 // ------------------------------------------------------------------ fused MOCCA kernels
 
-__global__ void __launch_bounds__(kFwdThreads, 5) k_mocca_fwd(GeomC C, ExcTable E, RayRec* rec, SpecD S,
-                                                              StepParams P, SolveD D) {
+// a1: line integrals of the three maps at the expansion point xbar.
+__global__ void __launch_bounds__(kFwdThreads) k_mocca_proj(GeomC C, ExcTable E, const RayRec* rec, SolveD D) {
+    const int l = ray_of_thread(C);
+    if (l < 0) return;
+    const float4 r0 = rec[l].r0, r1 = rec[l].r1;
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) {
+        const float4 v = __ldg(D.xbar + k);
+        g0 = fmaf(w, v.x, g0);
+        g1 = fmaf(w, v.y, g1);
+        g2 = fmaf(w, v.z, g2);
+    });
+    D.g[l] = make_float4(g0, g1, g2, 0.f);
+}
+
+// a2-a5 and the per-ray half of a8: spectral model, curvature, dual step.
+__global__ void __launch_bounds__(kFwdThreads, 5) k_mocca_ray(GeomC C, RayRec* rec, SpecD S, StepParams P,
+                                                              SolveD D) {
     __shared__ float sm[kSmemStride * kMaxEnergies];
     load_mu_smem(S, sm);
     __syncthreads();
     const int l = ray_of_thread(C);
     double dsum = 0.0;
     if (l >= 0) {
-        const float4 r0 = rec[l].r0, r1 = rec[l].r1;
-        // a1: line integrals of the three maps at the expansion point xbar
-        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-        ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) {
-            const float4 v = __ldg(D.xbar + k);
-            g0 = fmaf(w, v.x, g0);
-            g1 = fmaf(w, v.y, g1);
-            g2 = fmaf(w, v.z, g2);
-        });
+        const float4 r1 = rec[l].r1;
+        const float4 gg = D.g[l];
+        const float g0 = gg.x, g1 = gg.y, g2 = gg.z;
         // a2/a3, first pass over energies: D_w (compensated) and alpha_w numerators
         const int b = l % C.n_bins, nb = C.n_bins, nE = S.n_energies;
         float Ds[4] = {0.f, 0.f, 0.f, 0.f}, Dc[4] = {0.f, 0.f, 0.f, 0.f}, An[4][3];
@@ -500,11 +535,11 @@ __global__ void __launch_bounds__(kFwdThreads, 5) k_mocca_fwd(GeomC C, ExcTable 
                 Bt[4] = fmaf(beta, qb.w, Bt[4]);
                 Bt[5] = fmaf(beta, qc.x, Bt[5]);
             }
-            // a5: m-block SPC dual step length Sigma_w = 1 / (lambda |alpha_w| (X 1)_l)
-            float sig[4];
+            // a5: m-block SPC dual step matrix (Sigma^-1)_w = lambda |alpha_w| (X 1)_l
+            float sinv[4];
 #pragma unroll
-            for (int w = 0; w < 4; ++w) sig[w] = 1.0f / (P.lambda * nw[w] * X1);
-            ray_dual(al, sig, cw, rw, Bt, y, yo);
+            for (int w = 0; w < 4; ++w) sinv[w] = P.lambda * nw[w] * X1;
+            ray_dual(al, sinv, cw, rw, Bt, y, yo);
         }
         const float yf[4] = {(float)yo[0], (float)yo[1], (float)yo[2], (float)yo[3]};
         D.y[l] = make_float4(yf[0], yf[1], yf[2], yf[3]);
@@ -607,22 +642,39 @@ __global__ void __launch_bounds__(kBpMaxThreads) k_mocca_bp(GeomC C, ExcTable E,
         for (int v = v0; v < v1; ++v) {
             int blo, bhi;
             pixel_bin_range(C, views[v], ix, iy, blo, bhi);
-            for (int b = blo; b <= bhi; ++b) {
+            // two candidate rays per step: both records' first halves are loaded before either is used
+            for (int b = blo; b <= bhi; b += 2) {
                 const int l = v * C.n_bins + b;
-                const float4 r0 = __ldg(&rec[l].r0);
-                const float4 r1 = __ldg(&rec[l].r1);
-                const float w = x_weight(r0, r1.x, r1.y, C.grid, E, l, ix, iy);
-                if (w == 0.0f) continue;
-                const float4 r2 = __ldg(&rec[l].r2), r3 = __ldg(&rec[l].r3);
-                acc[0] = fmaf(w, r1.z, acc[0]);
-                acc[1] = fmaf(w, r1.w, acc[1]);
-                acc[2] = fmaf(w, r2.x, acc[2]);
-                acc[3] = fmaf(w, r2.y, acc[3]);
-                acc[4] = fmaf(w, r2.z, acc[4]);
-                acc[5] = fmaf(w, r2.w, acc[5]);
-                acc[6] = fmaf(w, r3.x, acc[6]);
-                acc[7] = fmaf(w, r3.y, acc[7]);
-                acc[8] = fmaf(w, r3.z, acc[8]);
+                const bool two = b < bhi;
+                const RecHalf A = ldg_half(&rec[l].r0);
+                RecHalf B = A;
+                if (two) B = ldg_half(&rec[l + 1].r0);
+                const float wa = x_weight(A.a, A.b.x, A.b.y, C.grid, E, l, ix, iy);
+                const float wb = two ? x_weight(B.a, B.b.x, B.b.y, C.grid, E, l + 1, ix, iy) : 0.0f;
+                if (wa != 0.0f) {
+                    const RecHalf A2 = ldg_half(&rec[l].r2);
+                    acc[0] = fmaf(wa, A.b.z, acc[0]);
+                    acc[1] = fmaf(wa, A.b.w, acc[1]);
+                    acc[2] = fmaf(wa, A2.a.x, acc[2]);
+                    acc[3] = fmaf(wa, A2.a.y, acc[3]);
+                    acc[4] = fmaf(wa, A2.a.z, acc[4]);
+                    acc[5] = fmaf(wa, A2.a.w, acc[5]);
+                    acc[6] = fmaf(wa, A2.b.x, acc[6]);
+                    acc[7] = fmaf(wa, A2.b.y, acc[7]);
+                    acc[8] = fmaf(wa, A2.b.z, acc[8]);
+                }
+                if (wb != 0.0f) {
+                    const RecHalf B2 = ldg_half(&rec[l + 1].r2);
+                    acc[0] = fmaf(wb, B.b.z, acc[0]);
+                    acc[1] = fmaf(wb, B.b.w, acc[1]);
+                    acc[2] = fmaf(wb, B2.a.x, acc[2]);
+                    acc[3] = fmaf(wb, B2.a.y, acc[3]);
+                    acc[4] = fmaf(wb, B2.a.z, acc[4]);
+                    acc[5] = fmaf(wb, B2.a.w, acc[5]);
+                    acc[6] = fmaf(wb, B2.b.x, acc[6]);
+                    acc[7] = fmaf(wb, B2.b.y, acc[7]);
+                    acc[8] = fmaf(wb, B2.b.z, acc[8]);
+                }
             }
         }
     }
@@ -667,11 +719,22 @@ __global__ void __launch_bounds__(kBpMaxThreads) k_mocca_bp(GeomC C, ExcTable E,
     D.xbar[k] = make_float4(2.f * xn.x - x.x, 2.f * xn.y - x.y, 2.f * xn.z - x.z, 0.f);
 }
 
-__global__ void k_dtpl_reduce(const double* part, int n, double* out) {
-    __shared__ double red[256 / 32];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
-    const double t = block_sum(s, red);
+constexpr int kReduceThreads = 1024;
+
+// Fixed-order sum of the partials: four independent strided accumulators per
+// thread, then a block tree (deterministic for a given n).
+__global__ void __launch_bounds__(kReduceThreads) k_dtpl_reduce(const double* part, int n, double* out) {
+    __shared__ double red[kReduceThreads / 32];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = threadIdx.x;
+    for (; i + 3 * kReduceThreads < n; i += 4 * kReduceThreads) {
+        s0 += part[i];
+        s1 += part[i + kReduceThreads];
+        s2 += part[i + 2 * kReduceThreads];
+        s3 += part[i + 3 * kReduceThreads];
+    }
+    for (; i < n; i += kReduceThreads) s0 += part[i];
+    const double t = block_sum((s0 + s1) + (s2 + s3), red);
     if (threadIdx.x == 0) *out = t;
 }
 
@@ -698,9 +761,15 @@ cudaError_t launch_counts(const GeomC& C, const ExcTable& E, const RayRec* rec, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_mocca_fwd(const GeomC& C, const ExcTable& E, RayRec* rec, const SpecD& S, const StepParams& P,
-                             const SolveD& D, cudaStream_t st) {
-    k_mocca_fwd<<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, E, rec, S, P, D);
+cudaError_t launch_mocca_proj(const GeomC& C, const ExcTable& E, const RayRec* rec, const SolveD& D,
+                              cudaStream_t st) {
+    k_mocca_proj<<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, E, rec, D);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mocca_ray(const GeomC& C, RayRec* rec, const SpecD& S, const StepParams& P, const SolveD& D,
+                             cudaStream_t st) {
+    k_mocca_ray<<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, rec, S, P, D);
     return cudaGetLastError();
 }
 
@@ -714,7 +783,7 @@ cudaError_t launch_mocca_bp(const GeomC& C, const ExcTable& E, const RayRec* rec
 }
 
 cudaError_t launch_dtpl_reduce(const double* part, int n, double* out, cudaStream_t st) {
-    k_dtpl_reduce<<<1, 256, 0, st>>>(part, n, out);
+    k_dtpl_reduce<<<1, kReduceThreads, 0, st>>>(part, n, out);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ struct osscir_ctx {
     float4* N4 = nullptr;
     float* mu = nullptr;
     // solver state
+    float4* g = nullptr;
     float4* c = nullptr;
     float4* y = nullptr;
     float4* x = nullptr;
@@ -39,11 +40,11 @@ struct osscir_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // recorded around the kernels inside the graph
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // recorded around the kernels inside the graph
 
     osscir::ExcTable exc() const { return osscir::ExcTable{exc_off, exc_ent}; }
     osscir::SpecD spec() const { return osscir::SpecD{nE, s4, N4, mu}; }
-    osscir::SolveD solve() const { return osscir::SolveD{c, y, x, xbar, chord, dtpl_part}; }
+    osscir::SolveD solve() const { return osscir::SolveD{g, c, y, x, xbar, chord, dtpl_part}; }
 };
 
 namespace osscir {

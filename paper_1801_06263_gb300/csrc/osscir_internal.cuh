@@ -44,20 +44,23 @@ __device__ __forceinline__ float t_plane(float X, float b, float inv_d) {
     return __fmul_rn(__fsub_rn(X, b), inv_d);
 }
 
+// The error bound of a chord: that of the plane deciding each end (both on a tie).
+__device__ __forceinline__ float chord_bound(float txl, float txh, float tyl, float tyh, float ex, float ey) {
+    const float elo = txl > tyl ? ex : (tyl > txl ? ey : fmaxf(ex, ey));
+    const float ehi = txh < tyh ? ex : (tyh < txh ? ey : fmaxf(ex, ey));
+    return __fadd_rn(elo, ehi);
+}
+
 // The chord of a pixel from the ray parameters of its four planes: the ray is
 // inside the pixel for max(entry planes) < t < min(exit planes).  The planes of
 // each axis are ordered by the sign of the reciprocal direction (t is monotone
-// in the plane position), which equals fminf/fmaxf on these values.  The error
-// bound is the one of the plane that decides each end.
+// in the plane position), which equals fminf/fmaxf on these values.
 __device__ __forceinline__ void chord_from_planes(float tx0, float tx1, float ty0, float ty1, float idx, float idy,
                                                   float ex, float ey, float& w, float& eb) {
     const float txl = idx >= 0.0f ? tx0 : tx1, txh = idx >= 0.0f ? tx1 : tx0;
     const float tyl = idy >= 0.0f ? ty0 : ty1, tyh = idy >= 0.0f ? ty1 : ty0;
-    const float lo = fmaxf(txl, tyl), hi = fminf(txh, tyh);
-    w = __fsub_rn(hi, lo);
-    const float elo = txl > tyl ? ex : (tyl > txl ? ey : fmaxf(ex, ey));
-    const float ehi = txh < tyh ? ex : (tyh < txh ? ey : fmaxf(ex, ey));
-    eb = __fadd_rn(elo, ehi);
+    w = __fsub_rn(fminf(txh, tyh), fmaxf(txl, tyl));
+    eb = chord_bound(txl, txh, tyl, tyh, ex, ey);
 }
 
 // FP32 chord of pixel (ix, iy) on the ray and the error bound that applies to it.
@@ -83,14 +86,30 @@ __device__ __forceinline__ float exc_lookup(const ExcTable& E, int l, int k) {
     return 0.0f;
 }
 
+// Membership decision shared by both projectors: chord w > bound -> member with
+// weight w; w < -bound -> not a member; otherwise the FP64 table decides.  The
+// bound of a chord never exceeds 2 max(ex, ey), so that test settles most pairs
+// before the exact bound is formed; the outcome is the same either way.
+__device__ __forceinline__ float member_weight(float w, float txl, float txh, float tyl, float tyh, float ex,
+                                               float ey, const ExcTable& E, int l, int k) {
+    const float ebmax = 2.0f * fmaxf(ex, ey);
+    if (w > ebmax) return w;
+    if (w < -ebmax) return 0.0f;
+    const float eb = chord_bound(txl, txh, tyl, tyh, ex, ey);
+    if (w > eb) return w;
+    if (w < -eb) return 0.0f;
+    return exc_lookup(E, l, k);   // also reached by NaN (axis-parallel rays)
+}
+
 // X_{l,k}: the weight both projectors use.
 __device__ __forceinline__ float x_weight(const float4& r0, float ex, float ey, const GridF& G,
                                           const ExcTable& E, int l, int ix, int iy) {
-    float w, eb;
-    chord32(r0, ex, ey, G, ix, iy, w, eb);
-    if (w > eb) return w;
-    if (w < -eb) return 0.0f;
-    return exc_lookup(E, l, iy * G.n + ix);   // also reached by NaN (axis-parallel rays)
+    const float tx0 = t_plane(grid_plane(G, ix), r0.x, r0.z), tx1 = t_plane(grid_plane(G, ix + 1), r0.x, r0.z);
+    const float ty0 = t_plane(grid_plane(G, iy), r0.y, r0.w), ty1 = t_plane(grid_plane(G, iy + 1), r0.y, r0.w);
+    const float txl = r0.z >= 0.0f ? tx0 : tx1, txh = r0.z >= 0.0f ? tx1 : tx0;
+    const float tyl = r0.w >= 0.0f ? ty0 : ty1, tyh = r0.w >= 0.0f ? ty1 : ty0;
+    const float w = __fsub_rn(fminf(txh, tyh), fmaxf(txl, tyl));
+    return member_weight(w, txl, txh, tyl, tyh, ex, ey, E, l, iy * G.n + ix);
 }
 
 // float -> int with saturation (huge or infinite coordinates stay in range).
@@ -157,15 +176,85 @@ __device__ __forceinline__ void ray_chords(const float4& r0, float ex, float ey,
     else ray_chords_dir<false>(r0, ex, ey, G, margin, visit);
 }
 
-// X_{l,k} for every pixel of ray l with a nonzero weight: visit(k, w).
+// X_{l,k} for every pixel of ray l with a nonzero weight: visit(k, w).  The
+// same slab enumeration as ray_chords, specialised on the dominant axis and
+// the signs of the direction (so the planes need no ordering at run time) and
+// unrolled over the at most three cells a slab can contribute (|slope| <= 1 and
+// margin < h/2); every weight equals x_weight's bit for bit.
+template <bool ROWS, bool PX, bool PY, class Visit>
+__device__ __forceinline__ void ray_weights_dir(const float4& r0, float ex, float ey, const GridF& G, float margin,
+                                                const ExcTable& E, int l, Visit&& visit) {
+    const float bM = ROWS ? r0.y : r0.x, bm = ROWS ? r0.x : r0.y;
+    const float iM = ROWS ? r0.w : r0.z, im = ROWS ? r0.z : r0.w;
+    const float slope = iM / im;
+    const float xlo = G.x0, xhi = grid_plane(G, G.n);
+    int jlo = 0, jhi = G.n - 1;
+    if (slope != 0.0f) {
+        const float ya = bM + (xlo - margin - bm) / slope;
+        const float yb = bM + (xhi + margin - bm) / slope;
+        jlo = max(jlo, sat_floor((fminf(ya, yb) - G.x0) / G.h) - 1);
+        jhi = min(jhi, sat_floor((fmaxf(ya, yb) - G.x0) / G.h) + 1);
+    } else if (bm < xlo - margin || bm > xhi + margin) {
+        return;
+    }
+    const bool PM = ROWS ? PY : PX, Pm = ROWS ? PX : PY;   // sign of the major / minor reciprocal direction
+    const float inv_h = 1.0f / G.h;
+    const float c_lo = (-margin - G.x0) * inv_h, c_hi = (margin - G.x0) * inv_h;
+    float pM0 = grid_plane(G, jlo);
+    float tM0 = t_plane(pM0, bM, iM);
+    float m0 = fmaf(slope, pM0 - bM, bm);
+    for (int j = jlo; j <= jhi; ++j) {
+        const float pM1 = grid_plane(G, j + 1);
+        const float tM1 = t_plane(pM1, bM, iM);
+        const float m1 = fmaf(slope, pM1 - bM, bm);
+        const int ilo = max(__float2int_rd(fmaf(fminf(m0, m1), inv_h, c_lo)), 0);
+        const int ihi = min(__float2int_rd(fmaf(fmaxf(m0, m1), inv_h, c_hi)), G.n - 1);
+        const float tMl = PM ? tM0 : tM1, tMh = PM ? tM1 : tM0;
+        if (ilo <= ihi) {
+            float tm[4];
+            tm[0] = t_plane(grid_plane(G, ilo), bm, im);
+            tm[1] = t_plane(grid_plane(G, ilo + 1), bm, im);
+            tm[2] = t_plane(grid_plane(G, ilo + 2), bm, im);
+            tm[3] = t_plane(grid_plane(G, ilo + 3), bm, im);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int i = ilo + c;
+                if (i > ihi) break;
+                const float tml = Pm ? tm[c] : tm[c + 1], tmh = Pm ? tm[c + 1] : tm[c];
+                const float txl = ROWS ? tml : tMl, txh = ROWS ? tmh : tMh;
+                const float tyl = ROWS ? tMl : tml, tyh = ROWS ? tMh : tmh;
+                const float w = __fsub_rn(fminf(txh, tyh), fmaxf(txl, tyl));
+                const int k = ROWS ? j * G.n + i : i * G.n + j;
+                const float x = member_weight(w, txl, txh, tyl, tyh, ex, ey, E, l, k);
+                if (x != 0.0f) visit(k, x);
+            }
+        }
+        tM0 = tM1;
+        m0 = m1;
+    }
+}
+
 template <class Visit>
 __device__ __forceinline__ void ray_weights(const float4& r0, float ex, float ey, const GridF& G, float margin,
                                             const ExcTable& E, int l, Visit&& visit) {
-    ray_chords(r0, ex, ey, G, margin, [&](int ix, int iy, float w, float eb) {
-        if (w < -eb) return;
-        const float x = w > eb ? w : exc_lookup(E, l, iy * G.n + ix);   // also reached by NaN
-        if (x != 0.0f) visit(iy * G.n + ix, x);
-    });
+    const bool rows = fabsf(r0.w) <= fabsf(r0.z), px = r0.z >= 0.0f, py = r0.w >= 0.0f;
+    if (rows) {
+        if (px) {
+            if (py) ray_weights_dir<true, true, true>(r0, ex, ey, G, margin, E, l, visit);
+            else ray_weights_dir<true, true, false>(r0, ex, ey, G, margin, E, l, visit);
+        } else {
+            if (py) ray_weights_dir<true, false, true>(r0, ex, ey, G, margin, E, l, visit);
+            else ray_weights_dir<true, false, false>(r0, ex, ey, G, margin, E, l, visit);
+        }
+    } else {
+        if (px) {
+            if (py) ray_weights_dir<false, true, true>(r0, ex, ey, G, margin, E, l, visit);
+            else ray_weights_dir<false, true, false>(r0, ex, ey, G, margin, E, l, visit);
+        } else {
+            if (py) ray_weights_dir<false, false, true>(r0, ex, ey, G, margin, E, l, visit);
+            else ray_weights_dir<false, false, false>(r0, ex, ey, G, margin, E, l, visit);
+        }
+    }
 }
 
 // Per-view constants for the pixel-driven back-projection: the detector bin

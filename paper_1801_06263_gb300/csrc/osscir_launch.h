@@ -38,6 +38,7 @@ struct StepParams {
 
 // MOCCA per-solve device state.
 struct SolveD {
+    float4* g;          // [L] line integrals of the three maps at xbar
     const float4* c;    // [L] measured counts
     float4* y;          // [L] dual
     float4* x;          // [P] x_n
@@ -76,8 +77,10 @@ cudaError_t launch_backproject4(const GeomC& C, const ExcTable& E, const RayRec*
                                 const float4* rf, float4* img, cudaStream_t st);
 cudaError_t launch_counts(const GeomC& C, const ExcTable& E, const RayRec* rec, const SpecD& S, const float4* f,
                           float4* chat, const float4* c, double* dtpl_part, cudaStream_t st);
-cudaError_t launch_mocca_fwd(const GeomC& C, const ExcTable& E, RayRec* rec, const SpecD& S, const StepParams& P,
-                             const SolveD& D, cudaStream_t st);
+cudaError_t launch_mocca_proj(const GeomC& C, const ExcTable& E, const RayRec* rec, const SolveD& D,
+                              cudaStream_t st);
+cudaError_t launch_mocca_ray(const GeomC& C, RayRec* rec, const SpecD& S, const StepParams& P, const SolveD& D,
+                             cudaStream_t st);
 cudaError_t launch_mocca_bp(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
                             const StepParams& P, const SolveD& D, cudaStream_t st);
 cudaError_t launch_dtpl_reduce(const double* part, int n, double* out, cudaStream_t st);

@@ -93,16 +93,18 @@ def test_admission_respects_budget_and_slots(problems):
     from paper_1801_06263_gb300 import _lib as L
     g, sp, c = problems[0]
     g2, sp2, c2 = problems[1]
-    probe = L.osscir_server_create(8 << 30, 1)
-    try:
-        rc, _ = L.osscir_poll(probe, _submit(L, probe, g, sp, c, 1e-7, 1), -1)
-        assert rc == 0
-        one = L.osscir_server_info(probe)[2]
-    finally:
-        L.osscir_server_destroy(probe)
-    # a budget that holds one context of this size but not two: different
-    # configurations must run one after the other, the same one reuses its context
-    budget = int(1.5 * one)
+    sizes = []
+    for pb in problems[:2]:
+        probe = L.osscir_server_create(8 << 30, 1)
+        try:
+            rc, _ = L.osscir_poll(probe, _submit(L, probe, *pb, 1e-7, 1), -1)
+            assert rc == 0
+            sizes.append(L.osscir_server_info(probe)[2])
+        finally:
+            L.osscir_server_destroy(probe)
+    # a budget that holds a context of either configuration but not both: the two
+    # configurations must run one after the other, each reusing its cached context
+    budget = max(sizes) + min(sizes) // 2
     srv = L.osscir_server_create(budget, 4)
     try:
         ts = [_submit(L, srv, *(problems[i % 2]), 1e-7, 60) for i in range(4)]
