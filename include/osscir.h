@@ -80,12 +80,17 @@ typedef struct {
  * model = 1 uses zero curvature (a preconditioned gradient step).  use_box = 1
  * constrains every iterate to lo <= f <= hi per material (the convex constraint
  * set of the one-step framework, Sec. 1); 0 leaves f unconstrained (Sec. 2: the
- * softexp model avoids the need for constraints). */
+ * softexp model avoids the need for constraints).  spc = 0 selects the
+ * m-block-diagonal step-preconditioner of Sec. 2; spc = 1 the diagonal one of
+ * Pock and Chambolle that it replaces (Sigma_wl = (1/lambda) / sum_mk |K|,
+ * T_mk = lambda / sum_wl |K|, Sec. 2) — with a material basis orthogonalised
+ * over energy by the caller this is the mu-PC of Sec. 2. */
 typedef struct {
     double lambda;
     int model;
     int use_box;
     float lo[3], hi[3];
+    int spc;
 } osscir_params;
 
 /* Human-readable name of a status code (static string). */
@@ -94,7 +99,8 @@ const char *osscir_status_string(osscir_status s);
 /* Create a reconstruction context on the current CUDA device (Sec. 2, the data
  * model's fixed inputs: geometry X, spectra s and N, attenuation mu).
  *   geom, spectra, params: host structs, copied.
- *   mu: host float[3][n_energies], mu_{m,i} in 1/mm per unit of f (Eq. matdecomp), copied.
+ *   mu: host float[3][n_energies], mu_{m,i} in 1/mm per unit of f (Eq. matdecomp), finite
+ *       (a transformed basis such as mu-PC's may be negative), copied.
  *   out: receives the handle.
  * Builds the per-geometry ray tables and footprint tables on the device and
  * synchronises before returning.  Errors: OSSCIR_E_INVALID (geometry outside

@@ -78,10 +78,11 @@ osscir_status validate(const osscir_geometry* g, const osscir_spectra* sp, const
             if (!finite_pos(sp->N[(size_t)b * 4 + w])) return OSSCIR_E_INVALID;
         }
     }
-    for (int i = 0; i < 3 * nE; ++i)
-        if (!std::isfinite(mu[i]) || mu[i] < 0.f) return OSSCIR_E_INVALID;
+    for (int i = 0; i < 3 * nE; ++i)   // a transformed basis (mu-PC) may have negative curves
+        if (!std::isfinite(mu[i])) return OSSCIR_E_INVALID;
     if (!finite_pos(pa->lambda) || !(pa->lambda < 3.0e38)) return OSSCIR_E_INVALID;
     if (pa->model != 0 && pa->model != 1) return OSSCIR_E_INVALID;
+    if (pa->spc != 0 && pa->spc != 1) return OSSCIR_E_INVALID;
     if (pa->use_box)
         for (int m = 0; m < 3; ++m)
             if (!std::isfinite(pa->lo[m]) || !std::isfinite(pa->hi[m]) || !(pa->lo[m] <= pa->hi[m]))
@@ -121,6 +122,7 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     C.margin_bins = 0.01f;
     h->params.lambda = (float)pa->lambda;
     h->params.model = pa->model;
+    h->params.spc = pa->spc;
     h->params.use_box = pa->use_box;
     for (int m = 0; m < 3; ++m) {
         h->params.lo[m] = pa->lo[m];

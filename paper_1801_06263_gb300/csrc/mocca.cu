@@ -535,25 +535,35 @@ __global__ void __launch_bounds__(kFwdThreads, 5) k_mocca_ray(GeomC C, RayRec* r
                 Bt[4] = fmaf(beta, qb.w, Bt[4]);
                 Bt[5] = fmaf(beta, qc.x, Bt[5]);
             }
-            // a5: m-block SPC dual step matrix (Sigma^-1)_w = lambda |alpha_w| (X 1)_l
+            // a5: dual step matrix.  m-block SPC: (Sigma^-1)_w = lambda sum_k sqrt(sum_m K^2)
+            // = lambda |alpha_w| (X 1)_l;  diagonal SPC: lambda sum_mk |K| = lambda (sum_m |alpha_wm|) (X 1)_l
             float sinv[4];
 #pragma unroll
-            for (int w = 0; w < 4; ++w) sinv[w] = P.lambda * nw[w] * X1;
+            for (int w = 0; w < 4; ++w)
+                sinv[w] = P.lambda * X1 *
+                          (P.spc == 0 ? nw[w] : fabsf(al[w][0]) + fabsf(al[w][1]) + fabsf(al[w][2]));
             ray_dual(al, sinv, cw, rw, Bt, y, yo);
         }
         const float yf[4] = {(float)yo[0], (float)yo[1], (float)yo[2], (float)yo[3]};
         D.y[l] = make_float4(yf[0], yf[1], yf[2], yf[3]);
-        // b = alpha^T y',  S = sum_w alpha_w alpha_w^T / |alpha_w|
+        // b = alpha^T y';  the ray's share of T^-1: m-block SPC S = sum_w alpha_w alpha_w^T / |alpha_w|,
+        // diagonal SPC S = diag(sum_w |alpha_wm|)
         float bb[3] = {0.f, 0.f, 0.f}, Sm[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
-            const float inw = nw[w] > 0.f ? 1.0f / nw[w] : 0.f;
 #pragma unroll
             for (int m = 0; m < 3; ++m) bb[m] = fmaf(al[w][m], yf[w], bb[m]);
-            const float a0 = al[w][0] * inw, a1 = al[w][1] * inw, a2 = al[w][2] * inw;
-            Sm[0] = fmaf(a0, al[w][0], Sm[0]); Sm[1] = fmaf(a0, al[w][1], Sm[1]);
-            Sm[2] = fmaf(a0, al[w][2], Sm[2]); Sm[3] = fmaf(a1, al[w][1], Sm[3]);
-            Sm[4] = fmaf(a1, al[w][2], Sm[4]); Sm[5] = fmaf(a2, al[w][2], Sm[5]);
+            if (P.spc == 0) {
+                const float inw = nw[w] > 0.f ? 1.0f / nw[w] : 0.f;
+                const float a0 = al[w][0] * inw, a1 = al[w][1] * inw, a2 = al[w][2] * inw;
+                Sm[0] = fmaf(a0, al[w][0], Sm[0]); Sm[1] = fmaf(a0, al[w][1], Sm[1]);
+                Sm[2] = fmaf(a0, al[w][2], Sm[2]); Sm[3] = fmaf(a1, al[w][1], Sm[3]);
+                Sm[4] = fmaf(a1, al[w][2], Sm[4]); Sm[5] = fmaf(a2, al[w][2], Sm[5]);
+            } else {
+                Sm[0] += fabsf(al[w][0]);
+                Sm[3] += fabsf(al[w][1]);
+                Sm[5] += fabsf(al[w][2]);
+            }
         }
         rec[l].r1 = make_float4(r1.x, r1.y, bb[0], bb[1]);
         rec[l].r2 = make_float4(bb[2], Sm[0], Sm[1], Sm[2]);

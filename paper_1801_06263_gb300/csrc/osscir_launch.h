@@ -32,6 +32,7 @@ struct SpecD {
 struct StepParams {
     float lambda;
     int model;       // 0: eigen-clipped Hessian, 1: W = 0
+    int spc;         // 0: m-block-diagonal SPC, 1: diagonal SPC
     int use_box;
     float lo[3], hi[3];
 };

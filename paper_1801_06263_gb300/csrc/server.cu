@@ -36,7 +36,7 @@ struct Config {
 
     bool same(const Config& o) const {
         return std::memcmp(&geom, &o.geom, sizeof geom) == 0 && nE == o.nE && s == o.s && N == o.N && mu == o.mu &&
-               params.lambda == o.params.lambda && params.model == o.params.model &&
+               params.lambda == o.params.lambda && params.model == o.params.model && params.spc == o.params.spc &&
                params.use_box == o.params.use_box && std::memcmp(params.lo, o.params.lo, sizeof params.lo) == 0 &&
                std::memcmp(params.hi, o.params.hi, sizeof params.hi) == 0;
     }
@@ -52,6 +52,7 @@ struct Config {
         mix(mu.data(), mu.size() * sizeof(float));
         mix(&params.lambda, sizeof params.lambda);
         mix(&params.model, sizeof params.model);
+        mix(&params.spc, sizeof params.spc);
         return h;
     }
 };

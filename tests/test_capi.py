@@ -49,7 +49,7 @@ def _args():
     lambda g, sp: (g.__class__(**{**g.__dict__, "bin_mm": float("nan")}), sp),
     lambda g, sp: (g, inputs.Spectra(sp.energies, sp.s * 1.01, sp.N, sp.mu)),
     lambda g, sp: (g, inputs.Spectra(sp.energies, sp.s, -sp.N, sp.mu)),
-    lambda g, sp: (g, inputs.Spectra(sp.energies, sp.s, sp.N, -sp.mu)),
+    lambda g, sp: (g, inputs.Spectra(sp.energies, sp.s, sp.N, sp.mu * np.nan)),
 ])
 def test_create_rejects_invalid_inputs(lib, mutate):
     g, sp = mutate(*_args())
