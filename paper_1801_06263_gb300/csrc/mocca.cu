@@ -128,6 +128,31 @@ __device__ __forceinline__ void pixel_rays(const GeomC& C, const ExcTable& E, co
     }
 }
 
+// Line sums of the interleaved maps along one ray, summed in two levels: an FP32
+// partial over at most kFold pixels is folded into the running total.  The rounding
+// error then grows with kFold + n / kFold terms instead of n (about 700 pixels per
+// ray at 512 x 512), which keeps the counts model within 1e-5 relative even on the
+// most attenuated rays.
+constexpr int kFold = 16;
+struct LineSum {
+    float4 part = make_float4(0.f, 0.f, 0.f, 0.f), total = make_float4(0.f, 0.f, 0.f, 0.f);
+    int n = 0;
+    __device__ __forceinline__ void add(float w, const float4& v) {
+        part.x = fmaf(w, v.x, part.x);
+        part.y = fmaf(w, v.y, part.y);
+        part.z = fmaf(w, v.z, part.z);
+        part.w = fmaf(w, v.w, part.w);
+        if (++n == kFold) {
+            total.x += part.x, total.y += part.y, total.z += part.z, total.w += part.w;
+            part = make_float4(0.f, 0.f, 0.f, 0.f);
+            n = 0;
+        }
+    }
+    __device__ __forceinline__ float4 sum() const {
+        return make_float4(total.x + part.x, total.y + part.y, total.z + part.z, total.w + part.w);
+    }
+};
+
 // ------------------------------------------------------------------ plain projectors
 
 __global__ void __launch_bounds__(kFwdThreads) k_forward4(GeomC C, ExcTable E, const RayRec* rec, const float4* x,
@@ -135,15 +160,9 @@ __global__ void __launch_bounds__(kFwdThreads) k_forward4(GeomC C, ExcTable E, c
     const int l = ray_of_thread(C);
     if (l < 0) return;
     const float4 r0 = rec[l].r0, r1 = rec[l].r1;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) {
-        const float4 v = __ldg(x + k);
-        acc.x = fmaf(w, v.x, acc.x);
-        acc.y = fmaf(w, v.y, acc.y);
-        acc.z = fmaf(w, v.z, acc.z);
-        acc.w = fmaf(w, v.w, acc.w);
-    });
-    g[l] = acc;
+    LineSum acc;
+    ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) { acc.add(w, __ldg(x + k)); });
+    g[l] = acc.sum();
 }
 
 __global__ void k_backproject4(GeomC C, ExcTable E, const RayRec* rec, const ViewF* views, const float4* rf,
@@ -172,13 +191,10 @@ __global__ void __launch_bounds__(kFwdThreads) k_counts(GeomC C, ExcTable E, con
     double dsum = 0.0;
     if (l >= 0) {
         const float4 r0 = rec[l].r0, r1 = rec[l].r1;
-        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-        ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) {
-            const float4 v = __ldg(f + k);
-            g0 = fmaf(w, v.x, g0);
-            g1 = fmaf(w, v.y, g1);
-            g2 = fmaf(w, v.z, g2);
-        });
+        LineSum acc;
+        ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) { acc.add(w, __ldg(f + k)); });
+        const float4 gs = acc.sum();
+        const float g0 = gs.x, g1 = gs.y, g2 = gs.z;
         const int b = l % C.n_bins, nb = C.n_bins;
         float Ds[4] = {0.f, 0.f, 0.f, 0.f}, Dc[4] = {0.f, 0.f, 0.f, 0.f};
         for (int i = 0; i < S.n_energies; ++i) {
@@ -444,14 +460,10 @@ __global__ void __launch_bounds__(kFwdThreads) k_mocca_proj(GeomC C, ExcTable E,
     const int l = ray_of_thread(C);
     if (l < 0) return;
     const float4 r0 = rec[l].r0, r1 = rec[l].r1;
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) {
-        const float4 v = __ldg(D.xbar + k);
-        g0 = fmaf(w, v.x, g0);
-        g1 = fmaf(w, v.y, g1);
-        g2 = fmaf(w, v.z, g2);
-    });
-    D.g[l] = make_float4(g0, g1, g2, 0.f);
+    LineSum acc;
+    ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) { acc.add(w, __ldg(D.xbar + k)); });
+    const float4 gs = acc.sum();
+    D.g[l] = make_float4(gs.x, gs.y, gs.z, 0.f);
 }
 
 // a2-a5 and the per-ray half of a8: spectral model, curvature, dual step.
