@@ -40,9 +40,13 @@ LAMBDA = 10.0 ** -7.5   # tuned with the oracle: tests/golden/lambda_sweeps.json
 SOLVE_ITERS = 500
 # FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes per launch from an ncu capture of the dominant kernel; valid only for the
-# kernel source it was taken on (see profiles/), otherwise reported as null.
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch of each per-iteration kernel, from one
+# ncu --set full capture (cold cache), valid only for the mocca.cu it was taken on
+TRAFFIC = {
+    "k_mocca_proj": {"bytes_per_launch": 18913792, "source_sha": "d770a41425c31945"},
+    "k_mocca_ray": {"bytes_per_launch": 31374848 + 20480, "source_sha": "d770a41425c31945"},
+    "k_mocca_bp": {"bytes_per_launch": 16078080 + 512, "source_sha": "d770a41425c31945"},
+}
 
 
 def _source_sha() -> str:
