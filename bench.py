@@ -38,6 +38,15 @@ WORKLOAD_DESC = ("256x256 (0.5 mm), 512 views x 512 bins, 4 windows, 101 energie
                  "(PMMA/Al/Gd), ellipse phantom 4 Al + 6 Gd, Poisson 1e5 photons/ray")
 LAMBDA = 10.0 ** -7.5   # tuned with the oracle: tests/golden/lambda_sweeps.json
 SOLVE_ITERS = 500
+def _hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback (6.8 TB/s, earlier GB300 copy measurement)"
+
+
+HBM_PEAK_GBPS, HBM_PEAK_SOURCE = _hbm_peak()
 # FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of each per-iteration kernel, from one
@@ -250,6 +259,7 @@ def run_gpu(args):
     finite = bool(torch.isfinite(maps_host).all().item())
 
     served = run_served(args, w, R, chat, rank) if args.served > 0 else None
+    batched = run_batched(args, rank) if args.batch > 0 else None
 
     if rank != 0:
         return 0
@@ -294,6 +304,7 @@ def run_gpu(args):
                 "recon_per_s": e2e_rate / SOLVE_ITERS},
         "plain_recon_per_s": e2e_rate / SOLVE_ITERS,
         "served": served,
+        "batched": batched,
         "clocks": clk.summary(),
         "gpu_launches": 4 * args.steps,
         "dtpl_last": d_last,
@@ -302,6 +313,83 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
     R.close()
     return 0
+
+
+def run_batched(args, rank):
+    """64 independent reconstructions of uneven sizes (n in {128..512}, 90-720 views,
+    1e4-1e6 photons per ray): one MOCCA iteration of all of them per step, (a) each
+    solve's own iteration graph one after another (plain per-solve form), (b) the
+    batched kernels with the default configuration, (c) after autotuning.  Inputs
+    (maps, rays, tables, about 2 GB) exceed L2; nothing is flushed between steps."""
+    import numpy as np
+    import torch
+    from paper_1801_06263_gb300 import Batch, Reconstructor, _lib, inputs
+
+    ws = inputs.batch_workloads(args.batch)
+    recs = []
+    for i, w in enumerate(ws):
+        R = Reconstructor(w.geom, w.spectra, inputs.step_ratio(w.geom.n, w.photons_per_ray))
+        f4 = torch.zeros((w.geom.n_pixels, 4), dtype=torch.float32, device="cuda")
+        f4[:, :3] = torch.tensor(w.f_true, dtype=torch.float32, device="cuda")
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(w.noise_seed + 7919 * rank)
+        R.set_counts(torch.poisson(R.simulate(f4), generator=gen).contiguous())
+        recs.append(R)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    K = max(1, args.batch_steps)
+
+    def timed(step):
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K
+
+    def plain_step():
+        for R in recs:
+            R.step(1)
+
+    plain_ms = timed(plain_step)
+    B = Batch(recs)
+    default_ms = timed(lambda: B.step(1))
+    kms_default = _lib.osscir_batch_last_kernel_ms(B.handle)
+    B.close()
+    t0 = time.perf_counter()
+    B = Batch(recs, autotune=True)
+    tune_s = time.perf_counter() - t0
+    tuned_ms = timed(lambda: B.step(1))
+    kms_tuned = _lib.osscir_batch_last_kernel_ms(B.handle)
+    cfg = B.config
+    B.close()
+    finite = sum(1 for R in recs if np.isfinite(R.dtpl(1)))
+    P = sum(w.geom.n_pixels for w in ws)
+    L = sum(w.geom.n_rays for w in ws)
+    alg_bytes = 48.0 * P + 124.0 * L        # per iteration: x_n, x_{n-1} read, x_{n+1} written; per-ray fields
+    best_ms = min(default_ms, tuned_ms)
+    for R in recs:
+        R.close()
+    mix = {}
+    for w in ws:
+        mix[w.geom.n] = mix.get(w.geom.n, 0) + 1
+    return {
+        "solves": len(ws), "image_sizes": {str(k): v for k, v in sorted(mix.items())},
+        "views": [min(w.geom.n_views for w in ws), max(w.geom.n_views for w in ws)],
+        "pixels": P, "rays": L, "steps": K,
+        "plain_ms_per_iteration": plain_ms, "batched_ms_per_iteration": default_ms,
+        "tuned_ms_per_iteration": tuned_ms, "speedup_vs_plain": plain_ms / best_ms,
+        "solve_iterations_per_s": len(ws) * 1e3 / best_ms,
+        "kernel_ms_default": list(kms_default), "kernel_ms_tuned": list(kms_tuned),
+        "tuned_config": cfg, "autotune_s": tune_s, "finite_solves": finite,
+        "hbm": {"algorithmic_bytes_per_iteration": alg_bytes, "achieved_GBps": alg_bytes / (best_ms * 1e-3) / 1e9,
+                "peak_GBps": HBM_PEAK_GBPS, "frac": alg_bytes / (best_ms * 1e-3) / 1e9 / HBM_PEAK_GBPS,
+                "peak_source": HBM_PEAK_SOURCE},
+    }
 
 
 def run_served(args, w, R, chat, rank):
@@ -365,6 +453,8 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle iterations for the CPU baseline")
     ap.add_argument("--served", type=int, default=16, help="requests for the served measurement (0: skip)")
     ap.add_argument("--slots", type=int, default=4, help="server slots")
+    ap.add_argument("--batch", type=int, default=64, help="solves in the batched measurement (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=5, help="timed iterations of the batched measurement")
     ap.add_argument("--rate", type=float, default=1.5, help="Poisson request arrival rate, requests/s")
     args = ap.parse_args()
     if args.impl == "reference":

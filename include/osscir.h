@@ -180,6 +180,66 @@ osscir_status osscir_footprint_rays(osscir_t h, int l0, int n, int cap, int *cnt
 osscir_status osscir_footprint_pixels(osscir_t h, int k0, int n, int cap, int *cnt, int *idx, float *wt,
                                       void *stream);
 
+/* ------------------------------------------------------------------ batched form
+ * Many independent solves, each its own context (any geometry, spectra, mu,
+ * parameters; counts loaded with osscir_set_counts), advanced together: each
+ * MOCCA step of the batch is one launch per kernel over a work list of
+ * (solve, tile) items from all solves, captured once as one CUDA graph.  The
+ * MOCCA iteration of Sec. 2 is unchanged: every solve's iterates, D_TPL and
+ * iteration count are bit-identical to what osscir_mocca_step gives the same
+ * context alone, for any batch composition and any configuration below.
+ *
+ * The batch refers to its contexts; they must outlive it and must not be
+ * stepped on their own or destroyed while it exists.  Counts and state may be
+ * reloaded (osscir_set_counts, osscir_set_state) between batch steps, in
+ * stream order.  Per-solve results are read with the per-context calls
+ * (osscir_get_maps, osscir_get_state, osscir_dtpl(h, 1, ...)). */
+typedef struct osscir_batch *osscir_batch_t;
+
+/* Launch configuration of a batch (the paper has no counterpart: it sets how
+ * work is spread over the GPU, never what is computed).
+ *   proj_views:  views per projection block (1, 2, 4 or 8; 32 bins each);
+ *   proj_grid, ray_grid, bp_grid: 0 = one CTA per work item (flat grid),
+ *                > 0 = that many persistent CTAs striding over the items;
+ *   bp_tile_x:   width of the 64-pixel back-projection tile (4, 8, 16 or 32);
+ *   *_order:     work-list order of each kernel: 0 solve by solve, 1 the
+ *                solves with the costliest items first, 2 solves interleaved
+ *                item by item. */
+typedef struct {
+    int proj_views;
+    int proj_grid;
+    int proj_order;
+    int ray_grid;
+    int ray_order;
+    int bp_tile_x;
+    int bp_grid;
+    int bp_order;
+} osscir_batch_config;
+
+/* Build a batch over n (1 .. 4096) distinct contexts of the current device.
+ * autotune = 0 takes the default configuration; autotune = 1 times candidate
+ * configurations on the batch itself (a few launches each, restoring every
+ * solve's state afterwards) and keeps the fastest (synchronises).  Errors:
+ * OSSCIR_E_INVALID (NULL or repeated handles, contexts of another device),
+ * OSSCIR_E_NOMEM, OSSCIR_E_CUDA. */
+osscir_status osscir_batch_create(const osscir_t *solves, int n, int autotune, osscir_batch_t *out);
+
+/* Release the batch (not its contexts; synchronises).  NULL is a no-op. */
+osscir_status osscir_batch_destroy(osscir_batch_t b);
+
+/* Enqueue n_iters (>= 0) MOCCA iterations of every solve on stream. */
+osscir_status osscir_batch_step(osscir_batch_t b, int n_iters, void *stream);
+
+/* The configuration in use; set replaces it (validated as documented above,
+ * else OSSCIR_E_INVALID) and rebuilds the work lists and the graph (it
+ * synchronises the device first). */
+osscir_status osscir_batch_get_config(osscir_batch_t b, osscir_batch_config *out);
+osscir_status osscir_batch_set_config(osscir_batch_t b, const osscir_batch_config *cfg);
+
+/* Device time (ms) of the projection, ray and back-projection launches of
+ * the last batch iteration enqueued on stream (synchronises the stream). */
+osscir_status osscir_batch_last_kernel_ms(osscir_batch_t b, float ms[3], void *stream);
+
 /* ------------------------------------------------------------------ served form
  * A server owns a worker thread on the device that is current when it is
  * created.  Requests (complete reconstruction problems with host data) are

@@ -13,7 +13,7 @@ from ._lib import (OsscirError, load, osscir_backproject, osscir_create, osscir_
                    osscir_get_state, osscir_info, osscir_mocca_step, osscir_set_counts, osscir_set_state,
                    osscir_simulate)
 
-__all__ = ["inputs", "Reconstructor", "OsscirError", "load"]
+__all__ = ["inputs", "Reconstructor", "Batch", "OsscirError", "load"]
 
 
 class Reconstructor:
@@ -85,6 +85,43 @@ class Reconstructor:
     def close(self):
         if getattr(self, "handle", None):
             osscir_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several Reconstructors advanced together by the batched kernels (one launch
+    per kernel per iteration for all of them).  The Reconstructors must stay open
+    and must not be stepped on their own while the batch exists."""
+
+    def __init__(self, recons, autotune: bool = False):
+        from . import _lib
+        self._lib = _lib
+        self.recons = list(recons)
+        self.handle = _lib.osscir_batch_create([r.handle for r in self.recons], autotune)
+
+    def step(self, n_iters: int, stream=None):
+        self._lib.osscir_batch_step(self.handle, n_iters, stream)
+
+    @property
+    def config(self):
+        return self._lib.osscir_batch_get_config(self.handle)
+
+    @config.setter
+    def config(self, cfg):
+        self._lib.osscir_batch_set_config(self.handle, cfg)
+
+    def last_kernel_ms(self, stream=None):
+        return self._lib.osscir_batch_last_kernel_ms(self.handle, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.osscir_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -30,6 +30,8 @@ EXPORTS = (
     "osscir_get_state", "osscir_set_state", "osscir_dtpl", "osscir_footprint_rays",
     "osscir_footprint_pixels", "osscir_reconstruct", "osscir_last_kernel_ms", "osscir_dtpl_counts_static",
     "osscir_server_create", "osscir_server_destroy", "osscir_submit", "osscir_poll", "osscir_server_info",
+    "osscir_batch_create", "osscir_batch_destroy", "osscir_batch_step", "osscir_batch_get_config",
+    "osscir_batch_set_config", "osscir_batch_last_kernel_ms",
 )
 
 
@@ -57,6 +59,15 @@ class Params(ct.Structure):
 class Request(ct.Structure):
     _fields_ = [("geom", Geometry), ("spectra", Spectra), ("mu", ct.POINTER(ct.c_float)), ("params", Params),
                 ("counts", ct.POINTER(ct.c_float)), ("n_iters", ct.c_int)]
+
+
+class BatchConfig(ct.Structure):
+    _fields_ = [("proj_views", ct.c_int), ("proj_grid", ct.c_int), ("proj_order", ct.c_int),
+                ("ray_grid", ct.c_int), ("ray_order", ct.c_int), ("bp_tile_x", ct.c_int),
+                ("bp_grid", ct.c_int), ("bp_order", ct.c_int)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class Stats(ct.Structure):
@@ -107,6 +118,12 @@ def load(build_if_missing: bool = True):
         "osscir_submit": ([vp, ct.POINTER(Request), ct.POINTER(ct.c_uint64)], ct.c_int),
         "osscir_poll": ([vp, ct.c_uint64, ct.c_int, vp, ct.POINTER(Stats)], ct.c_int),
         "osscir_server_info": ([vp, ip, ip, ct.POINTER(ct.c_size_t)], ct.c_int),
+        "osscir_batch_create": ([ct.POINTER(ct.c_void_p), ct.c_int, ct.c_int, ct.POINTER(ct.c_void_p)], ct.c_int),
+        "osscir_batch_destroy": ([vp], ct.c_int),
+        "osscir_batch_step": ([vp, ct.c_int, vp], ct.c_int),
+        "osscir_batch_get_config": ([vp, ct.POINTER(BatchConfig)], ct.c_int),
+        "osscir_batch_set_config": ([vp, ct.POINTER(BatchConfig)], ct.c_int),
+        "osscir_batch_last_kernel_ms": ([vp, ct.POINTER(ct.c_float), vp], ct.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -303,3 +320,40 @@ def osscir_server_info(server):
     _check("osscir_server_info", load().osscir_server_info(ct.c_void_p(server), ct.byref(r), ct.byref(q),
                                                            ct.byref(b)))
     return r.value, q.value, b.value
+
+
+# --------------------------------------------------------------------------- batched form
+
+def osscir_batch_create(handles, autotune=False):
+    """handles: context handles (ints) of the current device.  Returns the batch handle."""
+    arr = (ct.c_void_p * len(handles))(*handles)
+    b = ct.c_void_p()
+    _check("osscir_batch_create", load().osscir_batch_create(arr, len(handles), int(bool(autotune)), ct.byref(b)))
+    return b.value
+
+
+def osscir_batch_destroy(batch):
+    _check("osscir_batch_destroy", load().osscir_batch_destroy(ct.c_void_p(batch)))
+
+
+def osscir_batch_step(batch, n_iters, stream=None):
+    _check("osscir_batch_step", load().osscir_batch_step(ct.c_void_p(batch), int(n_iters), _stream(stream)))
+
+
+def osscir_batch_get_config(batch):
+    c = BatchConfig()
+    _check("osscir_batch_get_config", load().osscir_batch_get_config(ct.c_void_p(batch), ct.byref(c)))
+    return c.as_dict()
+
+
+def osscir_batch_set_config(batch, cfg):
+    """cfg: dict with the osscir_batch_config fields."""
+    c = BatchConfig(**{k: int(v) for k, v in cfg.items()})
+    _check("osscir_batch_set_config", load().osscir_batch_set_config(ct.c_void_p(batch), ct.byref(c)))
+
+
+def osscir_batch_last_kernel_ms(batch, stream=None):
+    ms = (ct.c_float * 3)()
+    _check("osscir_batch_last_kernel_ms", load().osscir_batch_last_kernel_ms(ct.c_void_p(batch), ms,
+                                                                             _stream(stream)))
+    return tuple(ms)

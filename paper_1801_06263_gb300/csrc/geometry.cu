@@ -93,11 +93,13 @@ __global__ void k_exc_pass(GeomC C, GeomD G, const RayRec* rec, const Ray64* r64
     const Ray64 R = r64[l];
     int cnt = 0;
     const int base = count ? 0 : off[l];
+    const bool rows = ray_rows(r0);
+    // ray_chords enumerates (major, minor) in increasing order, so the keys come out sorted
     ray_chords(r0, ex, ey, C.grid, C.margin_mm, [&](int ix, int iy, float w, float eb) {
         if (w > eb || w < -eb) return;
         const double c64 = chord64(R, G, ix, iy);
         if (c64 > G.thr) {
-            if (!count) ent[base + cnt] = make_int2(iy * C.grid.n + ix, __float_as_int((float)c64));
+            if (!count) ent[base + cnt] = make_int2(exc_key(rows, C.grid.n, ix, iy), __float_as_int((float)c64));
             ++cnt;
         }
     });

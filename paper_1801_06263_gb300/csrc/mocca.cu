@@ -53,20 +53,28 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return s;
 }
 
-__device__ __forceinline__ void warp_partial(double v, double* part) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0)
-        part[(blockIdx.y * gridDim.x + blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)] = v;
+// Ray-driven kernels give each warp 32 consecutive detector bins (one per lane)
+// of one view, and a block vb consecutive views (one per warp), so the block's
+// slice of the energy-major spectral table is shared by its warps.  (bx, by)
+// is the block's tile: bins [32 bx, 32 bx + 32), views [vb by, vb by + vb).
+__device__ __forceinline__ int warp_view(int by, int vb) { return by * vb + (threadIdx.x >> 5); }
+
+__device__ __forceinline__ int ray_at(const GeomC& C, int bx, int by, int vb) {
+    const int b = bx * 32 + (threadIdx.x & 31);
+    const int v = warp_view(by, vb);
+    return (b < C.n_bins && v < C.n_views) ? v * C.n_bins + b : -1;
 }
 
-// Ray of this thread in the ray-driven kernels: a block covers 32 consecutive
-// detector bins (one per lane) of 4 consecutive views (one per warp), so the
-// block's slice of the energy-major spectral table is shared by its warps.
 __device__ __forceinline__ int ray_of_thread(const GeomC& C) {
-    const int b = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int v = blockIdx.y * (kFwdThreads / 32) + (threadIdx.x >> 5);
-    return (b < C.n_bins && v < C.n_views) ? v * C.n_bins + b : -1;
+    return ray_at(C, blockIdx.x, blockIdx.y, kFwdThreads / 32);
+}
+
+// The warp's D_TPL partial, stored at (view, 32-bin group) whatever the block
+// shape, so the fixed-order reduction sees the same sequence for any tiling.
+__device__ __forceinline__ void warp_partial(const GeomC& C, int bx, int v, double val, double* part) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) val += __shfl_down_sync(0xffffffffu, val, o);
+    if ((threadIdx.x & 31) == 0 && v < C.n_views) part[v * ((C.n_bins + 31) >> 5) + bx] = val;
 }
 
 __device__ __forceinline__ void load_mu_smem(const SpecD& S, float* sm) {
@@ -218,7 +226,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_counts(GeomC C, ExcTable E, con
                    (double)dtpl_term(ch.w, cc.w);
         }
     }
-    if (part) warp_partial(dsum, part);
+    if (part) warp_partial(C, blockIdx.x, warp_view(blockIdx.y, kFwdThreads / 32), dsum, part);
 }
 
 // ------------------------------------------------------------------ FP64 3x3 / 4x4 algebra
@@ -456,9 +464,8 @@ __device__ void ray_dual(const float al[4][3], const float sinv[4], const double
 // ------------------------------------------------------------------ fused MOCCA kernels
 
 // a1: line integrals of the three maps at the expansion point xbar.
-__global__ void __launch_bounds__(kFwdThreads) k_mocca_proj(GeomC C, ExcTable E, const RayRec* rec, SolveD D) {
-    const int l = ray_of_thread(C);
-    if (l < 0) return;
+__device__ __forceinline__ void proj_ray(const GeomC& C, const ExcTable& E, const RayRec* rec, const SolveD& D,
+                                         int l) {
     const float4 r0 = rec[l].r0, r1 = rec[l].r1;
     LineSum acc;
     ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) { acc.add(w, __ldg(D.xbar + k)); });
@@ -466,15 +473,17 @@ __global__ void __launch_bounds__(kFwdThreads) k_mocca_proj(GeomC C, ExcTable E,
     D.g[l] = make_float4(gs.x, gs.y, gs.z, 0.f);
 }
 
-// a2-a5 and the per-ray half of a8: spectral model, curvature, dual step.
-__global__ void __launch_bounds__(kFwdThreads, 5) k_mocca_ray(GeomC C, RayRec* rec, SpecD S, StepParams P,
-                                                              SolveD D) {
-    __shared__ float sm[kSmemStride * kMaxEnergies];
-    load_mu_smem(S, sm);
-    __syncthreads();
+__global__ void __launch_bounds__(kFwdThreads) k_mocca_proj(GeomC C, ExcTable E, const RayRec* rec, SolveD D) {
     const int l = ray_of_thread(C);
+    if (l >= 0) proj_ray(C, E, rec, D, l);
+}
+
+// a2-a5 and the per-ray half of a8: spectral model, curvature, dual step.
+// Returns the ray's D_TPL terms; sm holds the block's mu table (load_mu_smem).
+__device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const SpecD& S, const StepParams& P,
+                                           const SolveD& D, const float* sm, int l) {
     double dsum = 0.0;
-    if (l >= 0) {
+    {
         const float4 r1 = rec[l].r1;
         const float4 gg = D.g[l];
         const float g0 = gg.x, g1 = gg.y, g2 = gg.z;
@@ -581,7 +590,17 @@ __global__ void __launch_bounds__(kFwdThreads, 5) k_mocca_ray(GeomC C, RayRec* r
         rec[l].r2 = make_float4(bb[2], Sm[0], Sm[1], Sm[2]);
         rec[l].r3 = make_float4(Sm[3], Sm[4], Sm[5], 0.f);
     }
-    warp_partial(dsum, D.dtpl_part);
+    return dsum;
+}
+
+__global__ void __launch_bounds__(kFwdThreads, 5) k_mocca_ray(GeomC C, RayRec* rec, SpecD S, StepParams P,
+                                                              SolveD D) {
+    __shared__ float sm[kSmemStride * kMaxEnergies];
+    load_mu_smem(S, sm);
+    __syncthreads();
+    const int l = ray_of_thread(C);
+    const double dsum = l >= 0 ? ray_step(C, rec, S, P, D, sm, l) : 0.0;
+    warp_partial(C, blockIdx.x, warp_view(blockIdx.y, kFwdThreads / 32), dsum, D.dtpl_part);
 }
 
 // Box-constrained primal step: argmin over lo <= x <= hi of 1/2 (x - t)^T Q (x - t),
@@ -650,12 +669,12 @@ __device__ void box_prox3(const double Q[3][3], const double t[3], const float l
 // Pixel-driven back-projection with the views split over blockDim.z thread
 // groups per pixel (contiguous view ranges); the groups' partial sums are
 // added in a fixed order in shared memory, so results are deterministic.
-__global__ void __launch_bounds__(kBpMaxThreads) k_mocca_bp(GeomC C, ExcTable E, const RayRec* rec,
-                                                           const ViewF* views, StepParams P, SolveD D) {
-    extern __shared__ float red[];   // [blockDim.z - 1][9][kBpPix]
-    const int G = blockDim.z, g = threadIdx.z;
-    const int ix = blockIdx.x * kBpPixX + threadIdx.x, iy = blockIdx.y * kBpPixY + threadIdx.y;
-    const int pix = threadIdx.y * kBpPixX + threadIdx.x;
+// One pixel's share of the tile: thread group g of G handles views
+// [g per, (g + 1) per).  red holds the tile's [G - 1][9][kBpPix] partials; every
+// thread of the block must call this (it contains a block barrier).
+__device__ __forceinline__ void bp_pixel(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
+                                         const StepParams& P, const SolveD& D, int ix, int iy, int pix, int g, int G,
+                                         float* red) {
     const bool valid = ix < C.grid.n && iy < C.grid.n;
     float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (valid) {
@@ -741,11 +760,18 @@ __global__ void __launch_bounds__(kBpMaxThreads) k_mocca_bp(GeomC C, ExcTable E,
     D.xbar[k] = make_float4(2.f * xn.x - x.x, 2.f * xn.y - x.y, 2.f * xn.z - x.z, 0.f);
 }
 
+__global__ void __launch_bounds__(kBpMaxThreads) k_mocca_bp(GeomC C, ExcTable E, const RayRec* rec,
+                                                           const ViewF* views, StepParams P, SolveD D) {
+    extern __shared__ float red[];   // [blockDim.z - 1][9][kBpPix]
+    const int ix = blockIdx.x * kBpPixX + threadIdx.x, iy = blockIdx.y * kBpPixY + threadIdx.y;
+    bp_pixel(C, E, rec, views, P, D, ix, iy, threadIdx.y * kBpPixX + threadIdx.x, threadIdx.z, blockDim.z, red);
+}
+
 constexpr int kReduceThreads = 1024;
 
 // Fixed-order sum of the partials: four independent strided accumulators per
 // thread, then a block tree (deterministic for a given n).
-__global__ void __launch_bounds__(kReduceThreads) k_dtpl_reduce(const double* part, int n, double* out) {
+__device__ __forceinline__ void dtpl_reduce_body(const double* part, int n, double* out) {
     __shared__ double red[kReduceThreads / 32];
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int i = threadIdx.x;
@@ -758,6 +784,81 @@ __global__ void __launch_bounds__(kReduceThreads) k_dtpl_reduce(const double* pa
     for (; i < n; i += kReduceThreads) s0 += part[i];
     const double t = block_sum((s0 + s1) + (s2 + s3), red);
     if (threadIdx.x == 0) *out = t;
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_dtpl_reduce(const double* part, int n, double* out) {
+    dtpl_reduce_body(part, n, out);
+}
+
+// ------------------------------------------------------------------ batched (multi-solve) kernels
+//
+// Many independent solves of different sizes in one launch per step.  Each
+// launch walks a work list of (solve, tile) items: CTA i takes items i,
+// i + gridDim.x, ...  With one CTA per item this is a flat grid scheduled by the
+// hardware; with fewer CTAs it is a persistent grid.  Every ray and pixel runs
+// the same arithmetic as in the per-solve kernels, so each solve's iterates
+// are bit-identical to its own plain path whatever the batch around it.
+
+__global__ void __launch_bounds__(kBatchProjMaxThreads) k_batch_proj(const SolveDesc* __restrict__ sd,
+                                                                     const int2* __restrict__ items, int n_items) {
+    const int vb = blockDim.x >> 5;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int2 w = __ldg(items + it);
+        const SolveDesc& d = sd[w.x];
+        const GeomC C = d.C;
+        const int nbx = (C.n_bins + 31) >> 5;
+        const int l = ray_at(C, w.y % nbx, w.y / nbx, vb);
+        if (l >= 0) proj_ray(C, d.E, d.rec, d.D, l);
+    }
+}
+
+__global__ void __launch_bounds__(kFwdThreads, 5) k_batch_ray(const SolveDesc* __restrict__ sd,
+                                                              const int2* __restrict__ items, int n_items) {
+    __shared__ float sm[kSmemStride * kMaxEnergies];
+    int cur = -1;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int2 w = __ldg(items + it);
+        const SolveDesc& d = sd[w.x];
+        if (w.x != cur) {   // the same for every thread of the block
+            __syncthreads();
+            load_mu_smem(d.S, sm);
+            __syncthreads();
+            cur = w.x;
+        }
+        const GeomC C = d.C;
+        const int nbx = (C.n_bins + 31) >> 5, bx = w.y % nbx, by = w.y / nbx;
+        const int l = ray_at(C, bx, by, kFwdThreads / 32);
+        const double dsum = l >= 0 ? ray_step(C, d.rec, d.S, d.P, d.D, sm, l) : 0.0;
+        warp_partial(C, bx, warp_view(by, kFwdThreads / 32), dsum, d.D.dtpl_part);
+    }
+}
+
+// 512 threads = kBpPix pixels x 8 thread groups.  A solve with G view groups
+// (G divides 8) takes 8 / G pixel tiles per item, so the block stays full.
+__global__ void __launch_bounds__(kBpMaxThreads) k_batch_bp(const SolveDesc* __restrict__ sd,
+                                                           const int2* __restrict__ items, int n_items, int tx) {
+    __shared__ float red[7 * 9 * kBpPix];
+    const int pix = threadIdx.x % kBpPix, z = threadIdx.x / kBpPix, ty = kBpPix / tx;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int2 w = __ldg(items + it);
+        const SolveDesc& d = sd[w.x];
+        const GeomC C = d.C;
+        const int G = d.bp_groups, sub = z / G, g = z % G;
+        const int ntx = (C.grid.n + tx - 1) / tx, nty = (C.grid.n + ty - 1) / ty;
+        const int tile = w.y * (8 / G) + sub;
+        int ix = C.grid.n, iy = C.grid.n;   // outside the image: no work, but the barrier is reached
+        if (tile < ntx * nty) {
+            ix = (tile % ntx) * tx + pix % tx;
+            iy = (tile / ntx) * ty + pix / tx;
+        }
+        bp_pixel(C, d.E, d.rec, d.views, d.P, d.D, ix, iy, pix, g, G, red + sub * (G - 1) * 9 * kBpPix);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_batch_dtpl(const SolveDesc* __restrict__ sd) {
+    const SolveDesc& d = sd[blockIdx.x];
+    dtpl_reduce_body(d.D.dtpl_part, d.n_part, d.dtpl_out);
 }
 
 inline int blocks(int n, int t) { return (n + t - 1) / t; }
@@ -807,6 +908,40 @@ cudaError_t launch_mocca_bp(const GeomC& C, const ExcTable& E, const RayRec* rec
 cudaError_t launch_dtpl_reduce(const double* part, int n, double* out, cudaStream_t st) {
     k_dtpl_reduce<<<1, kReduceThreads, 0, st>>>(part, n, out);
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch_proj(const SolveDesc* sd, const int2* items, int n_items, int vb, int grid,
+                              cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    k_batch_proj<<<grid > 0 ? grid : n_items, 32 * vb, 0, st>>>(sd, items, n_items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_ray(const SolveDesc* sd, const int2* items, int n_items, int grid, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    k_batch_ray<<<grid > 0 ? grid : n_items, kFwdThreads, 0, st>>>(sd, items, n_items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_bp(const SolveDesc* sd, const int2* items, int n_items, int tx, int grid,
+                            cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    k_batch_bp<<<grid > 0 ? grid : n_items, kBpMaxThreads, 0, st>>>(sd, items, n_items, tx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_dtpl(const SolveDesc* sd, int n_solves, cudaStream_t st) {
+    if (n_solves <= 0) return cudaSuccess;
+    k_batch_dtpl<<<n_solves, kReduceThreads, 0, st>>>(sd);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_resident_ctas(int kernel, int threads, int* per_sm) {
+    switch (kernel) {
+        case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch_proj, threads, 0);
+        case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch_ray, threads, 0);
+        default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch_bp, threads, 0);
+    }
 }
 
 }  // namespace osscir

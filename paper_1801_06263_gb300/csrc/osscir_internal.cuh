@@ -71,17 +71,33 @@ __device__ __forceinline__ void chord32(const float4& r0, float ex, float ey, co
                       r0.w, ex, ey, w, eb);
 }
 
-// Footprint exception table (CSR over rays): entries (pixel k, weight bits).
+// Footprint exception table (CSR over rays): entries (key, weight bits) of the
+// ray's pixels whose FP32 chord is within its error bound of zero.  key =
+// major * n + minor, with major the pixel's index along the ray's dominant axis
+// (iy when |d_y| >= |d_x|, else ix) and minor the other; each ray's entries
+// are in increasing key order (the order in which the setup pass enumerates
+// them).  A ray running exactly along a grid line has about 2n entries.
 struct ExcTable {
     const int* off;    // [L + 1]
     const int2* ent;   // [off[L]]
 };
 
-__device__ __forceinline__ float exc_lookup(const ExcTable& E, int l, int k) {
-    const int a = __ldg(E.off + l), b = __ldg(E.off + l + 1);
-    for (int j = a; j < b; ++j) {
-        const int2 e = __ldg(E.ent + j);
-        if (e.x == k) return __int_as_float(e.y);
+__device__ __forceinline__ bool ray_rows(const float4& r0) { return fabsf(r0.w) <= fabsf(r0.z); }
+
+__device__ __forceinline__ int exc_key(bool rows, int n, int ix, int iy) { return rows ? iy * n + ix : ix * n + iy; }
+
+// Binary search of the ray's entries for key.
+__device__ __forceinline__ float exc_lookup(const ExcTable& E, int l, int key) {
+    int lo = __ldg(E.off + l), hi = __ldg(E.off + l + 1);
+    const int end = hi;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&E.ent[mid].x) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < end) {
+        const int2 e = __ldg(E.ent + lo);
+        if (e.x == key) return __int_as_float(e.y);
     }
     return 0.0f;
 }
@@ -91,14 +107,14 @@ __device__ __forceinline__ float exc_lookup(const ExcTable& E, int l, int k) {
 // bound of a chord never exceeds 2 max(ex, ey), so that test settles most pairs
 // before the exact bound is formed; the outcome is the same either way.
 __device__ __forceinline__ float member_weight(float w, float txl, float txh, float tyl, float tyh, float ex,
-                                               float ey, const ExcTable& E, int l, int k) {
+                                               float ey, const ExcTable& E, int l, int key) {
     const float ebmax = 2.0f * fmaxf(ex, ey);
     if (w > ebmax) return w;
     if (w < -ebmax) return 0.0f;
     const float eb = chord_bound(txl, txh, tyl, tyh, ex, ey);
     if (w > eb) return w;
     if (w < -eb) return 0.0f;
-    return exc_lookup(E, l, k);   // also reached by NaN (axis-parallel rays)
+    return exc_lookup(E, l, key);   // also reached by NaN (axis-parallel rays)
 }
 
 // X_{l,k}: the weight both projectors use.
@@ -109,7 +125,7 @@ __device__ __forceinline__ float x_weight(const float4& r0, float ex, float ey, 
     const float txl = r0.z >= 0.0f ? tx0 : tx1, txh = r0.z >= 0.0f ? tx1 : tx0;
     const float tyl = r0.w >= 0.0f ? ty0 : ty1, tyh = r0.w >= 0.0f ? ty1 : ty0;
     const float w = __fsub_rn(fminf(txh, tyh), fmaxf(txl, tyl));
-    return member_weight(w, txl, txh, tyl, tyh, ex, ey, E, l, iy * G.n + ix);
+    return member_weight(w, txl, txh, tyl, tyh, ex, ey, E, l, exc_key(ray_rows(r0), G.n, ix, iy));
 }
 
 // float -> int with saturation (huge or infinite coordinates stay in range).
@@ -172,7 +188,7 @@ template <class Visit>
 __device__ __forceinline__ void ray_chords(const float4& r0, float ex, float ey, const GridF& G, float margin,
                                            Visit&& visit) {
     // r0.zw = (1/dx, 1/dy): the ray is row-major (|dy| >= |dx|) iff |1/dy| <= |1/dx|
-    if (fabsf(r0.w) <= fabsf(r0.z)) ray_chords_dir<true>(r0, ex, ey, G, margin, visit);
+    if (ray_rows(r0)) ray_chords_dir<true>(r0, ex, ey, G, margin, visit);
     else ray_chords_dir<false>(r0, ex, ey, G, margin, visit);
 }
 
@@ -225,7 +241,7 @@ __device__ __forceinline__ void ray_weights_dir(const float4& r0, float ex, floa
                 const float tyl = ROWS ? tMl : tml, tyh = ROWS ? tMh : tmh;
                 const float w = __fsub_rn(fminf(txh, tyh), fmaxf(txl, tyl));
                 const int k = ROWS ? j * G.n + i : i * G.n + j;
-                const float x = member_weight(w, txl, txh, tyl, tyh, ex, ey, E, l, k);
+                const float x = member_weight(w, txl, txh, tyl, tyh, ex, ey, E, l, j * G.n + i);
                 if (x != 0.0f) visit(k, x);
             }
         }
@@ -237,7 +253,7 @@ __device__ __forceinline__ void ray_weights_dir(const float4& r0, float ex, floa
 template <class Visit>
 __device__ __forceinline__ void ray_weights(const float4& r0, float ex, float ey, const GridF& G, float margin,
                                             const ExcTable& E, int l, Visit&& visit) {
-    const bool rows = fabsf(r0.w) <= fabsf(r0.z), px = r0.z >= 0.0f, py = r0.w >= 0.0f;
+    const bool rows = ray_rows(r0), px = r0.z >= 0.0f, py = r0.w >= 0.0f;
     if (rows) {
         if (px) {
             if (py) ray_weights_dir<true, true, true>(r0, ex, ey, G, margin, E, l, visit);

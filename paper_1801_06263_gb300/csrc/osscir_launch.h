@@ -90,10 +90,46 @@ cudaError_t launch_dtpl_reduce(const double* part, int n, double* out, cudaStrea
 inline dim3 fwd_grid(int n_bins, int n_views) {
     return dim3((n_bins + 31) / 32, (n_views + kFwdThreads / 32 - 1) / (kFwdThreads / 32));
 }
-// D_TPL partial sums: one per warp of the ray-driven kernels.
-inline int dtpl_partials(int n_bins, int n_views) {
-    const dim3 g = fwd_grid(n_bins, n_views);
-    return (int)(g.x * g.y) * (kFwdThreads / 32);
+// D_TPL partial sums: one per (view, group of 32 bins), i.e. per warp of the ray-driven kernels.
+inline int dtpl_partials(int n_bins, int n_views) { return n_views * ((n_bins + 31) / 32); }
+
+// ------------------------------------------------------------------ batched kernels
+
+// One solve of a batch as the batched kernels see it (device array, one per solve).
+struct SolveDesc {
+    GeomC C;
+    ExcTable E;
+    RayRec* rec;
+    const ViewF* views;
+    SpecD S;
+    StepParams P;
+    SolveD D;
+    double* dtpl_out;   // D_TPL at the last expansion point
+    int n_part;         // dtpl_partials(n_bins, n_views)
+    int bp_groups;      // bp_view_groups(P, n_views), a divisor of 8
+};
+
+constexpr int kBatchProjMaxThreads = 256;   // up to 8 views x 32 bins per projection block
+
+// Work-list sizes per solve.  Projection: tiles of 32 bins x vb views; ray
+// kernel: 32 bins x 4 views; back-projection: 8 / G pixel tiles of kBpPix pixels
+// (tx wide) per item.
+inline int batch_proj_tiles(int n_bins, int n_views, int vb) {
+    return ((n_bins + 31) / 32) * ((n_views + vb - 1) / vb);
 }
+inline int batch_bp_items(int n, int tx, int G) {
+    const int ty = kBpPix / tx, tiles = ((n + tx - 1) / tx) * ((n + ty - 1) / ty), per = 8 / G;
+    return (tiles + per - 1) / per;
+}
+
+// grid <= 0: one CTA per work item; otherwise that many persistent CTAs.
+cudaError_t launch_batch_proj(const SolveDesc* sd, const int2* items, int n_items, int vb, int grid,
+                              cudaStream_t st);
+cudaError_t launch_batch_ray(const SolveDesc* sd, const int2* items, int n_items, int grid, cudaStream_t st);
+cudaError_t launch_batch_bp(const SolveDesc* sd, const int2* items, int n_items, int tx, int grid,
+                            cudaStream_t st);
+cudaError_t launch_batch_dtpl(const SolveDesc* sd, int n_solves, cudaStream_t st);
+// Resident CTAs per SM of a batched kernel (0 projection, 1 ray, 2 back-projection).
+cudaError_t batch_resident_ctas(int kernel, int threads, int* per_sm);
 
 }  // namespace osscir

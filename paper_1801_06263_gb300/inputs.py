@@ -292,6 +292,31 @@ def workload(name: str) -> Workload:
     raise KeyError(name)
 
 
+def step_ratio(n: int, photons_per_ray: float) -> float:
+    """Step ratio lambda for a solve of size n and dose: the values tuned with the
+    oracle (1e-7 at 64 x 64 / 1e5, 10^-7.5 at 256 x 256 / 1e5, 10^-8.5 at
+    512 x 512 / 1e6) follow roughly 10^-7.5 (256 / n) (1e5 / N0)^(1/2); half of
+    that keeps every size and dose of the batched workloads inside the stable range."""
+    return 0.5 * 10.0 ** -7.5 * (256.0 / n) * (1e5 / photons_per_ray) ** 0.5
+
+
+def batch_workloads(n_solves: int = 64, seed: int = 4000) -> list:
+    """Independent reconstructions of uneven sizes for the batched form: n from
+    {128, 192, 256, 384, 512} (0.5 mm pixels), views uniform in [90, 720] with as
+    many detector bins, dose log-uniform in [1e4, 1e6] photons per ray, and
+    their own ellipse phantom (seed 1000 + i) and noise seed (2000 + i)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_solves):
+        n = int(rng.choice([128, 192, 256, 384, 512]))
+        views = int(rng.integers(90, 721))
+        photons = float(10.0 ** rng.uniform(4.0, 6.0))
+        g = make_geometry(n, 0.5, views, views)
+        out.append(Workload(f"batch_{i}", g, make_spectra(views, photons), ellipse_phantom(g, 1000 + i),
+                            photons, 2000 + i, 500))
+    return out
+
+
 def random_state(geom: Geometry, seed: int, scale: float = 1.0):
     """Seeded random image (float [P,3]) and dual (float [L,4]) for projector tests."""
     rng = np.random.default_rng(seed)

@@ -81,3 +81,22 @@ def test_null_handle_calls_are_rejected(lib):
     out = ct.c_double()
     assert lib.osscir_dtpl(null, 0, ct.byref(out), None) == _lib.OSSCIR_E_INVALID
     assert lib.osscir_destroy(null) == _lib.OSSCIR_OK
+
+
+def test_batch_calls_reject_invalid_arguments(lib):
+    null = ct.c_void_p(0)
+    out = ct.c_void_p()
+    assert lib.osscir_batch_create(None, 1, 0, ct.byref(out)) == _lib.OSSCIR_E_INVALID
+    arr = (ct.c_void_p * 2)(None, None)
+    assert lib.osscir_batch_create(arr, 0, 0, ct.byref(out)) == _lib.OSSCIR_E_INVALID
+    assert lib.osscir_batch_create(arr, 2, 0, ct.byref(out)) == _lib.OSSCIR_E_INVALID
+    # the same context twice: rejected before any device call
+    fake = (ct.c_void_p * 2)(0x1000, 0x1000)
+    assert lib.osscir_batch_create(fake, 2, 0, ct.byref(out)) == _lib.OSSCIR_E_INVALID
+    assert lib.osscir_batch_create(fake, 1, 2, ct.byref(out)) == _lib.OSSCIR_E_INVALID
+    assert out.value is None
+    assert lib.osscir_batch_step(null, 1, None) == _lib.OSSCIR_E_INVALID
+    cfg = _lib.BatchConfig(4, 0, 0, 0, 0, 8, 0, 0)
+    assert lib.osscir_batch_get_config(null, ct.byref(cfg)) == _lib.OSSCIR_E_INVALID
+    assert lib.osscir_batch_set_config(null, ct.byref(cfg)) == _lib.OSSCIR_E_INVALID
+    assert lib.osscir_batch_destroy(null) == _lib.OSSCIR_OK
