@@ -204,7 +204,12 @@ typedef struct osscir_batch *osscir_batch_t;
  *   bp_tile_x:   width of the 64-pixel back-projection tile (4, 8, 16 or 32);
  *   *_order:     work-list order of each kernel: 0 solve by solve, 1 the
  *                solves with the costliest items first, 2 solves interleaved
- *                item by item. */
+ *                item by item;
+ *   branches:    1, 2 or 4 (at most the number of solves): the solves are
+ *                split into that many groups of about equal work, each with
+ *                its own launches, as parallel branches of the iteration graph
+ *                (so one group's projection can overlap another's per-ray
+ *                step). */
 typedef struct {
     int proj_views;
     int proj_grid;
@@ -214,12 +219,14 @@ typedef struct {
     int bp_tile_x;
     int bp_grid;
     int bp_order;
+    int branches;
 } osscir_batch_config;
 
-/* Build a batch over n (1 .. 4096) distinct contexts of the current device.
- * autotune = 0 takes the default configuration; autotune = 1 times candidate
- * configurations on the batch itself (a few launches each, restoring every
- * solve's state afterwards) and keeps the fastest (synchronises).  Errors:
+/* Build a batch over n (1 .. 4096) distinct contexts of the current device
+ * (synchronises the device first).  autotune = 0 takes the default
+ * configuration; autotune = 1 times candidate configurations on the batch
+ * itself (a few launches each, restoring every solve's state afterwards) and
+ * keeps the fastest.  Errors:
  * OSSCIR_E_INVALID (NULL or repeated handles, contexts of another device),
  * OSSCIR_E_NOMEM, OSSCIR_E_CUDA. */
 osscir_status osscir_batch_create(const osscir_t *solves, int n, int autotune, osscir_batch_t *out);
@@ -237,19 +244,26 @@ osscir_status osscir_batch_get_config(osscir_batch_t b, osscir_batch_config *out
 osscir_status osscir_batch_set_config(osscir_batch_t b, const osscir_batch_config *cfg);
 
 /* Device time (ms) of the projection, ray and back-projection launches of
- * the last batch iteration enqueued on stream (synchronises the stream). */
+ * the last batch iteration enqueued on stream (synchronises the stream); with
+ * several branches, those of the first branch. */
 osscir_status osscir_batch_last_kernel_ms(osscir_batch_t b, float ms[3], void *stream);
 
 /* ------------------------------------------------------------------ served form
- * A server owns a worker thread on the device that is current when it is
- * created.  Requests (complete reconstruction problems with host data) are
- * queued by osscir_submit and admitted while a slot is free and the device
- * memory of all cached contexts stays within the budget; admitted requests run
- * concurrently on their own streams (continuous batching: new requests join
- * while others are on the GPU).  Contexts of finished requests stay cached and
- * are reused by later requests with the same geometry, spectra, mu and
- * parameters; the least recently used idle ones are released when memory is
- * needed.  A request's result does not depend on what else runs. */
+ * A server owns a worker thread and a stream on the device that is current
+ * when it is created.  Requests (complete reconstruction problems with host
+ * data) are queued by osscir_submit and admitted while a slot is free and the
+ * device memory of all cached contexts stays within the budget.  Admitted
+ * requests are spread over up to four groups of about equal work; each group
+ * advances all its requests together, a few MOCCA iterations per round,
+ * through the batched kernels (one launch per kernel per iteration for the
+ * group) on its own stream, and the groups run side by side.  A group's batch
+ * is re-formed between its rounds, so requests that arrive while others are on
+ * the GPU join at the next round and finished ones leave (continuous
+ * batching).  Contexts of finished requests stay cached and are reused by later
+ * requests with the same geometry, spectra, mu and parameters; the least
+ * recently used idle ones are released when memory is needed.  A request's
+ * result does not depend on what else runs: it equals the plain form's bit for
+ * bit. */
 typedef struct osscir_server *osscir_server_t;
 
 typedef struct {
@@ -267,7 +281,8 @@ typedef struct {
     double dtpl;          /* D_TPL at the last expansion point */
     double latency_ms;    /* submit to result ready (host clock) */
     double queue_ms;      /* submit to work enqueued on the GPU */
-    double gpu_ms;        /* device time of the solve (events on its stream) */
+    double gpu_ms;        /* device time from its first work to its results (the
+                             rounds it shares with other requests included) */
 } osscir_stats;
 
 /* Create a server.  hbm_budget_bytes: device memory the server's contexts may

@@ -64,7 +64,7 @@ class Request(ct.Structure):
 class BatchConfig(ct.Structure):
     _fields_ = [("proj_views", ct.c_int), ("proj_grid", ct.c_int), ("proj_order", ct.c_int),
                 ("ray_grid", ct.c_int), ("ray_order", ct.c_int), ("bp_tile_x", ct.c_int),
-                ("bp_grid", ct.c_int), ("bp_order", ct.c_int)]
+                ("bp_grid", ct.c_int), ("bp_order", ct.c_int), ("branches", ct.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

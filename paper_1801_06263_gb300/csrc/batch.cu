@@ -1,9 +1,11 @@
 // Batched form of the C-ABI (include/osscir.h): many independent solves
-// advanced by one launch per kernel per MOCCA step, over work lists of
-// (solve, tile) items, captured once as a CUDA graph; plus the autotuner that
-// picks tile shapes, grid policy and work-list order by timing them on the
-// batch itself.
+// advanced by one launch per kernel (per branch) per MOCCA step, over work
+// lists of (solve, tile) items, captured once as a CUDA graph whose branches
+// run concurrently; the autotuner that picks tile shapes, grid policy,
+// work-list order and branch count by timing them on the batch itself; and the
+// batch runner the served form drives.
 #include <algorithm>
+#include <cstring>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -11,21 +13,6 @@
 #include "osscir_ctx.h"
 
 using namespace osscir;
-
-struct osscir_batch {
-    int device = 0;
-    int sms = 0;
-    std::vector<osscir_ctx*> ctx;
-    osscir_batch_config cfg{};
-    SolveDesc* desc = nullptr;   // device [n]
-    int2* items[3] = {nullptr, nullptr, nullptr};   // projection, ray, back-projection work lists
-    int n_items[3] = {0, 0, 0};
-    size_t cap_items[3] = {0, 0, 0};
-    cudaStream_t cap_stream = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-};
 
 namespace {
 
@@ -49,7 +36,8 @@ osscir_status from_cuda(cudaError_t e) {
 
 inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
-constexpr osscir_batch_config kDefault = {4, 0, 0, 0, 0, 8, 0, 0};
+constexpr int kMaxBranches = 4;
+constexpr osscir_batch_config kDefault = {4, 0, 0, 0, 0, 8, 0, 0, 1};
 
 bool valid_config(const osscir_batch_config& c) {
     const auto pow2_in = [](int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; };
@@ -57,7 +45,7 @@ bool valid_config(const osscir_batch_config& c) {
     const auto order_ok = [](int o) { return o >= 0 && o <= 2; };
     return pow2_in(c.proj_views, 1, 8) && pow2_in(c.bp_tile_x, 4, 32) && grid_ok(c.proj_grid) &&
            grid_ok(c.ray_grid) && grid_ok(c.bp_grid) && order_ok(c.proj_order) && order_ok(c.ray_order) &&
-           order_ok(c.bp_order);
+           order_ok(c.bp_order) && pow2_in(c.branches, 1, kMaxBranches);
 }
 
 SolveDesc make_desc(const osscir_ctx* h) {
@@ -75,156 +63,292 @@ SolveDesc make_desc(const osscir_ctx* h) {
     return d;
 }
 
+// Relative device time of one iteration of a solve: footprint pairs (~ rays x
+// image side) for the projection, rays x energies for the per-ray step, pixels
+// x views for the back-projection, weighted by their measured costs per unit.
+double solve_cost(const osscir_ctx* h) {
+    const double L = (double)h->L, N = h->g64.n, P = (double)h->P;
+    return L * N + 2.1 * L * h->nE + 1.8 * P * h->g64.n_views;
+}
+
 // Items per solve and the relative cost of one item, for kernel k (0 projection,
 // 1 ray, 2 back-projection) under configuration c.
-void item_counts(const osscir_batch* b, int k, const osscir_batch_config& c, std::vector<int>& count,
-                 std::vector<double>& cost) {
-    const int n = (int)b->ctx.size();
-    count.assign(n, 0);
-    cost.assign(n, 0.0);
-    for (int s = 0; s < n; ++s) {
-        const osscir_ctx* h = b->ctx[s];
-        const int nb = h->g64.n_bins, nv = h->g64.n_views, N = h->g64.n;
-        if (k == 0) {
-            count[s] = batch_proj_tiles(nb, nv, c.proj_views);
-            cost[s] = (double)N;                         // pixels per ray ~ image side
-        } else if (k == 1) {
-            count[s] = batch_proj_tiles(nb, nv, kFwdThreads / 32);
-            cost[s] = (double)h->nE;                     // energy passes per ray
-        } else {
-            const int G = bp_view_groups(h->P, nv);
-            count[s] = batch_bp_items(N, c.bp_tile_x, G);
-            cost[s] = (double)nv / G;                    // views per thread group
-        }
+void item_counts(const osscir_ctx* h, int k, const osscir_batch_config& c, int* count, double* cost) {
+    const int nb = h->g64.n_bins, nv = h->g64.n_views, N = h->g64.n;
+    if (k == 0) {
+        *count = batch_proj_tiles(nb, nv, c.proj_views);
+        *cost = (double)N;                       // pixels per ray ~ image side
+    } else if (k == 1) {
+        *count = batch_proj_tiles(nb, nv, kFwdThreads / 32);
+        *cost = (double)h->nE;                   // energies per ray
+    } else {
+        const int G = bp_view_groups(h->P, nv);
+        *count = batch_bp_items(N, c.bp_tile_x, G);
+        *cost = (double)nv / G;                  // views per thread group
     }
 }
 
-void build_items(const osscir_batch* b, int k, const osscir_batch_config& c, std::vector<int2>& out) {
-    std::vector<int> count;
-    std::vector<double> cost;
-    item_counts(b, k, c, count, cost);
+// Work list of kernel k over solves [first, first + n) of the descriptor array.
+void build_items(const std::vector<osscir_ctx*>& ctx, int first, int n, int k, const osscir_batch_config& c,
+                 std::vector<int2>& out) {
+    std::vector<int> count(n);
+    std::vector<double> cost(n);
+    for (int s = 0; s < n; ++s) item_counts(ctx[first + s], k, c, &count[s], &cost[s]);
     const int order = k == 0 ? c.proj_order : (k == 1 ? c.ray_order : c.bp_order);
-    const int n = (int)count.size();
-    std::vector<int> solves(n);
-    std::iota(solves.begin(), solves.end(), 0);
     out.clear();
-    if (order == 1)
-        std::stable_sort(solves.begin(), solves.end(), [&](int a, int bb) { return cost[a] > cost[bb]; });
+    if (n == 0) return;
     if (order == 2) {
         const int most = *std::max_element(count.begin(), count.end());
         for (int t = 0; t < most; ++t)
             for (int s = 0; s < n; ++s)
-                if (t < count[s]) out.push_back(make_int2(s, t));
+                if (t < count[s]) out.push_back(make_int2(first + s, t));
         return;
     }
+    std::vector<int> solves(n);
+    std::iota(solves.begin(), solves.end(), 0);
+    if (order == 1)
+        std::stable_sort(solves.begin(), solves.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     for (int s : solves)
-        for (int t = 0; t < count[s]; ++t) out.push_back(make_int2(s, t));
+        for (int t = 0; t < count[s]; ++t) out.push_back(make_int2(first + s, t));
 }
 
-osscir_status upload_items(osscir_batch* b, int k, const std::vector<int2>& v) {
-    if (v.size() > (size_t)0x7fffffff) return OSSCIR_E_INVALID;
-    if (v.size() > b->cap_items[k]) {
-        if (b->items[k]) cudaFree(b->items[k]);
-        b->items[k] = nullptr;
-        b->cap_items[k] = 0;
-        CK(cudaMalloc(reinterpret_cast<void**>(&b->items[k]), sizeof(int2) * v.size()));
-        b->cap_items[k] = v.size();
+// A batch laid out for the device: solves grouped by branch (about equal work
+// per branch, largest first to the least loaded), their descriptors, and each
+// branch's three work lists, as one byte image.
+struct Plan {
+    int branches = 1;
+    std::vector<osscir_ctx*> order;   // descriptor order
+    int first[kMaxBranches] = {0, 0, 0, 0}, count[kMaxBranches] = {0, 0, 0, 0};
+    size_t off[kMaxBranches][3] = {};
+    int n_items[kMaxBranches][3] = {};
+    std::vector<char> image;
+};
+
+void make_plan(const std::vector<osscir_ctx*>& ctx, const osscir_batch_config& c, Plan& p) {
+    const int n = (int)ctx.size();
+    p.branches = std::max(1, std::min(c.branches, n));
+    std::vector<int> idx(n), owner(n);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return solve_cost(ctx[a]) > solve_cost(ctx[b]); });
+    double load[kMaxBranches] = {0, 0, 0, 0};
+    for (int i : idx) {
+        int b = 0;
+        for (int j = 1; j < p.branches; ++j)
+            if (load[j] < load[b]) b = j;
+        owner[i] = b;
+        load[b] += solve_cost(ctx[i]);
     }
-    if (!v.empty()) CK(cudaMemcpy(b->items[k], v.data(), sizeof(int2) * v.size(), cudaMemcpyHostToDevice));
-    b->n_items[k] = (int)v.size();
-    return OSSCIR_OK;
-}
-
-osscir_status build_all_items(osscir_batch* b) {
-    std::vector<int2> v;
-    for (int k = 0; k < 3; ++k) {
-        build_items(b, k, b->cfg, v);
-        CKS(upload_items(b, k, v));
+    p.order.clear();
+    for (int b = 0; b < p.branches; ++b) {
+        p.first[b] = (int)p.order.size();
+        for (int i = 0; i < n; ++i)
+            if (owner[i] == b) p.order.push_back(ctx[i]);
+        p.count[b] = (int)p.order.size() - p.first[b];
     }
-    return OSSCIR_OK;
-}
-
-cudaError_t launch_kernel(const osscir_batch* b, int k, const osscir_batch_config& c, cudaStream_t st) {
-    if (k == 0) return launch_batch_proj(b->desc, b->items[0], b->n_items[0], c.proj_views, c.proj_grid, st);
-    if (k == 1) return launch_batch_ray(b->desc, b->items[1], b->n_items[1], c.ray_grid, st);
-    return launch_batch_bp(b->desc, b->items[2], b->n_items[2], c.bp_tile_x, c.bp_grid, st);
-}
-
-cudaError_t enqueue_iteration(const osscir_batch* b, cudaStream_t st) {
-    for (int k = 0; k < 3; ++k) {
-        cudaError_t e = cudaEventRecordWithFlags(b->ev[k], st, cudaEventRecordExternal);
-        if (e != cudaSuccess) return e;
-        e = launch_kernel(b, k, b->cfg, st);
-        if (e != cudaSuccess) return e;
+    size_t bytes = sizeof(SolveDesc) * n;
+    std::vector<int2> lists[kMaxBranches][3];
+    for (int b = 0; b < p.branches; ++b)
+        for (int k = 0; k < 3; ++k) {
+            build_items(p.order, p.first[b], p.count[b], k, c, lists[b][k]);
+            bytes = (bytes + 255) & ~size_t(255);
+            p.off[b][k] = bytes;
+            p.n_items[b][k] = (int)lists[b][k].size();
+            bytes += sizeof(int2) * lists[b][k].size();
+        }
+    p.image.assign(std::max<size_t>(bytes, 1), 0);
+    for (int i = 0; i < n; ++i) {
+        const SolveDesc d = make_desc(p.order[i]);
+        std::memcpy(p.image.data() + sizeof(SolveDesc) * i, &d, sizeof d);
     }
-    const cudaError_t e = cudaEventRecordWithFlags(b->ev[3], st, cudaEventRecordExternal);
-    if (e != cudaSuccess) return e;
-    return launch_batch_dtpl(b->desc, (int)b->ctx.size(), st);
+    for (int b = 0; b < p.branches; ++b)
+        for (int k = 0; k < 3; ++k)
+            if (!lists[b][k].empty())
+                std::memcpy(p.image.data() + p.off[b][k], lists[b][k].data(), sizeof(int2) * lists[b][k].size());
 }
 
-void drop_graph(osscir_batch* b) {
-    if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    if (b->graph) cudaGraphDestroy(b->graph);
-    b->gexec = nullptr;
-    b->graph = nullptr;
+inline const SolveDesc* plan_desc(const char* dev) { return reinterpret_cast<const SolveDesc*>(dev); }
+inline const int2* plan_items(const Plan& p, const char* dev, int b, int k) {
+    return reinterpret_cast<const int2*>(dev + p.off[b][k]);
 }
 
-osscir_status capture(osscir_batch* b) {
-    drop_graph(b);
-    CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-    const cudaError_t e = enqueue_iteration(b, b->cap_stream);
+cudaError_t launch_branch_kernel(const Plan& p, const char* dev, int b, int k, const osscir_batch_config& c,
+                                 cudaStream_t st) {
+    const SolveDesc* d = plan_desc(dev);
+    const int2* it = plan_items(p, dev, b, k);
+    const int n = p.n_items[b][k];
+    if (k == 0) return launch_batch_proj(d, it, n, c.proj_views, c.proj_grid, st);
+    if (k == 1) return launch_batch_ray(d, it, n, c.ray_grid, st);
+    return launch_batch_bp(d, it, n, c.bp_tile_x, c.bp_grid, st);
+}
+
+// Streams and events a batch needs to capture its iteration with branches.
+struct Lanes {
+    cudaStream_t main = nullptr;
+    cudaStream_t aux[kMaxBranches - 1] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t fork_at[kMaxBranches - 1] = {nullptr, nullptr, nullptr};
+    cudaEvent_t join[kMaxBranches - 1] = {nullptr, nullptr, nullptr};
+
+    cudaError_t create() {
+        cudaError_t e = cudaStreamCreateWithFlags(&main, cudaStreamNonBlocking);
+        for (int i = 0; i < kMaxBranches - 1 && e == cudaSuccess; ++i)
+            e = cudaStreamCreateWithFlags(&aux[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        for (int i = 0; i < kMaxBranches - 1 && e == cudaSuccess; ++i) {
+            e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork_at[i], cudaEventDisableTiming);
+        }
+        return e;
+    }
+    void destroy() {
+        if (main) cudaStreamSynchronize(main);
+        for (auto& s : aux)
+            if (s) cudaStreamDestroy(s);
+        if (main) cudaStreamDestroy(main);
+        if (fork) cudaEventDestroy(fork);
+        for (auto& e : join)
+            if (e) cudaEventDestroy(e);
+        for (auto& e : fork_at)
+            if (e) cudaEventDestroy(e);
+        main = nullptr;
+    }
+};
+
+// `iters` iterations of every solve into the stream being captured on L.main:
+// in each iteration branch b launches projection, ray step, back-projection
+// and its D_TPL reduction; branches other than 0 fork from L.main and join
+// back after their last iteration.  With skew, branch b starts when branch
+// b - 1 has finished its first projection, so the branches run different
+// kernels side by side.  ev (optional) is recorded around branch 0's kernels
+// of its last iteration.
+cudaError_t enqueue_plan(const Plan& p, const char* dev, const osscir_batch_config& c, const Lanes& L,
+                         const cudaEvent_t* ev, int iters = 1, bool skew = false) {
+    cudaError_t e = cudaSuccess;
+    auto stream_of = [&](int b) { return b == 0 ? L.main : L.aux[b - 1]; };
+    if (p.branches > 1 && !skew) {
+        e = cudaEventRecord(L.fork, L.main);
+        for (int b = 1; b < p.branches && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(L.aux[b - 1], L.fork, 0);
+    }
+    for (int b = 0; b < p.branches && e == cudaSuccess; ++b) {
+        cudaStream_t st = stream_of(b);
+        for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+            const bool timed = ev && b == 0 && it == iters - 1;
+            for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+                if (timed) e = cudaEventRecordWithFlags(ev[k], st, cudaEventRecordExternal);
+                if (e == cudaSuccess) e = launch_branch_kernel(p, dev, b, k, c, st);
+                // the next branch starts after this branch's first projection
+                if (e == cudaSuccess && skew && it == 0 && k == 0 && b + 1 < p.branches) {
+                    e = cudaEventRecord(L.fork_at[b], st);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream_of(b + 1), L.fork_at[b], 0);
+                }
+            }
+            if (e == cudaSuccess && timed) e = cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
+            if (e == cudaSuccess) e = launch_batch_dtpl(plan_desc(dev) + p.first[b], p.count[b], st);
+        }
+    }
+    for (int b = 1; b < p.branches && e == cudaSuccess; ++b) {
+        e = cudaEventRecord(L.join[b - 1], L.aux[b - 1]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(L.main, L.join[b - 1], 0);
+    }
+    return e;
+}
+
+// Capture `iters` iterations as an executable graph.
+osscir_status capture_plan(const Plan& p, const char* dev, const osscir_batch_config& c, const Lanes& L,
+                           const cudaEvent_t* ev, cudaGraphExec_t* out, int iters = 1, bool skew = false) {
+    *out = nullptr;
+    CK(cudaStreamBeginCapture(L.main, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t e = enqueue_plan(p, dev, c, L, ev, iters, skew);
     cudaGraph_t g = nullptr;
-    const cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
-    if (e != cudaSuccess) {
+    const cudaError_t e2 = cudaStreamEndCapture(L.main, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
-        return from_cuda(e);
+        return from_cuda(e != cudaSuccess ? e : e2);
     }
-    CK(e2);
-    b->graph = g;
-    CK(cudaGraphInstantiate(&b->gexec, g, 0));
+    const cudaError_t e3 = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return from_cuda(e3);
+}
+
+}  // namespace
+
+struct osscir_batch {
+    int device = 0;
+    int sms = 0;
+    std::vector<osscir_ctx*> ctx;
+    osscir_batch_config cfg{};
+    Plan plan;
+    char* dev = nullptr;   // descriptors and work lists
+    size_t cap = 0;
+    Lanes lanes;
+    cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+// Lay the batch out for configuration c and copy it to the device (synchronous).
+osscir_status upload(osscir_batch* b, const osscir_batch_config& c) {
+    make_plan(b->ctx, c, b->plan);
+    const size_t bytes = b->plan.image.size();
+    if (bytes > b->cap) {
+        if (b->dev) cudaFree(b->dev);
+        b->dev = nullptr;
+        b->cap = 0;
+        CK(cudaMalloc(reinterpret_cast<void**>(&b->dev), bytes));
+        b->cap = bytes;
+    }
+    CK(cudaMemcpy(b->dev, b->plan.image.data(), bytes, cudaMemcpyHostToDevice));
     return OSSCIR_OK;
+}
+
+osscir_status rebuild(osscir_batch* b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    CKS(upload(b, b->cfg));
+    return capture_plan(b->plan, b->dev, b->cfg, b->lanes, b->ev, &b->gexec);
 }
 
 void free_batch(osscir_batch* b) {
     if (!b) return;
-    if (b->cap_stream) cudaStreamSynchronize(b->cap_stream);
-    drop_graph(b);
+    cudaDeviceSynchronize();   // launches of the batch's graph may still be queued on callers' streams
+    b->lanes.destroy();
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
     for (auto& e : b->ev)
         if (e) cudaEventDestroy(e);
-    for (auto& p : b->items)
-        if (p) cudaFree(p);
-    if (b->desc) cudaFree(b->desc);
-    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->dev) cudaFree(b->dev);
     delete b;
 }
 
 // ------------------------------------------------------------------ autotuner
 
-// Mean device time (ms) of `reps` launches of kernel k under configuration c,
-// after one untimed launch, on the batch's own stream.
-osscir_status time_kernel(osscir_batch* b, int k, const osscir_batch_config& c, cudaEvent_t t0, cudaEvent_t t1,
+// Mean device time (ms) of `reps` runs after one untimed run.  k = 0, 1, 2: that
+// kernel alone over the whole batch (one branch); k = 3: a whole iteration graph.
+osscir_status time_config(osscir_batch* b, int k, const osscir_batch_config& c, cudaEvent_t t0, cudaEvent_t t1,
                           float* ms) {
-    std::vector<int2> v;
-    build_items(b, k, c, v);
-    CKS(upload_items(b, k, v));
+    CKS(upload(b, c));
+    cudaGraphExec_t gx = nullptr;
+    if (k == 3) CKS(capture_plan(b->plan, b->dev, c, b->lanes, nullptr, &gx));
     const int reps = 3;
-    CK(launch_kernel(b, k, c, b->cap_stream));
-    CK(cudaEventRecord(t0, b->cap_stream));
-    for (int r = 0; r < reps; ++r) CK(launch_kernel(b, k, c, b->cap_stream));
-    CK(cudaEventRecord(t1, b->cap_stream));
-    CK(cudaEventSynchronize(t1));
-    CK(cudaEventElapsedTime(ms, t0, t1));
+    cudaStream_t st = b->lanes.main;
+    auto run = [&]() { return k == 3 ? cudaGraphLaunch(gx, st) : launch_branch_kernel(b->plan, b->dev, 0, k, c, st); };
+    cudaError_t e = run();
+    if (e == cudaSuccess) e = cudaEventRecord(t0, st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = run();
+    if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, t0, t1);
+    if (gx) cudaGraphExecDestroy(gx);
+    CK(e);
     *ms /= reps;
     return OSSCIR_OK;
 }
 
-// Coordinate search per kernel: grid policy x order at the default tile, then
-// the tile shape at the best of those.
+// Coordinate search per kernel with one branch: grid policy x order at the
+// default tile, then the tile shape at the best of those.
 osscir_status tune_kernel(osscir_batch* b, int k, int persistent_grid, cudaEvent_t t0, cudaEvent_t t1) {
     osscir_batch_config best = b->cfg;
     float best_ms = 3.0e38f;
-    int* grid = k == 0 ? &best.proj_grid : (k == 1 ? &best.ray_grid : &best.bp_grid);
-    int* order = k == 0 ? &best.proj_order : (k == 1 ? &best.ray_order : &best.bp_order);
     osscir_batch_config c = best;
     int* cgrid = k == 0 ? &c.proj_grid : (k == 1 ? &c.ray_grid : &c.bp_grid);
     int* corder = k == 0 ? &c.proj_order : (k == 1 ? &c.ray_order : &c.bp_order);
@@ -233,30 +357,29 @@ osscir_status tune_kernel(osscir_batch* b, int k, int persistent_grid, cudaEvent
             *cgrid = g;
             *corder = o;
             float ms;
-            CKS(time_kernel(b, k, c, t0, t1, &ms));
+            CKS(time_config(b, k, c, t0, t1, &ms));
             if (ms < best_ms) {
                 best_ms = ms;
-                *grid = g;
-                *order = o;
+                best = c;
             }
         }
     if (k != 1) {
         c = best;
-        const int tiles[4] = {1, 2, 4, 8};
+        const int views[4] = {1, 2, 4, 8};
         const int txs[4] = {4, 8, 16, 32};
         for (int i = 0; i < 4; ++i) {
             if (k == 0) {
-                if (tiles[i] == best.proj_views) continue;
-                c.proj_views = tiles[i];
+                if (views[i] == best.proj_views) continue;
+                c.proj_views = views[i];
                 int per_sm = 0;
-                CK(batch_resident_ctas(0, 32 * tiles[i], &per_sm));
+                CK(batch_resident_ctas(0, 32 * views[i], &per_sm));
                 if (c.proj_grid > 0) c.proj_grid = std::max(1, per_sm) * b->sms;
             } else {
                 if (txs[i] == best.bp_tile_x) continue;
                 c.bp_tile_x = txs[i];
             }
             float ms;
-            CKS(time_kernel(b, k, c, t0, t1, &ms));
+            CKS(time_config(b, k, c, t0, t1, &ms));
             if (ms < best_ms) {
                 best_ms = ms;
                 best = c;
@@ -267,30 +390,47 @@ osscir_status tune_kernel(osscir_batch* b, int k, int persistent_grid, cudaEvent
     return OSSCIR_OK;
 }
 
+// Whole iterations with 1, 2 and 4 branches at the tuned kernel settings.
+osscir_status tune_branches(osscir_batch* b, cudaEvent_t t0, cudaEvent_t t1) {
+    osscir_batch_config best = b->cfg, c = b->cfg;
+    float best_ms = 3.0e38f;
+    for (int br = 1; br <= kMaxBranches && br <= (int)b->ctx.size(); br *= 2) {
+        c.branches = br;
+        float ms;
+        CKS(time_config(b, 3, c, t0, t1, &ms));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    b->cfg = best;
+    return OSSCIR_OK;
+}
+
 osscir_status autotune(osscir_batch* b) {
     // every solve's state (x_n, xbar_n, y_n) is saved and put back afterwards;
-    // g, b, S and the D_TPL partials are recomputed by the next iteration
+    // g, b, S, the D_TPL partials and D_TPL itself are recomputed by the next iteration
     size_t total = 0;
-    for (const osscir_ctx* h : b->ctx) total += sizeof(float4) * (2 * (size_t)h->P + h->L);
+    for (const osscir_ctx* h : b->ctx) total += sizeof(float4) * (2 * (size_t)h->P + h->L) + sizeof(double);
     char* save = nullptr;
     CK(cudaMalloc(reinterpret_cast<void**>(&save), total));
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     osscir_status s = OSSCIR_OK;
+    cudaStream_t st = b->lanes.main;
     auto copy_state = [&](bool out) -> cudaError_t {
         size_t off = 0;
         for (osscir_ctx* h : b->ctx) {
-            void* buf[3] = {h->x, h->xbar, h->y};
-            const size_t sz[3] = {sizeof(float4) * h->P, sizeof(float4) * h->P, sizeof(float4) * h->L};
-            for (int i = 0; i < 3; ++i) {
-                const cudaError_t e = out ? cudaMemcpyAsync(save + off, buf[i], sz[i], cudaMemcpyDeviceToDevice,
-                                                            b->cap_stream)
-                                          : cudaMemcpyAsync(buf[i], save + off, sz[i], cudaMemcpyDeviceToDevice,
-                                                            b->cap_stream);
+            void* buf[4] = {h->x, h->xbar, h->y, h->dtpl_out + 1};
+            const size_t sz[4] = {sizeof(float4) * h->P, sizeof(float4) * h->P, sizeof(float4) * h->L,
+                                  sizeof(double)};
+            for (int i = 0; i < 4; ++i) {
+                const cudaError_t e = out ? cudaMemcpyAsync(save + off, buf[i], sz[i], cudaMemcpyDeviceToDevice, st)
+                                          : cudaMemcpyAsync(buf[i], save + off, sz[i], cudaMemcpyDeviceToDevice, st);
                 if (e != cudaSuccess) return e;
                 off += sz[i];
             }
         }
-        return cudaStreamSynchronize(b->cap_stream);
+        return cudaStreamSynchronize(st);
     };
     cudaError_t e = copy_state(true);
     if (e == cudaSuccess) e = cudaEventCreate(&t0);
@@ -306,6 +446,7 @@ osscir_status autotune(osscir_batch* b) {
         }
         s = tune_kernel(b, k, std::max(1, per_sm) * b->sms, t0, t1);
     }
+    if (s == OSSCIR_OK) s = tune_branches(b, t0, t1);
     e = copy_state(false);
     if (s == OSSCIR_OK && e != cudaSuccess) s = from_cuda(e);
     if (t0) cudaEventDestroy(t0);
@@ -315,6 +456,103 @@ osscir_status autotune(osscir_batch* b) {
 }
 
 }  // namespace
+
+// ------------------------------------------------------------------ batch runner (served form)
+
+namespace osscir {
+
+struct BatchRun {
+    std::vector<osscir_ctx*> ctx;
+    Plan plan;
+    char* dev = nullptr;
+    size_t cap = 0;
+    char* stage[2] = {nullptr, nullptr};   // pinned staging, used alternately
+    size_t cap_stage[2] = {0, 0};
+    cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+    bool stage_used[2] = {false, false};
+    int next = 0;
+    Lanes lanes;
+    bool lanes_ok = false;
+    cudaGraphExec_t gexec = nullptr;    // one iteration
+    cudaGraphExec_t ground = nullptr;   // kRound iterations, branches skewed
+};
+
+constexpr int kRound = 4;
+
+BatchRun* batchrun_new() { return new (std::nothrow) BatchRun(); }
+
+void batchrun_free(BatchRun* r) {
+    if (!r) return;
+    if (r->gexec) cudaGraphExecDestroy(r->gexec);
+    if (r->ground) cudaGraphExecDestroy(r->ground);
+    r->lanes.destroy();
+    cudaDeviceSynchronize();
+    if (r->dev) cudaFree(r->dev);
+    for (int i = 0; i < 2; ++i) {
+        if (r->stage[i]) cudaFreeHost(r->stage[i]);
+        if (r->stage_ev[i]) cudaEventDestroy(r->stage_ev[i]);
+    }
+    delete r;
+}
+
+double batch_solve_cost(const osscir_ctx* h) { return solve_cost(h); }
+
+osscir_status batchrun_set(BatchRun* r, const std::vector<osscir_ctx*>& ctx, int branches, cudaStream_t st) {
+    r->ctx = ctx;
+    if (ctx.empty()) return OSSCIR_OK;
+    if (branches < 1 || branches > kMaxBranches || (branches & (branches - 1))) return OSSCIR_E_INVALID;
+    if (!r->lanes_ok) {
+        CK(r->lanes.create());
+        r->lanes_ok = true;
+    }
+    osscir_batch_config c = kDefault;
+    c.branches = branches;
+    make_plan(ctx, c, r->plan);
+    const size_t bytes = r->plan.image.size();
+    // device image: grown in stream order, so changing the batch never stalls the device
+    if (bytes > r->cap) {
+        const size_t n = std::max(bytes, 2 * r->cap);
+        if (r->dev) CK(cudaFreeAsync(r->dev, st));
+        r->dev = nullptr;
+        r->cap = 0;
+        CK(cudaMallocAsync(reinterpret_cast<void**>(&r->dev), n, st));
+        r->cap = n;
+    }
+    // staging buffer: wait until the copy that last read it has run
+    const int b = r->next;
+    r->next ^= 1;
+    if (!r->stage_ev[b]) CK(cudaEventCreateWithFlags(&r->stage_ev[b], cudaEventDisableTiming));
+    if (r->stage_used[b]) CK(cudaEventSynchronize(r->stage_ev[b]));
+    if (bytes > r->cap_stage[b]) {
+        if (r->stage[b]) CK(cudaFreeHost(r->stage[b]));
+        r->stage[b] = nullptr;
+        r->cap_stage[b] = 0;
+        CK(cudaHostAlloc(reinterpret_cast<void**>(&r->stage[b]), bytes, cudaHostAllocDefault));
+        r->cap_stage[b] = bytes;
+    }
+    std::memcpy(r->stage[b], r->plan.image.data(), bytes);
+    CK(cudaMemcpyAsync(r->dev, r->stage[b], bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(r->stage_ev[b], st));
+    r->stage_used[b] = true;
+    // an executable graph still in flight is released when it completes
+    if (r->gexec) cudaGraphExecDestroy(r->gexec);
+    if (r->ground) cudaGraphExecDestroy(r->ground);
+    r->gexec = r->ground = nullptr;
+    CKS(capture_plan(r->plan, r->dev, c, r->lanes, nullptr, &r->gexec));
+    return capture_plan(r->plan, r->dev, c, r->lanes, nullptr, &r->ground, kRound, r->plan.branches > 1);
+}
+
+osscir_status batchrun_step(BatchRun* r, int n_iters, cudaStream_t st) {
+    if (r->ctx.empty() || n_iters <= 0) return OSSCIR_OK;
+    if (!r->gexec || !r->ground) return OSSCIR_E_INVALID;
+    int i = 0;
+    for (; i + kRound <= n_iters; i += kRound) CK(cudaGraphLaunch(r->ground, st));
+    for (; i < n_iters; ++i) CK(cudaGraphLaunch(r->gexec, st));
+    for (osscir_ctx* h : r->ctx) h->iter += n_iters;
+    return OSSCIR_OK;
+}
+
+}  // namespace osscir
 
 extern "C" {
 
@@ -332,30 +570,24 @@ osscir_status osscir_batch_create(const osscir_t* solves, int n, int autotune_fl
     CK(cudaGetDevice(&dev));
     for (osscir_ctx* h : v)
         if (h->device != dev) return OSSCIR_E_INVALID;
+    // work already queued on the solves (on any stream) must be done before the
+    // autotuner saves their state
+    CK(cudaDeviceSynchronize());
 
     osscir_batch* b = new (std::nothrow) osscir_batch();
     if (!b) return OSSCIR_E_NOMEM;
     b->device = dev;
     b->ctx = std::move(v);
     b->cfg = kDefault;
-    auto fail = [&](osscir_status s) {
+    osscir_status s = from_cuda(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
+    if (s == OSSCIR_OK) s = from_cuda(b->lanes.create());
+    for (int i = 0; i < 4 && s == OSSCIR_OK; ++i) s = from_cuda(cudaEventCreate(&b->ev[i]));
+    if (s == OSSCIR_OK && autotune_flag) s = autotune(b);
+    if (s == OSSCIR_OK) s = rebuild(b);
+    if (s != OSSCIR_OK) {
         free_batch(b);
         return s;
-    };
-    auto ck = [&](cudaError_t e) { return from_cuda(e); };
-    osscir_status s = ck(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
-    if (s == OSSCIR_OK) s = ck(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
-    for (int i = 0; i < 4 && s == OSSCIR_OK; ++i) s = ck(cudaEventCreate(&b->ev[i]));
-    if (s == OSSCIR_OK) s = ck(cudaMalloc(reinterpret_cast<void**>(&b->desc), sizeof(SolveDesc) * n));
-    if (s == OSSCIR_OK) {
-        std::vector<SolveDesc> d(n);
-        for (int i = 0; i < n; ++i) d[i] = make_desc(b->ctx[i]);
-        s = ck(cudaMemcpy(b->desc, d.data(), sizeof(SolveDesc) * n, cudaMemcpyHostToDevice));
     }
-    if (s == OSSCIR_OK && autotune_flag) s = autotune(b);
-    if (s == OSSCIR_OK) s = build_all_items(b);
-    if (s == OSSCIR_OK) s = capture(b);
-    if (s != OSSCIR_OK) return fail(s);
     *out = b;
     return OSSCIR_OK;
 }
@@ -382,8 +614,7 @@ osscir_status osscir_batch_set_config(osscir_batch_t b, const osscir_batch_confi
     if (!b || !cfg || !valid_config(*cfg)) return OSSCIR_E_INVALID;
     CK(cudaDeviceSynchronize());   // no launch of the old work lists may still be in flight
     b->cfg = *cfg;
-    CKS(build_all_items(b));
-    return capture(b);
+    return rebuild(b);
 }
 
 osscir_status osscir_batch_last_kernel_ms(osscir_batch_t b, float* ms, void* stream) {

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <vector>
 
 #include "../../include/osscir.h"
 #include "osscir_launch.h"
@@ -58,5 +59,19 @@ osscir_status ctx_validate(const osscir_geometry* geom, const osscir_spectra* sp
                            const osscir_params* params);
 // Capture the per-iteration graph once.
 osscir_status ctx_ensure_graph(osscir_ctx* h);
+
+// Batch runner for the served form: the batched kernels over a set of contexts
+// that changes over time, with all updates in stream order on one stream.
+struct BatchRun;
+BatchRun* batchrun_new();
+void batchrun_free(BatchRun* r);   // synchronises the device
+// Make ctx the batch, split into `branches` (1, 2 or 4) graph branches
+// (descriptors, work lists and the iteration graphs are rebuilt; device
+// buffers grow with stream-ordered allocation on st).
+osscir_status batchrun_set(BatchRun* r, const std::vector<osscir_ctx*>& ctx, int branches, cudaStream_t st);
+// Relative device time of one MOCCA iteration of a context (for load balancing).
+double batch_solve_cost(const osscir_ctx* h);
+// Enqueue n_iters MOCCA iterations of every solve of the batch on st.
+osscir_status batchrun_step(BatchRun* r, int n_iters, cudaStream_t st);
 
 }  // namespace osscir

@@ -1,9 +1,13 @@
 // Served form of the library (include/osscir.h, "served form"): a worker
 // thread admits queued reconstruction requests into slots under a device
-// memory budget and runs each admitted request's MOCCA iterations on its own
-// stream, so requests that arrive while others are on the GPU join the work
-// in flight (continuous batching).  Contexts are cached by configuration and
-// reused; a request's arithmetic is exactly that of the plain form.
+// memory budget.  Admitted requests are spread over a few groups of about
+// equal work; each group is a batch on its own stream that advances all its
+// requests together, a few MOCCA iterations per round, through the batched
+// kernels (one launch per kernel per iteration for the whole group), while the
+// groups run side by side.  A group's batch is re-formed between its rounds as
+// requests finish and new ones join (continuous batching at iteration
+// granularity).  Contexts are cached by configuration and reused; a request's
+// arithmetic is exactly that of the plain form.
 #include <chrono>
 #include <condition_variable>
 #include <cmath>
@@ -72,24 +76,23 @@ struct Ticket {
     float gpu_ms = 0.f;
 };
 
-constexpr int kChunk = 4;      // MOCCA iterations per enqueued chunk
-constexpr int kInFlight = 2;   // chunks queued per stream at a time
+constexpr int kChunk = 4;      // MOCCA iterations per round (fewer if a request needs fewer)
+constexpr int kInFlight = 2;   // rounds queued per group at a time
+constexpr int kGroups = 4;     // batches running side by side, each on its own stream
 
 struct Slot {
     osscir_ctx* ctx = nullptr;
     Config cfg;
     uint64_t key = 0;
-    cudaStream_t stream = nullptr;
     float* h_counts = nullptr;   // pinned
     float* h_maps = nullptr;     // pinned
     double* h_dtpl = nullptr;    // pinned
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    cudaEvent_t evc[kInFlight] = {nullptr, nullptr};
     Ticket* running = nullptr;
-    int enq = 0;        // iterations enqueued
-    int head = 0;       // oldest chunk event in flight
-    int in_flight = 0;  // chunks in flight
-    bool tail = false;  // results copy-back enqueued
+    int group = 0;       // the batch it runs in
+    double cost = 0.0;   // relative device time of one iteration
+    int remaining = 0;   // iterations not yet enqueued
+    bool tail = false;   // results copy-back enqueued
     bool failed = false;
     uint64_t last_used = 0;
     size_t bytes = 0;
@@ -104,13 +107,9 @@ size_t estimate_bytes(const Config& c) {
 }
 
 void release_slot(Slot* s) {
-    if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->ctx) osscir::ctx_destroy(s->ctx);
-    if (s->stream) cudaStreamDestroy(s->stream);
     if (s->ev0) cudaEventDestroy(s->ev0);
     if (s->ev1) cudaEventDestroy(s->ev1);
-    for (cudaEvent_t e : s->evc)
-        if (e) cudaEventDestroy(e);
     if (s->h_counts) cudaFreeHost(s->h_counts);
     if (s->h_maps) cudaFreeHost(s->h_maps);
     if (s->h_dtpl) cudaFreeHost(s->h_dtpl);
@@ -133,12 +132,23 @@ struct osscir_server {
     bool stop = false;
     uint64_t next_id = 1, clock = 0;
     std::thread worker;
+    // worker-thread state: per group its stream, batch and rounds in flight
+    struct Group {
+        cudaStream_t stream = nullptr;
+        osscir::BatchRun* batch = nullptr;
+        std::vector<osscir_ctx*> members;
+        std::deque<cudaEvent_t> rounds;
+        double load = 0.0;
+    };
+    Group groups[kGroups];
+    std::deque<cudaEvent_t> spare;
 
     void run();
-    Slot* acquire(Ticket* t);   // with mu held
-    bool begin(Slot* s);        // worker thread, no lock
-    bool advance(Slot* s);      // worker thread, no lock; true if anything happened
-    void finish(Slot* s);       // with mu held
+    Slot* acquire(Ticket* t);     // with mu held
+    bool begin(Slot* s);          // worker thread, no lock
+    bool enqueue_round(int g);    // worker thread, no lock
+    bool enqueue_tail(Slot* s);   // worker thread, no lock
+    void finish(Slot* s);         // with mu held
 };
 
 // An idle cached context of the same configuration, or a new one once memory
@@ -151,6 +161,7 @@ Slot* osscir_server::acquire(Ticket* t) {
         for (Slot* s : slots)
             if (!s->running && (!victim || s->last_used < victim->last_used)) victim = s;
         if (!victim) return nullptr;
+        for (Group& g : groups) g.members.clear();   // a new context may reuse the address: re-form the batches
         slots.remove(victim);
         bytes_in_use -= victim->bytes;
         release_slot(victim);
@@ -162,15 +173,11 @@ Slot* osscir_server::acquire(Ticket* t) {
     osscir_spectra sp{t->cfg.nE, t->cfg.s.data(), t->cfg.N.data()};
     osscir_status st = osscir::ctx_create(&t->cfg.geom, &sp, t->cfg.mu.data(), &t->cfg.params, &s->ctx);
     const size_t L = (size_t)t->cfg.geom.n_views * t->cfg.geom.n_bins, P = (size_t)t->cfg.geom.n * t->cfg.geom.n;
-    if (st == OSSCIR_OK && (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
-                            cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess ||
-                            cudaEventCreateWithFlags(&s->evc[0], cudaEventDisableTiming) != cudaSuccess ||
-                            cudaEventCreateWithFlags(&s->evc[1], cudaEventDisableTiming) != cudaSuccess ||
+    if (st == OSSCIR_OK && (cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess ||
                             cudaHostAlloc(&s->h_counts, L * 16, cudaHostAllocDefault) != cudaSuccess ||
                             cudaHostAlloc(&s->h_maps, P * 16, cudaHostAllocDefault) != cudaSuccess ||
                             cudaHostAlloc(&s->h_dtpl, sizeof(double), cudaHostAllocDefault) != cudaSuccess))
         st = OSSCIR_E_NOMEM;
-    if (st == OSSCIR_OK) st = osscir::ctx_ensure_graph(s->ctx);
     if (st != OSSCIR_OK) {
         release_slot(s);
         t->status = st;
@@ -182,13 +189,13 @@ Slot* osscir_server::acquire(Ticket* t) {
     return s;
 }
 
-// Copy the counts in and reset the state (the iterations follow in chunks).
+// Copy the counts in and reset the state (the iterations follow in rounds).
 bool osscir_server::begin(Slot* s) {
     Ticket* t = s->running;
     osscir_ctx* h = s->ctx;
     std::memcpy(s->h_counts, t->counts.data(), t->counts.size() * sizeof(float));
-    cudaStream_t st = s->stream;
-    s->enq = s->head = s->in_flight = 0;
+    cudaStream_t st = groups[s->group].stream;
+    s->remaining = t->n_iters;
     s->tail = s->failed = false;
     h->iter = 0;
     return cudaEventRecord(s->ev0, st) == cudaSuccess &&
@@ -199,49 +206,72 @@ bool osscir_server::begin(Slot* s) {
            cudaMemsetAsync(h->dtpl_out, 0, sizeof(double) * 2, st) == cudaSuccess;
 }
 
-// Keep at most kInFlight chunks of kChunk iterations queued on the slot's
-// stream, then the copy-back of the results; returns true if it did anything.
-bool osscir_server::advance(Slot* s) {
-    Ticket* t = s->running;
+// Results of a request whose iterations are all enqueued: maps and D_TPL back
+// to pinned host memory, then its completion event.
+bool osscir_server::enqueue_tail(Slot* s) {
     osscir_ctx* h = s->ctx;
-    bool acted = false;
-    while (s->in_flight > 0) {
-        const cudaError_t q = cudaEventQuery(s->evc[s->head]);
-        if (q == cudaErrorNotReady) break;
-        if (q != cudaSuccess) s->failed = true;
-        s->head = (s->head + 1) % kInFlight;
-        --s->in_flight;
-        acted = true;
+    cudaStream_t stream = groups[s->group].stream;
+    const bool ok =
+        cudaMemcpyAsync(s->h_maps, h->x, sizeof(float4) * h->P, cudaMemcpyDeviceToHost, stream) == cudaSuccess &&
+        cudaMemcpyAsync(s->h_dtpl, h->dtpl_out + 1, sizeof(double), cudaMemcpyDeviceToHost, stream) == cudaSuccess &&
+        cudaEventRecord(s->ev1, stream) == cudaSuccess;
+    s->tail = true;
+    return ok;
+}
+
+// One round of group g: every running request of the group that still has
+// iterations to do advances by k = min(kChunk, fewest remaining) iterations in
+// the batched kernels; the group's batch is re-formed first if its members
+// changed.  False if nothing was enqueued.
+bool osscir_server::enqueue_round(int g) {
+    Group& G = groups[g];
+    std::vector<osscir_ctx*> active;
+    std::vector<Slot*> act;
+    int k = kChunk;
+    for (Slot* s : slots)
+        if (s->running && s->group == g && !s->failed && !s->tail && s->remaining > 0) {
+            active.push_back(s->ctx);
+            act.push_back(s);
+            k = std::min(k, s->remaining);
+        }
+    if (act.empty()) return false;
+    osscir_status st = OSSCIR_OK;
+    if (active != G.members) {
+        st = osscir::batchrun_set(G.batch, active, 1, G.stream);
+        G.members = active;
     }
-    while (!s->tail && !s->failed && s->in_flight < kInFlight && s->enq < t->n_iters) {
-        const int k = std::min(kChunk, t->n_iters - s->enq);
-        bool ok = true;
-        for (int i = 0; ok && i < k; ++i) ok = cudaGraphLaunch(h->gexec, s->stream) == cudaSuccess;
-        ok = ok && cudaEventRecord(s->evc[(s->head + s->in_flight) % kInFlight], s->stream) == cudaSuccess;
-        if (!ok) s->failed = true;
-        ++s->in_flight;
-        s->enq += k;
-        acted = true;
+    if (st == OSSCIR_OK) st = osscir::batchrun_step(G.batch, k, G.stream);
+    cudaEvent_t ev = nullptr;
+    if (!spare.empty()) {
+        ev = spare.front();
+        spare.pop_front();
+    } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        ev = nullptr;
     }
-    if (!s->tail && (s->enq >= t->n_iters || s->failed)) {
-        const bool ok =
-            cudaMemcpyAsync(s->h_maps, h->x, sizeof(float4) * h->P, cudaMemcpyDeviceToHost, s->stream) == cudaSuccess &&
-            cudaMemcpyAsync(s->h_dtpl, h->dtpl_out + 1, sizeof(double), cudaMemcpyDeviceToHost, s->stream) ==
-                cudaSuccess &&
-            cudaEventRecord(s->ev1, s->stream) == cudaSuccess;
-        if (!ok) s->failed = true;
-        h->iter = s->enq;
-        s->tail = true;
-        acted = true;
+    if (st == OSSCIR_OK && ev && cudaEventRecord(ev, G.stream) == cudaSuccess) {
+        G.rounds.push_back(ev);
+    } else {
+        if (ev) spare.push_back(ev);
+        st = OSSCIR_E_CUDA;
     }
-    return acted;
+    for (Slot* s : act) {
+        if (st != OSSCIR_OK) {
+            s->failed = true;
+            G.members.clear();   // the batch must be rebuilt before it is used again
+            continue;
+        }
+        s->remaining -= k;
+        if (s->remaining == 0 && !enqueue_tail(s)) s->failed = true;
+    }
+    return true;
 }
 
 void osscir_server::finish(Slot* s) {
     Ticket* t = s->running;
     const osscir_ctx* h = s->ctx;
+    groups[s->group].load -= s->cost;
     if (s->failed) {
-        cudaStreamSynchronize(s->stream);
+        cudaStreamSynchronize(groups[s->group].stream);
         t->status = OSSCIR_E_CUDA;
         t->t_done = clk::now();
         t->done = true;
@@ -249,6 +279,7 @@ void osscir_server::finish(Slot* s) {
         --running;
         return;
     }
+    s->ctx->iter = t->n_iters;
     t->maps.assign(s->h_maps, s->h_maps + (size_t)h->P * 4);
     t->dtpl = *s->h_dtpl;
     float ms = 0.f;
@@ -268,6 +299,12 @@ void osscir_server::finish(Slot* s) {
 
 void osscir_server::run() {
     cudaSetDevice(device);
+    bool dead = false;
+    for (Group& g : groups) {
+        dead = dead || cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess;
+        g.batch = osscir::batchrun_new();
+        dead = dead || !g.batch;
+    }
     std::vector<Slot*> started;
     while (true) {
         started.clear();
@@ -277,10 +314,11 @@ void osscir_server::run() {
             // admissions, first come first served, while a slot and the memory budget allow
             while (!stop && !queue.empty() && running < max_slots) {
                 Ticket* t = queue.front();
-                Slot* s = acquire(t);
+                Slot* s = dead ? reinterpret_cast<Slot*>(-1) : acquire(t);
                 if (!s) break;   // wait for memory
                 queue.pop_front();
                 if (s == reinterpret_cast<Slot*>(-1)) {
+                    if (dead) t->status = OSSCIR_E_CUDA;
                     t->t_start = t->t_done = clk::now();
                     t->done = true;
                     cv_done.notify_all();
@@ -288,19 +326,38 @@ void osscir_server::run() {
                 }
                 s->running = t;
                 s->last_used = ++clock;
+                s->cost = osscir::batch_solve_cost(s->ctx);
+                s->group = 0;
+                for (int g = 1; g < kGroups; ++g)
+                    if (groups[g].load < groups[s->group].load) s->group = g;
+                groups[s->group].load += s->cost;
                 t->t_start = clk::now();
                 ++running;
                 started.push_back(s);
             }
         }
-        // CUDA work without the lock: the worker thread alone touches the slots' streams
+        // CUDA work without the lock: the worker thread alone touches the stream and the batch
         bool acted = !started.empty();
         for (Slot* s : started)
             if (!begin(s)) s->failed = true;
+        for (int g = 0; g < kGroups; ++g) {
+            std::deque<cudaEvent_t>& rounds = groups[g].rounds;
+            while (!rounds.empty()) {
+                const cudaError_t q = cudaEventQuery(rounds.front());
+                if (q == cudaErrorNotReady) break;
+                spare.push_back(rounds.front());
+                rounds.pop_front();
+                acted = true;
+            }
+            while ((int)rounds.size() < kInFlight && enqueue_round(g)) acted = true;
+        }
         std::vector<Slot*> done;
         for (Slot* s : slots) {
             if (!s->running) continue;
-            if (advance(s)) acted = true;
+            if (!s->tail && (s->failed || s->remaining == 0)) {
+                if (!enqueue_tail(s)) s->failed = true;
+                acted = true;
+            }
             if (s->tail) {
                 const cudaError_t q = cudaEventQuery(s->ev1);
                 if (q == cudaErrorNotReady) continue;
@@ -319,6 +376,17 @@ void osscir_server::run() {
             else if (!stop && queue.empty()) cv_work.wait(lock);
         }
     }
+    for (Group& g : groups) {
+        if (g.stream) cudaStreamSynchronize(g.stream);
+        for (cudaEvent_t e : g.rounds) cudaEventDestroy(e);
+        g.rounds.clear();
+        osscir::batchrun_free(g.batch);
+        g.batch = nullptr;
+        if (g.stream) cudaStreamDestroy(g.stream);
+        g.stream = nullptr;
+    }
+    for (cudaEvent_t e : spare) cudaEventDestroy(e);
+    spare.clear();
 }
 
 extern "C" {

@@ -96,7 +96,7 @@ def test_batch_calls_reject_invalid_arguments(lib):
     assert lib.osscir_batch_create(fake, 1, 2, ct.byref(out)) == _lib.OSSCIR_E_INVALID
     assert out.value is None
     assert lib.osscir_batch_step(null, 1, None) == _lib.OSSCIR_E_INVALID
-    cfg = _lib.BatchConfig(4, 0, 0, 0, 0, 8, 0, 0)
+    cfg = _lib.BatchConfig(4, 0, 0, 0, 0, 8, 0, 0, 1)
     assert lib.osscir_batch_get_config(null, ct.byref(cfg)) == _lib.OSSCIR_E_INVALID
     assert lib.osscir_batch_set_config(null, ct.byref(cfg)) == _lib.OSSCIR_E_INVALID
     assert lib.osscir_batch_destroy(null) == _lib.OSSCIR_OK

@@ -98,10 +98,12 @@ def test_batch_equals_plain(solves):
 
 
 CONFIGS = [
-    dict(proj_views=1, proj_grid=0, proj_order=1, ray_grid=0, ray_order=2, bp_tile_x=4, bp_grid=0, bp_order=1),
+    dict(proj_views=1, proj_grid=0, proj_order=1, ray_grid=0, ray_order=2, bp_tile_x=4, bp_grid=0, bp_order=1,
+         branches=2),
     dict(proj_views=8, proj_grid=152, proj_order=2, ray_grid=300, ray_order=0, bp_tile_x=32, bp_grid=304,
-         bp_order=2),
-    dict(proj_views=2, proj_grid=7, proj_order=0, ray_grid=5, ray_order=1, bp_tile_x=16, bp_grid=3, bp_order=0),
+         bp_order=2, branches=4),
+    dict(proj_views=2, proj_grid=7, proj_order=0, ray_grid=5, ray_order=1, bp_tile_x=16, bp_grid=3, bp_order=0,
+         branches=1),
 ]
 
 
@@ -134,8 +136,11 @@ def test_autotune_keeps_state_and_results(solves):
     B.step(n_it - 2)
     for (R, _, _), r in zip(solves, ref):
         _same(_result(R), r)
+    assert cfg["branches"] in (1, 2, 4)
     with pytest.raises(_lib.OsscirError):
         B.config = dict(cfg, proj_views=3)
+    with pytest.raises(_lib.OsscirError):
+        B.config = dict(cfg, branches=3)
     B.close()
 
 
