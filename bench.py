@@ -260,6 +260,7 @@ def run_gpu(args):
 
     served = run_served(args, w, R, chat, rank) if args.served > 0 else None
     batched = run_batched(args, rank) if args.batch > 0 else None
+    mixed = run_served_mixed(args, rank) if args.mixed > 0 else None
 
     if rank != 0:
         return 0
@@ -305,6 +306,7 @@ def run_gpu(args):
         "plain_recon_per_s": e2e_rate / SOLVE_ITERS,
         "served": served,
         "batched": batched,
+        "served_mixed": mixed,
         "clocks": clk.summary(),
         "gpu_launches": 4 * args.steps,
         "dtpl_last": d_last,
@@ -440,7 +442,78 @@ def run_served(args, w, R, chat, rank):
             "p99_ms": float(np.percentile(lat_p, 99)), "poisson_recon_per_s": args.served / wall_p,
             "requests": args.served, "slots": args.slots, "all_ok": bool(ok_b and ok_p),
             "note": "burst of requests for throughput; seeded Poisson arrivals below capacity for latency; "
-                    "150 GB budget; one stream per admitted request"}
+                    "150 GB budget; admitted requests batched in up to 4 groups, one stream each"}
+
+
+def run_served_mixed(args, rank):
+    """Mixed requests (128^2-512^2, 90-1024 views, 200-500 iterations, 1e4-1e6
+    photons per ray) at seeded Poisson arrival rates, through a fresh server
+    (150 GB budget, args.slots slots, no cached contexts) per rate, beside the
+    plain per-solve form (create, load, iterate, read back, release, one request
+    after another) on the same requests."""
+    import numpy as np
+    import torch
+
+    from paper_1801_06263_gb300 import Reconstructor, _lib, inputs
+    reqs = inputs.served_requests(args.mixed, seed=3000 + rank)
+    counts = []
+    for w in reqs:
+        lam = inputs.step_ratio(w.geom.n, w.photons_per_ray)
+        R = Reconstructor(w.geom, w.spectra, lam)
+        f4 = torch.zeros((w.geom.n_pixels, 4), dtype=torch.float32, device="cuda")
+        f4[:, :3] = torch.tensor(w.f_true, dtype=torch.float32, device="cuda")
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(w.noise_seed)
+        counts.append(torch.poisson(R.simulate(f4), generator=gen).cpu().numpy())
+        R.close()
+    lams = [inputs.step_ratio(w.geom.n, w.photons_per_ray) for w in reqs]
+    total_iters = sum(w.n_iters for w in reqs)
+
+    # plain per-solve form, one request after another
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for w, c, lam in zip(reqs, counts, lams):
+        R = Reconstructor(w.geom, w.spectra, lam)
+        c_host = torch.from_numpy(c).pin_memory()
+        out = torch.empty((w.geom.n_pixels, 4), dtype=torch.float32).pin_memory()
+        _lib.osscir_reconstruct(R.handle, c_host, w.n_iters, out)
+        R.close()
+    plain_s = time.perf_counter() - t0
+
+    rates = {}
+    for rate in args.mixed_rates:
+        gaps = np.random.default_rng(4000 + rank + int(rate)).exponential(1.0 / rate, size=len(reqs))
+        srv = _lib.osscir_server_create(150 << 30, args.slots)
+        try:
+            t0 = time.perf_counter()
+            tickets = []
+            for k, (w, c, lam) in enumerate(zip(reqs, counts, lams)):
+                target = t0 + float(np.sum(gaps[:k]))
+                while time.perf_counter() < target:
+                    time.sleep(min(0.0005, max(0.0, target - time.perf_counter())))
+                sp = w.spectra
+                tickets.append(_lib.osscir_submit(srv, w.geom, sp.s, sp.N, sp.mu, lam, c, w.n_iters))
+            lat, ok = [], True
+            for t in tickets:
+                rc, st = _lib.osscir_poll(srv, t, -1)
+                ok = ok and rc == 0
+                lat.append(st.latency_ms)
+            wall = time.perf_counter() - t0
+        finally:
+            _lib.osscir_server_destroy(srv)
+        lat = np.array(lat)
+        rates[str(rate)] = {"recon_per_s": len(reqs) / wall, "iters_per_s": total_iters / wall,
+                            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                            "all_ok": bool(ok)}
+    mix = {}
+    for w in reqs:
+        mix[w.geom.n] = mix.get(w.geom.n, 0) + 1
+    return {"requests": len(reqs), "image_sizes": {str(k): v for k, v in sorted(mix.items())},
+            "views": [min(w.geom.n_views for w in reqs), max(w.geom.n_views for w in reqs)],
+            "iterations": total_iters, "slots": args.slots, "budget_GB": 150,
+            "plain_recon_per_s": len(reqs) / plain_s, "plain_iters_per_s": total_iters / plain_s,
+            "served_by_rate": rates,
+            "note": "wall-clock from first submit to last result; context creation included on both sides"}
 
 
 def main():
@@ -454,6 +527,9 @@ def main():
     ap.add_argument("--served", type=int, default=16, help="requests for the served measurement (0: skip)")
     ap.add_argument("--slots", type=int, default=4, help="server slots")
     ap.add_argument("--batch", type=int, default=64, help="solves in the batched measurement (0: skip)")
+    ap.add_argument("--mixed", type=int, default=16, help="mixed requests in the served sweep (0: skip)")
+    ap.add_argument("--mixed-rates", type=float, nargs="+", default=[5.0, 10.0, 20.0, 50.0],
+                    help="Poisson arrival rates of the mixed served sweep, requests/s")
     ap.add_argument("--batch-steps", type=int, default=5, help="timed iterations of the batched measurement")
     ap.add_argument("--rate", type=float, default=1.5, help="Poisson request arrival rate, requests/s")
     args = ap.parse_args()

@@ -317,6 +317,24 @@ def batch_workloads(n_solves: int = 64, seed: int = 4000) -> list:
     return out
 
 
+def served_requests(n_requests: int = 16, seed: int = 3000) -> list:
+    """A stream of mixed reconstruction requests for the served form: n from
+    {128, 192, 256, 384, 512} (0.5 mm pixels), views uniform in [90, 1024] with
+    as many detector bins, dose log-uniform in [1e4, 1e6] photons per ray,
+    iterations uniform in [200, 500], their own ellipse phantom and noise seed."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_requests):
+        n = int(rng.choice([128, 192, 256, 384, 512]))
+        views = int(rng.integers(90, 1025))
+        photons = float(10.0 ** rng.uniform(4.0, 6.0))
+        iters = int(rng.integers(200, 501))
+        g = make_geometry(n, 0.5, views, views)
+        out.append(Workload(f"request_{i}", g, make_spectra(views, photons), ellipse_phantom(g, seed + 100 + i),
+                            photons, seed + 200 + i, iters))
+    return out
+
+
 def random_state(geom: Geometry, seed: int, scale: float = 1.0):
     """Seeded random image (float [P,3]) and dual (float [L,4]) for projector tests."""
     rng = np.random.default_rng(seed)
