@@ -193,16 +193,23 @@ __device__ __forceinline__ void ray_chords(const float4& r0, float ex, float ey,
 }
 
 // X_{l,k} for every pixel of ray l with a nonzero weight: visit(k, w).  The
-// same slab enumeration as ray_chords, specialised on the dominant axis and
-// the signs of the direction (so the planes need no ordering at run time) and
-// unrolled over the at most three cells a slab can contribute (|slope| <= 1 and
-// margin < h/2); every weight equals x_weight's bit for bit.
-template <bool ROWS, bool PX, bool PY, class Visit>
-__device__ __forceinline__ void ray_weights_dir(const float4& r0, float ex, float ey, const GridF& G, float margin,
-                                                const ExcTable& E, int l, Visit&& visit) {
-    const float bM = ROWS ? r0.y : r0.x, bm = ROWS ? r0.x : r0.y;
-    const float iM = ROWS ? r0.w : r0.z, im = ROWS ? r0.z : r0.w;
-    const float slope = iM / im;
+// same slab enumeration as ray_chords, written once in (major, minor)
+// coordinates: the membership test is symmetric under exchanging the x and y
+// roles (fminf, fmaxf and chord_bound commute with the exchange), so one code
+// path serves both orientations and both direction signs, and every weight
+// equals x_weight's bit for bit.  A single copy matters: eight specialised
+// copies (axis x signs) made instruction fetch the projection's main stall.
+// The <= 3 cells a slab can contribute (|slope| <= 1, margin < h/2) are unrolled.
+template <class Visit>
+__device__ __forceinline__ void ray_weights(const float4& r0, float ex, float ey, const GridF& G, float margin,
+                                            const ExcTable& E, int l, Visit&& visit) {
+    const bool rows = ray_rows(r0);
+    const float bM = rows ? r0.y : r0.x, bm = rows ? r0.x : r0.y;   // foot point, major / minor axis
+    const float iM = rows ? r0.w : r0.z, im = rows ? r0.z : r0.w;   // reciprocal direction
+    const float eM = rows ? ey : ex, em = rows ? ex : ey;           // plane-parameter error bounds
+    const int sM = rows ? G.n : 1, sm = rows ? 1 : G.n;             // pixel-index strides
+    const bool PM = iM >= 0.0f, Pm = im >= 0.0f;
+    const float slope = iM / im;   // d_minor / d_major, |slope| <= 1 (0 for axis-parallel rays)
     const float xlo = G.x0, xhi = grid_plane(G, G.n);
     int jlo = 0, jhi = G.n - 1;
     if (slope != 0.0f) {
@@ -213,7 +220,6 @@ __device__ __forceinline__ void ray_weights_dir(const float4& r0, float ex, floa
     } else if (bm < xlo - margin || bm > xhi + margin) {
         return;
     }
-    const bool PM = ROWS ? PY : PX, Pm = ROWS ? PX : PY;   // sign of the major / minor reciprocal direction
     const float inv_h = 1.0f / G.h;
     const float c_lo = (-margin - G.x0) * inv_h, c_hi = (margin - G.x0) * inv_h;
     float pM0 = grid_plane(G, jlo);
@@ -237,39 +243,13 @@ __device__ __forceinline__ void ray_weights_dir(const float4& r0, float ex, floa
                 const int i = ilo + c;
                 if (i > ihi) break;
                 const float tml = Pm ? tm[c] : tm[c + 1], tmh = Pm ? tm[c + 1] : tm[c];
-                const float txl = ROWS ? tml : tMl, txh = ROWS ? tmh : tMh;
-                const float tyl = ROWS ? tMl : tml, tyh = ROWS ? tMh : tmh;
-                const float w = __fsub_rn(fminf(txh, tyh), fmaxf(txl, tyl));
-                const int k = ROWS ? j * G.n + i : i * G.n + j;
-                const float x = member_weight(w, txl, txh, tyl, tyh, ex, ey, E, l, j * G.n + i);
-                if (x != 0.0f) visit(k, x);
+                const float w = __fsub_rn(fminf(tmh, tMh), fmaxf(tml, tMl));
+                const float x = member_weight(w, tml, tmh, tMl, tMh, em, eM, E, l, j * G.n + i);
+                if (x != 0.0f) visit(j * sM + i * sm, x);
             }
         }
         tM0 = tM1;
         m0 = m1;
-    }
-}
-
-template <class Visit>
-__device__ __forceinline__ void ray_weights(const float4& r0, float ex, float ey, const GridF& G, float margin,
-                                            const ExcTable& E, int l, Visit&& visit) {
-    const bool rows = ray_rows(r0), px = r0.z >= 0.0f, py = r0.w >= 0.0f;
-    if (rows) {
-        if (px) {
-            if (py) ray_weights_dir<true, true, true>(r0, ex, ey, G, margin, E, l, visit);
-            else ray_weights_dir<true, true, false>(r0, ex, ey, G, margin, E, l, visit);
-        } else {
-            if (py) ray_weights_dir<true, false, true>(r0, ex, ey, G, margin, E, l, visit);
-            else ray_weights_dir<true, false, false>(r0, ex, ey, G, margin, E, l, visit);
-        }
-    } else {
-        if (px) {
-            if (py) ray_weights_dir<false, true, true>(r0, ex, ey, G, margin, E, l, visit);
-            else ray_weights_dir<false, true, false>(r0, ex, ey, G, margin, E, l, visit);
-        } else {
-            if (py) ray_weights_dir<false, false, true>(r0, ex, ey, G, margin, E, l, visit);
-            else ray_weights_dir<false, false, false>(r0, ex, ey, G, margin, E, l, visit);
-        }
     }
 }
 
