@@ -50,17 +50,23 @@ HBM_PEAK_GBPS, HBM_PEAK_SOURCE = _hbm_peak()
 # FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of each per-iteration kernel, from one
-# ncu --set full capture (cold cache), valid only for the mocca.cu it was taken on
+# ncu --set full capture (cold cache), valid only for the kernel sources it was taken on
 TRAFFIC = {
-    "k_mocca_proj": {"bytes_per_launch": 18913792, "source_sha": "d770a41425c31945"},
-    "k_mocca_ray": {"bytes_per_launch": 31374848 + 20480, "source_sha": "d770a41425c31945"},
-    "k_mocca_bp": {"bytes_per_launch": 16078080 + 512, "source_sha": "d770a41425c31945"},
+    "k_mocca_proj": {"bytes_per_launch": 18866432, "source_sha": "c9f2346dc19cd95e"},
+    "k_mocca_ray": {"bytes_per_launch": 31365888 + 11264, "source_sha": "c9f2346dc19cd95e"},
+    "k_mocca_bp": {"bytes_per_launch": 16077312, "source_sha": "c9f2346dc19cd95e"},
 }
 
 
+KERNEL_SOURCES = ("mocca.cu", "osscir_internal.cuh", "osscir_launch.h")
+
+
 def _source_sha() -> str:
-    p = os.path.join(ROOT, "paper_1801_06263_gb300", "csrc", "mocca.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    """Hash of the sources of the per-iteration kernels (the traffic figures are tied to it)."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1801_06263_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 class Clocks:
