@@ -229,6 +229,70 @@ __global__ void __launch_bounds__(kFwdThreads) k_counts(GeomC C, ExcTable E, con
     if (part) warp_partial(C, blockIdx.x, warp_view(blockIdx.y, kFwdThreads / 32), dsum, part);
 }
 
+// ------------------------------------------------------------------ double-float arithmetic
+//
+// A value is the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi) / 2),
+// about 48 significant bits, computed on the FP32 pipe: on this GPU the FP64
+// pipe runs at 1/64 of the FP32 rate, so for the dual algebra (after the FP64
+// eigen-clip) two-float arithmetic is several times cheaper than FP64.  The
+// error-free transformations are Knuth's TwoSum and Dekker's exact product in
+// its FMA form (Dekker 1971); additions are the accurate ("IEEE-style")
+// double-word sum of Hida, Li and Bailey (2001), which keeps its accuracy under
+// cancellation; the reciprocal is one Newton step from the FP32 reciprocal.
+// Every operation is spelled with _rn intrinsics so that the compiler cannot
+// contract or reassociate them.
+struct dfl {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfl df_fast2sum(float a, float b) {   // |a| >= |b| (or a = 0)
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ dfl df_2sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ dfl df_2prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+    const dfl s = df_2sum(x.hi, y.hi), t = df_2sum(x.lo, y.lo);
+    const dfl u = df_fast2sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return df_fast2sum(u.hi, __fadd_rn(u.lo, t.lo));
+}
+
+__device__ __forceinline__ dfl df_sub(dfl x, dfl y) { return df_add(x, dfl{-y.hi, -y.lo}); }
+
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
+    const dfl p = df_2prod(x.hi, y.hi);
+    return df_fast2sum(p.hi, __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo)));
+}
+
+__device__ __forceinline__ dfl df_mulf(dfl x, float y) {
+    const dfl p = df_2prod(x.hi, y);
+    return df_fast2sum(p.hi, __fmaf_rn(x.lo, y, p.lo));
+}
+
+__device__ __forceinline__ dfl df_of(double a) {
+    const float h = __double2float_rn(a);
+    return {h, __double2float_rn(a - (double)h)};
+}
+
+__device__ __forceinline__ float df_f(dfl x) { return __fadd_rn(x.hi, x.lo); }
+
+// 1 / x: r + r (1 - x r) with r the FP32 reciprocal of x.hi.
+__device__ __forceinline__ dfl df_rcp(dfl x) {
+    const float r = __frcp_rn(x.hi);
+    const dfl e = df_sub(dfl{1.0f, 0.0f}, df_mulf(x, r));
+    return df_add(dfl{r, 0.0f}, df_mulf(e, r));
+}
+
 // ------------------------------------------------------------------ FP64 3x3 / 4x4 algebra
 
 // Symmetric 3x3 stored as (00, 01, 02, 11, 12, 22).
@@ -363,12 +427,6 @@ __device__ __forceinline__ bool inv_sym3(const double a[6], double o[6]) {
     return true;
 }
 
-// Entry (i, j) of a symmetric 3x3 packed as (00, 01, 02, 11, 12, 22).
-__device__ __forceinline__ double sym3(const double a[6], int i, int j) {
-    const int r = i < j ? i : j, c = i < j ? j : i;
-    return a[r == 0 ? c : (r == 1 ? 2 + c : 5)];
-}
-
 // Dual step of one ray that meets the image (see the file header).
 //   al: window-effective attenuations alpha (FP32), sinv: Sigma^-1 (FP32),
 //   cw: counts, rw: residuals, Bt: sum_i beta_i mu_i mu_i^T with
@@ -377,88 +435,120 @@ __device__ __forceinline__ double sym3(const double a[6], int i, int j) {
 //   y' = y - Sigma (W + Sigma)^-1 (y - r)
 // equals r + G^T z with (I + H+ F) z = H+ G Sigma^-1 (y - r), F = G Sigma^-1 G^T
 // (push-through identity: the rank-3 update is solved in the 3-dim space of g).
-// The Hessian, its clip and this 3x3 algebra are FP64.  Returns y' in yo.
+// The Hessian and its clip are FP64; the rest, whose Gram matrix alpha^T alpha
+// has a condition number near 1e7, is double-float.  Returns y' in yo.
 __device__ void ray_dual(const float al[4][3], const float sinv[4], const double cw[4], const double rw[4],
-                         const float Bt[6], const double y[4], double yo[4]) {
-    double a[4][3];
-#pragma unroll
-    for (int w = 0; w < 4; ++w)
-#pragma unroll
-        for (int m = 0; m < 3; ++m) a[w][m] = (double)al[w][m];
-    double H[6];
+                         const float Bt[6], const float y[4], float yo[4]) {
+    const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    double Hd[6];
     {
-        double ca[4][3];   // c_w alpha_w
+        double a[4][3], ca[4][3];   // alpha and c_w alpha_w
 #pragma unroll
         for (int w = 0; w < 4; ++w)
 #pragma unroll
-            for (int m = 0; m < 3; ++m) ca[w][m] = cw[w] * a[w][m];
-        const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+            for (int m = 0; m < 3; ++m) {
+                a[w][m] = (double)al[w][m];
+                ca[w][m] = cw[w] * a[w][m];
+            }
 #pragma unroll
         for (int e = 0; e < 6; ++e) {
             double acc = -(double)Bt[e];
 #pragma unroll
             for (int w = 0; w < 4; ++w) acc += ca[w][ij[e][0]] * a[w][ij[e][1]];
-            H[e] = acc;
+            Hd[e] = acc;
         }
     }
-    clip_psd3(H);
-    double A[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    clip_psd3(Hd);
+    dfl H[6], r[4];
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        A[0] += a[w][0] * a[w][0]; A[1] += a[w][0] * a[w][1]; A[2] += a[w][0] * a[w][2];
-        A[3] += a[w][1] * a[w][1]; A[4] += a[w][1] * a[w][2]; A[5] += a[w][2] * a[w][2];
-    }
-    double Ai[6];
-    if (!inv_sym3(A, Ai)) {   // degenerate alpha: no curvature term, y' = r
+    for (int e = 0; e < 6; ++e) H[e] = df_of(Hd[e]);
 #pragma unroll
-        for (int w = 0; w < 4; ++w) yo[w] = rw[w];
-        return;
+    for (int w = 0; w < 4; ++w) r[w] = df_of(rw[w]);
+    // A = alpha^T alpha (the products of two floats are exact)
+    dfl A[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+        dfl acc = df_2prod(al[0][ij[e][0]], al[0][ij[e][1]]);
+#pragma unroll
+        for (int w = 1; w < 4; ++w) acc = df_add(acc, df_2prod(al[w][ij[e][0]], al[w][ij[e][1]]));
+        A[e] = acc;
     }
-    double G[3][4], Gs[3][4];
+    // A^-1 by the adjugate
+    dfl Ai[6];
+    {
+        const dfl c00 = df_sub(df_mul(A[3], A[5]), df_mul(A[4], A[4]));
+        const dfl c01 = df_sub(df_mul(A[2], A[4]), df_mul(A[1], A[5]));
+        const dfl c02 = df_sub(df_mul(A[1], A[4]), df_mul(A[2], A[3]));
+        const dfl c11 = df_sub(df_mul(A[0], A[5]), df_mul(A[2], A[2]));
+        const dfl c12 = df_sub(df_mul(A[1], A[2]), df_mul(A[0], A[4]));
+        const dfl c22 = df_sub(df_mul(A[0], A[3]), df_mul(A[1], A[1]));
+        const dfl det = df_add(df_add(df_mul(A[0], c00), df_mul(A[1], c01)), df_mul(A[2], c02));
+        if (!(det.hi != 0.0f) || !isfinite(det.hi)) {   // degenerate alpha: no curvature term, y' = r
+#pragma unroll
+            for (int w = 0; w < 4; ++w) yo[w] = df_f(r[w]);
+            return;
+        }
+        const dfl id = df_rcp(det);
+        Ai[0] = df_mul(c00, id); Ai[1] = df_mul(c01, id); Ai[2] = df_mul(c02, id);
+        Ai[3] = df_mul(c11, id); Ai[4] = df_mul(c12, id); Ai[5] = df_mul(c22, id);
+    }
+    const int sidx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};   // packed index of (i, j)
+    dfl G[3][4], Gs[3][4];
 #pragma unroll
     for (int m = 0; m < 3; ++m)
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
-            G[m][w] = sym3(Ai, m, 0) * a[w][0] + sym3(Ai, m, 1) * a[w][1] + sym3(Ai, m, 2) * a[w][2];
-            Gs[m][w] = G[m][w] * (double)sinv[w];
+            G[m][w] = df_add(df_add(df_mulf(Ai[sidx[m][0]], al[w][0]), df_mulf(Ai[sidx[m][1]], al[w][1])),
+                             df_mulf(Ai[sidx[m][2]], al[w][2]));
+            Gs[m][w] = df_mulf(G[m][w], sinv[w]);
         }
-    double d[4];
+    dfl d[4];
 #pragma unroll
-    for (int w = 0; w < 4; ++w) d[w] = y[w] - rw[w];
-    double F[6], phi[3];
-    {
-        const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+    for (int w = 0; w < 4; ++w) d[w] = df_sub(dfl{y[w], 0.0f}, r[w]);
+    dfl F[6], phi[3];
 #pragma unroll
-        for (int e = 0; e < 6; ++e) {
-            const int m = ij[e][0], n = ij[e][1];
-            F[e] = Gs[m][0] * G[n][0] + Gs[m][1] * G[n][1] + Gs[m][2] * G[n][2] + Gs[m][3] * G[n][3];
-        }
-#pragma unroll
-        for (int m = 0; m < 3; ++m) phi[m] = Gs[m][0] * d[0] + Gs[m][1] * d[1] + Gs[m][2] * d[2] + Gs[m][3] * d[3];
+    for (int e = 0; e < 6; ++e) {
+        const int m = ij[e][0], n = ij[e][1];
+        F[e] = df_add(df_add(df_mul(Gs[m][0], G[n][0]), df_mul(Gs[m][1], G[n][1])),
+                      df_add(df_mul(Gs[m][2], G[n][2]), df_mul(Gs[m][3], G[n][3])));
     }
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+        phi[m] = df_add(df_add(df_mul(Gs[m][0], d[0]), df_mul(Gs[m][1], d[1])),
+                        df_add(df_mul(Gs[m][2], d[2]), df_mul(Gs[m][3], d[3])));
     // Mx = I + H+ F (3 x 3), rhs = H+ phi
-    double Mx[3][3], rhs[3];
+    dfl Mx[3][3], rhs[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
-            Mx[i][j] = (i == j ? 1.0 : 0.0) + sym3(H, i, 0) * sym3(F, 0, j) + sym3(H, i, 1) * sym3(F, 1, j) +
-                       sym3(H, i, 2) * sym3(F, 2, j);
-        rhs[i] = sym3(H, i, 0) * phi[0] + sym3(H, i, 1) * phi[1] + sym3(H, i, 2) * phi[2];
+        for (int j = 0; j < 3; ++j) {
+            dfl acc = df_add(df_add(df_mul(H[sidx[i][0]], F[sidx[0][j]]), df_mul(H[sidx[i][1]], F[sidx[1][j]])),
+                             df_mul(H[sidx[i][2]], F[sidx[2][j]]));
+            if (i == j) acc = df_add(acc, dfl{1.0f, 0.0f});
+            Mx[i][j] = acc;
+        }
+        rhs[i] = df_add(df_add(df_mul(H[sidx[i][0]], phi[0]), df_mul(H[sidx[i][1]], phi[1])),
+                        df_mul(H[sidx[i][2]], phi[2]));
     }
-    // z = Mx^-1 rhs (adjugate; the eigenvalues of Mx are >= 1)
-    const double c00 = Mx[1][1] * Mx[2][2] - Mx[1][2] * Mx[2][1];
-    const double c01 = Mx[1][2] * Mx[2][0] - Mx[1][0] * Mx[2][2];
-    const double c02 = Mx[1][0] * Mx[2][1] - Mx[1][1] * Mx[2][0];
-    const double idet = 1.0 / (Mx[0][0] * c00 + Mx[0][1] * c01 + Mx[0][2] * c02);
-    const double z0 = idet * (c00 * rhs[0] + (Mx[0][2] * Mx[2][1] - Mx[0][1] * Mx[2][2]) * rhs[1] +
-                              (Mx[0][1] * Mx[1][2] - Mx[0][2] * Mx[1][1]) * rhs[2]);
-    const double z1 = idet * (c01 * rhs[0] + (Mx[0][0] * Mx[2][2] - Mx[0][2] * Mx[2][0]) * rhs[1] +
-                              (Mx[0][2] * Mx[1][0] - Mx[0][0] * Mx[1][2]) * rhs[2]);
-    const double z2 = idet * (c02 * rhs[0] + (Mx[0][1] * Mx[2][0] - Mx[0][0] * Mx[2][1]) * rhs[1] +
-                              (Mx[0][0] * Mx[1][1] - Mx[0][1] * Mx[1][0]) * rhs[2]);
+    // z = Mx^-1 rhs (adjugate; the eigenvalues of Mx are >= 1).  C[i][j] is the
+    // cofactor of Mx[j][i]; cyclic indices carry the signs.
+    dfl C[3][3];
 #pragma unroll
-    for (int w = 0; w < 4; ++w) yo[w] = rw[w] + G[0][w] * z0 + G[1][w] * z1 + G[2][w] * z2;
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int r0 = (j + 1) % 3, r1 = (j + 2) % 3, c0 = (i + 1) % 3, c1 = (i + 2) % 3;
+            C[i][j] = df_sub(df_mul(Mx[r0][c0], Mx[r1][c1]), df_mul(Mx[r0][c1], Mx[r1][c0]));
+        }
+    const dfl idet =
+        df_rcp(df_add(df_add(df_mul(Mx[0][0], C[0][0]), df_mul(Mx[0][1], C[1][0])), df_mul(Mx[0][2], C[2][0])));
+    dfl z[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        z[i] = df_mul(idet, df_add(df_add(df_mul(C[i][0], rhs[0]), df_mul(C[i][1], rhs[1])), df_mul(C[i][2], rhs[2])));
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+        yo[w] = df_f(df_add(r[w], df_add(df_add(df_mul(G[0][w], z[0]), df_mul(G[1][w], z[1])), df_mul(G[2][w], z[2]))));
 }
 
 // ------------------------------------------------------------------ fused MOCCA kernels
@@ -530,7 +620,8 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
         }
         dsum = (double)dt;
         const float X1 = __ldg(D.chord + l);
-        double y[4] = {yy.x, yy.y, yy.z, yy.w}, yo[4];
+        const float y[4] = {yy.x, yy.y, yy.z, yy.w};
+        float yo[4];
         if (!(X1 > 0.f)) {   // the ray misses the image: Sigma^-1 = 0, the dual is kept
 #pragma unroll
             for (int w = 0; w < 4; ++w) yo[w] = y[w];
