@@ -43,8 +43,11 @@ void free_ctx(osscir_ctx* h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->side_stream) cudaStreamDestroy(h->side_stream);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
     void* ptrs[] = {h->rec, h->r64, h->views, h->chord, h->exc_off, h->exc_ent, h->s4, h->N4, h->mu,
                     h->g, h->c, h->y, h->x, h->xbar, h->dtpl_part, h->dtpl_out};
     for (void* p : ptrs)
@@ -147,7 +150,10 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     CK(dalloc(&h->dtpl_part, h->n_part));
     CK(dalloc(&h->dtpl_out, 2));
     CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
     for (cudaEvent_t& e : h->ev) CK(cudaEventCreate(&e));
+    CK(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
     cudaStream_t st = h->cap_stream;
 
     // spectral tables: s reordered to [nE][n_bins] float4 so consecutive rays read consecutive entries
@@ -190,6 +196,9 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
 }
 
 // One MOCCA iteration as launches on a stream (captured into a graph once).
+// One iteration on st: projection, per-ray step, back-projection; the D_TPL
+// reduction needs only the per-ray partials, so it runs on a side branch
+// beside the back-projection and joins before the iteration ends.
 cudaError_t enqueue_iteration(osscir_ctx* h, cudaStream_t st) {
     cudaError_t e = cudaEventRecordWithFlags(h->ev[0], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
@@ -199,13 +208,21 @@ cudaError_t enqueue_iteration(osscir_ctx* h, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     e = launch_mocca_ray(h->gc, h->rec, h->spec(), h->params, h->solve(), st);
     if (e != cudaSuccess) return e;
+    e = cudaEventRecord(h->fork, st);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamWaitEvent(h->side_stream, h->fork, 0);
+    if (e != cudaSuccess) return e;
+    e = launch_dtpl_reduce(h->dtpl_part, h->n_part, h->dtpl_out + 1, h->side_stream);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(h->join, h->side_stream);
+    if (e != cudaSuccess) return e;
     e = cudaEventRecordWithFlags(h->ev[2], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
     e = launch_mocca_bp(h->gc, h->exc(), h->rec, h->views, h->params, h->solve(), st);
     if (e != cudaSuccess) return e;
     e = cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
-    return launch_dtpl_reduce(h->dtpl_part, h->n_part, h->dtpl_out + 1, st);
+    return cudaStreamWaitEvent(st, h->join, 0);
 }
 
 osscir_status ensure_graph(osscir_ctx* h) {

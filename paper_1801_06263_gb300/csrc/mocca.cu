@@ -582,6 +582,7 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
         float Ds[4] = {0.f, 0.f, 0.f, 0.f}, Dc[4] = {0.f, 0.f, 0.f, 0.f}, An[4][3];
 #pragma unroll
         for (int w = 0; w < 4; ++w) An[w][0] = An[w][1] = An[w][2] = 0.f;
+#pragma unroll 2   // two energies in flight: the s-table loads overlap
         for (int i = 0; i < nE; ++i) {
             const float4 qa = *reinterpret_cast<const float4*>(sm + kSmemStride * i);
             const float p = fmaf(qa.z, g2, fmaf(qa.y, g1, qa.x * g0));
@@ -631,6 +632,7 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
         } else {
             // second pass: sum_i beta_i mu_i mu_i^T, beta_i = softexp''(-p_i) sum_w (r_w / D_w) s_wi
             float Bt[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
             for (int i = 0; i < nE; ++i) {
                 const float4 qa = *reinterpret_cast<const float4*>(sm + kSmemStride * i);
                 const float p = fmaf(qa.z, g2, fmaf(qa.y, g1, qa.x * g0));

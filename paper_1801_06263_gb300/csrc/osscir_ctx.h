@@ -42,6 +42,8 @@ struct osscir_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // recorded around the kernels inside the graph
+    cudaStream_t side_stream = nullptr;                 // D_TPL reduction beside the back-projection
+    cudaEvent_t fork = nullptr, join = nullptr;
 
     osscir::ExcTable exc() const { return osscir::ExcTable{exc_off, exc_ent}; }
     osscir::SpecD spec() const { return osscir::SpecD{nE, s4, N4, mu}; }

@@ -225,6 +225,7 @@ __device__ __forceinline__ void ray_weights(const float4& r0, float ex, float ey
     float pM0 = grid_plane(G, jlo);
     float tM0 = t_plane(pM0, bM, iM);
     float m0 = fmaf(slope, pM0 - bM, bm);
+#pragma unroll 2   // two slabs per trip: more independent loads in flight
     for (int j = jlo; j <= jhi; ++j) {
         const float pM1 = grid_plane(G, j + 1);
         const float tM1 = t_plane(pM1, bM, iM);
