@@ -201,7 +201,7 @@ typedef struct osscir_batch *osscir_batch_t;
  *   proj_views:  views per projection block (1, 2, 4 or 8; 32 bins each);
  *   proj_grid, ray_grid, bp_grid: 0 = one CTA per work item (flat grid),
  *                > 0 = that many persistent CTAs striding over the items;
- *   bp_tile_x:   width of the 64-pixel back-projection tile (4, 8, 16 or 32);
+ *   bp_tile_x:   width of the 64-pixel back-projection tile (2, 4, 8, 16 or 32);
  *   *_order:     work-list order of each kernel: 0 solve by solve, 1 the
  *                solves with the costliest items first, 2 solves interleaved
  *                item by item;

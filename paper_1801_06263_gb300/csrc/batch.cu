@@ -37,13 +37,13 @@ osscir_status from_cuda(cudaError_t e) {
 inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
 constexpr int kMaxBranches = 4;
-constexpr osscir_batch_config kDefault = {4, 0, 0, 0, 0, 8, 0, 0, 1};
+constexpr osscir_batch_config kDefault = {4, 0, 0, 0, 0, 2, 0, 0, 1};
 
 bool valid_config(const osscir_batch_config& c) {
     const auto pow2_in = [](int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; };
     const auto grid_ok = [](int g) { return g >= 0 && g <= (1 << 20); };
     const auto order_ok = [](int o) { return o >= 0 && o <= 2; };
-    return pow2_in(c.proj_views, 1, 8) && pow2_in(c.bp_tile_x, 4, 32) && grid_ok(c.proj_grid) &&
+    return pow2_in(c.proj_views, 1, 8) && pow2_in(c.bp_tile_x, 2, 32) && grid_ok(c.proj_grid) &&
            grid_ok(c.ray_grid) && grid_ok(c.bp_grid) && order_ok(c.proj_order) && order_ok(c.ray_order) &&
            order_ok(c.bp_order) && pow2_in(c.branches, 1, kMaxBranches);
 }
@@ -366,8 +366,8 @@ osscir_status tune_kernel(osscir_batch* b, int k, int persistent_grid, cudaEvent
     if (k != 1) {
         c = best;
         const int views[4] = {1, 2, 4, 8};
-        const int txs[4] = {4, 8, 16, 32};
-        for (int i = 0; i < 4; ++i) {
+        const int txs[5] = {2, 4, 8, 16, 32};
+        for (int i = 0; i < (k == 0 ? 4 : 5); ++i) {
             if (k == 0) {
                 if (views[i] == best.proj_views) continue;
                 c.proj_views = views[i];

@@ -50,7 +50,7 @@ struct SolveD {
 
 constexpr int kFwdThreads = 128;
 constexpr int kBpTileX = 16, kBpTileY = 8;            // plain back-projection tile
-constexpr int kBpPixX = 8, kBpPixY = 8;               // MOCCA back-projection pixel tile
+constexpr int kBpPixX = 2, kBpPixY = 32;              // MOCCA back-projection pixel tile (2 x 32: measured fastest)
 constexpr int kBpPix = kBpPixX * kBpPixY;
 constexpr int kBpMaxThreads = 512;                    // kBpPix x up to 8 view groups
 
