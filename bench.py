@@ -52,9 +52,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of each per-iteration kernel, from one
 # ncu --set full capture (cold cache), valid only for the kernel sources it was taken on
 TRAFFIC = {
-    "k_mocca_proj": {"bytes_per_launch": 18866432, "source_sha": "c9f2346dc19cd95e"},
-    "k_mocca_ray": {"bytes_per_launch": 31365888 + 11264, "source_sha": "c9f2346dc19cd95e"},
-    "k_mocca_bp": {"bytes_per_launch": 16077312, "source_sha": "c9f2346dc19cd95e"},
+    "k_mocca_proj": {"bytes_per_launch": 18874880, "source_sha": "bcda296a3f65f7ea"},
+    "k_mocca_ray": {"bytes_per_launch": 31450880 + 201216, "source_sha": "bcda296a3f65f7ea"},
+    "k_mocca_bp": {"bytes_per_launch": 16078336 + 1024, "source_sha": "bcda296a3f65f7ea"},
 }
 
 
