@@ -49,6 +49,8 @@ def _hbm_peak():
 HBM_PEAK_GBPS, HBM_PEAK_SOURCE = _hbm_peak()
 # FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# L1 to register-file bandwidth from unit counts: 152 SMs x 128 B per clock x 2.07 GHz
+L1_PEAK_TBPS = 152 * 128 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of each per-iteration kernel, from one
 # ncu --set full capture (cold cache), valid only for the kernel sources it was taken on
 TRAFFIC = {
@@ -313,6 +315,16 @@ def run_gpu(args):
         "k_mocca_bp": {"ms": mean[2], "flop": 18.0 * nnz},
     }
     dom = max(kern, key=lambda k: kern[k]["ms"])
+    # bytes each footprint pair must bring from L1 to the registers: proj the float4 of
+    # xbar; bp the ray's weight inputs (foot point, reciprocal direction, bounds: 24 B)
+    # and its b and S (36 B)
+    gather_bytes = {"k_mocca_proj": 16.0, "k_mocca_bp": 60.0}.get(dom)
+    gather = None
+    if gather_bytes:
+        g_ach = gather_bytes * nnz / (kern[dom]["ms"] * 1e-3) / 1e12
+        gather = {"bound": "l1", "kernel": dom, "bytes_per_pair": gather_bytes, "achieved": g_ach,
+                  "peak": L1_PEAK_TBPS, "unit": "TB/s", "frac": g_ach / L1_PEAK_TBPS,
+                  "peak_source": "152 SMs x 128 B per clock from L1 to registers x 2.07 GHz (unit counts)"}
     achieved = kern[dom]["flop"] / (kern[dom]["ms"] * 1e-3) / 1e12
     tr = TRAFFIC.get(dom)
     traffic = tr["bytes_per_launch"] if tr and tr.get("source_sha") == _source_sha() else None
@@ -335,6 +347,7 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and max clock)"},
+        "gather_roofline": gather,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_rate, "unit": "iter/s", "h2d_bytes_per_step": int(c_host.numel() * 4),
                 "d2h_bytes_per_step": int(maps_host.numel() * 4),
