@@ -563,7 +563,7 @@ __device__ __forceinline__ void proj_ray(const GeomC& C, const ExcTable& E, cons
     D.g[l] = make_float4(gs.x, gs.y, gs.z, 0.f);
 }
 
-__global__ void __launch_bounds__(kFwdThreads) k_mocca_proj(GeomC C, ExcTable E, const RayRec* rec, SolveD D) {
+__global__ void __launch_bounds__(kFwdThreads, 8) k_mocca_proj(GeomC C, ExcTable E, const RayRec* rec, SolveD D) {
     const int l = ray_of_thread(C);
     if (l >= 0) proj_ray(C, E, rec, D, l);
 }
