@@ -686,7 +686,7 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
     return dsum;
 }
 
-__global__ void __launch_bounds__(kFwdThreads, 5) k_mocca_ray(GeomC C, RayRec* rec, SpecD S, StepParams P,
+__global__ void __launch_bounds__(kFwdThreads, 6) k_mocca_ray(GeomC C, RayRec* rec, SpecD S, StepParams P,
                                                               SolveD D) {
     __shared__ float sm[kSmemStride * kMaxEnergies];
     load_mu_smem(S, sm);
@@ -905,7 +905,7 @@ __global__ void __launch_bounds__(kBatchProjMaxThreads) k_batch_proj(const Solve
     }
 }
 
-__global__ void __launch_bounds__(kFwdThreads, 5) k_batch_ray(const SolveDesc* __restrict__ sd,
+__global__ void __launch_bounds__(kFwdThreads, 6) k_batch_ray(const SolveDesc* __restrict__ sd,
                                                               const int2* __restrict__ items, int n_items) {
     __shared__ float sm[kSmemStride * kMaxEnergies];
     int cur = -1;
