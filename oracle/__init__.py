@@ -36,7 +36,7 @@ class _Geom(ct.Structure):
 
 
 class _Spectra(ct.Structure):
-    _fields_ = [("n_energies", ct.c_int), ("s", _dp), ("N", _dp), ("mu", _dp)]
+    _fields_ = [("n_energies", ct.c_int), ("s", _dp), ("N", _dp), ("mu", _dp), ("exp_model", ct.c_int)]
 
 
 class _Params(ct.Structure):
@@ -111,11 +111,12 @@ def _geom(g) -> _Geom:
 class _SpecHolder:
     """Keeps the numpy arrays alive while the C struct points at them."""
 
-    def __init__(self, sp, mu=None):
+    def __init__(self, sp, mu=None, counts_model="softexp"):
         self.s = _f64(sp.s)
         self.N = _f64(sp.N)
         self.mu = _f64(sp.mu if mu is None else mu)
-        self.c = _Spectra(self.s.shape[1], _ptr(self.s), _ptr(self.N), _ptr(self.mu))
+        self.c = _Spectra(self.s.shape[1], _ptr(self.s), _ptr(self.N), _ptr(self.mu),
+                          {"softexp": 0, "exp": 1}[counts_model])
 
 
 def _params(lam, use_box=False, lo=(0, 0, 0), hi=(0, 0, 0), spc="block", model="hessian"):
@@ -167,17 +168,17 @@ def backproject(geom, rf):
 
 # --------------------------------------------------------------------------- counts model
 
-def counts(geom, spectra, f, mu=None):
-    """Expected counts c^(f), [L, 4] (Eq. finalModel)."""
-    sh = _SpecHolder(spectra, mu)
+def counts(geom, spectra, f, mu=None, counts_model="softexp"):
+    """Expected counts c^(f), [L, 4] (Eq. finalModel; counts_model="exp": Eq. fullModel)."""
+    sh = _SpecHolder(spectra, mu, counts_model)
     f = _f64(f)
     chat = np.zeros((geom.n_rays, 4))
     lib().orc_counts(ct.byref(_geom(geom)), ct.byref(sh.c), _ptr(f), _ptr(chat))
     return chat
 
 
-def ray_terms(spectra, b, g, c=None, with_AB=False, mu=None):
-    sh = _SpecHolder(spectra, mu)
+def ray_terms(spectra, b, g, c=None, with_AB=False, mu=None, counts_model="softexp"):
+    sh = _SpecHolder(spectra, mu, counts_model)
     nE = sh.s.shape[1]
     g = _f64(g)
     cw = None if c is None else _f64(c)
@@ -202,8 +203,8 @@ def dtpl(c, chat):
     return float(lib().orc_dtpl(c.size, _ptr(c), _ptr(chat)))
 
 
-def objective(geom, spectra, c, f, with_grad=True, mu=None):
-    sh = _SpecHolder(spectra, mu)
+def objective(geom, spectra, c, f, with_grad=True, mu=None, counts_model="softexp"):
+    sh = _SpecHolder(spectra, mu, counts_model)
     c = _f64(c)
     f = _f64(f)
     grad = np.zeros((geom.n_pixels, 3)) if with_grad else None
@@ -261,8 +262,8 @@ def primal_update(Tinv, v, x, box=None):
 
 # --------------------------------------------------------------------------- MOCCA
 
-def step_matrices(geom, spectra, xbar, lam, spc="block", mu=None):
-    sh = _SpecHolder(spectra, mu)
+def step_matrices(geom, spectra, xbar, lam, spc="block", mu=None, counts_model="softexp"):
+    sh = _SpecHolder(spectra, mu, counts_model)
     P = _params(lam, spc=spc)
     xbar = _f64(xbar)
     sinv = np.zeros((geom.n_rays, 4))
@@ -289,10 +290,11 @@ class State:
 
 
 def mocca(geom, spectra, c, n_iters, lam, state=None, *, box=None, spc="block",
-          model="hessian", mu=None):
+          model="hessian", mu=None, counts_model="softexp"):
     """Run n_iters MOCCA iterations from `state` (zeros if None); returns
-    (state, dtpl_history) with dtpl_history[i] = D_TPL(c, c^(xbar_i))."""
-    sh = _SpecHolder(spectra, mu)
+    (state, dtpl_history) with dtpl_history[i] = D_TPL(c, c^(xbar_i)).
+    counts_model="exp" replaces softexp by exp (the standard model, Eq. fullModel)."""
+    sh = _SpecHolder(spectra, mu, counts_model)
     st = State(geom) if state is None else state
     lo, hi = (box if box is not None else ((0, 0, 0), (0, 0, 0)))
     P = _params(lam, box is not None, tuple(lo), tuple(hi), spc, model)

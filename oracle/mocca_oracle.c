@@ -58,6 +58,7 @@ typedef struct {
     const double *s;  /* [n_bins][nE][4]  normalised spectral response s_{w,l,i} */
     const double *N;  /* [n_bins][4]      incident photons N_{w,l}              */
     const double *mu; /* [3][nE]          mu_{m,i} in 1/mm                       */
+    int exp_model;    /* 0: softexp (Eq. finalModel); 1: exp (the standard model, Eq. fullModel) */
 } orc_spectra;
 
 typedef struct {
@@ -222,10 +223,11 @@ void orc_backproject(const orc_geometry *G, const double *rf, int C, double *img
 
 /* ------------------------------------------------------------------ counts model */
 
-/* softexp and its first two derivatives (Sec. 2): exp for x <= 0, x + 1 above. */
-static double sexp0(double x) { return x <= 0.0 ? exp(x) : x + 1.0; }
-static double sexp1(double x) { return x <= 0.0 ? exp(x) : 1.0; }
-static double sexp2(double x) { return x <= 0.0 ? exp(x) : 0.0; }
+/* softexp and its first two derivatives (Sec. 2): exp for x <= 0, x + 1 above.
+ * With expm = 1 the standard model's exp (Eq. fullModel) everywhere. */
+static double sexp0(double x, int expm) { return (x <= 0.0 || expm) ? exp(x) : x + 1.0; }
+static double sexp1(double x, int expm) { return (x <= 0.0 || expm) ? exp(x) : 1.0; }
+static double sexp2(double x, int expm) { return (x <= 0.0 || expm) ? exp(x) : 0.0; }
 
 /* Per-ray quantities of Sec. 2 at line integrals g (one ray, detector bin b):
  *   chat_w = N_w sum_i s_wi softexp(-p_i)                        (Eq. finalModel)
@@ -248,9 +250,9 @@ void orc_ray_terms(const orc_spectra *sp, int b, const double g[3], const double
     for (int i = 0; i < nE; ++i) {
         double p = 0.0;
         for (int m = 0; m < NM; ++m) p += sp->mu[m * nE + i] * g[m];
-        e0[i] = sexp0(-p);
-        e1[i] = sexp1(-p);
-        e2[i] = sexp2(-p);
+        e0[i] = sexp0(-p, sp->exp_model);
+        e1[i] = sexp1(-p, sp->exp_model);
+        e2[i] = sexp2(-p, sp->exp_model);
     }
     double D[NW], ch[NW], rr[NW], al[NW][NM];
     for (int w = 0; w < NW; ++w) {

@@ -126,10 +126,11 @@ def test_convex_monochromatic_case_reaches_minimiser(orc):
     assert np.linalg.norm(st.x - f_star) <= 1e-7 * np.linalg.norm(f_star)
 
 
-def test_noiseless_inverse_crime_converges(orc):
+@pytest.mark.parametrize("counts_model", ["softexp", "exp"])
+def test_noiseless_inverse_crime_converges(orc, counts_model):
     w = inputs.workload("tiny_16")
-    c = orc.counts(w.geom, w.spectra, w.f_true)
-    st, hist = orc.mocca(w.geom, w.spectra, c, 3000, 1e-6)
+    c = orc.counts(w.geom, w.spectra, w.f_true, counts_model=counts_model)
+    st, hist = orc.mocca(w.geom, w.spectra, c, 3000, 1e-6, counts_model=counts_model)
     assert np.all(np.isfinite(hist))
     assert hist[-1] < 1e-8 * hist[0]
     # after a burn-in the objective decreases (checked on a coarse grid)
@@ -138,8 +139,8 @@ def test_noiseless_inverse_crime_converges(orc):
     errs = [np.linalg.norm(st.x[:, m] - w.f_true[:, m]) / np.linalg.norm(w.f_true[:, m]) for m in range(3)]
     assert max(errs) < 0.06, errs
     # stationarity: the gradient Z^T A^T r shrinks by orders of magnitude
-    _, g0 = orc.objective(w.geom, w.spectra, c, np.zeros_like(w.f_true))
-    _, g1 = orc.objective(w.geom, w.spectra, c, st.x)
+    _, g0 = orc.objective(w.geom, w.spectra, c, np.zeros_like(w.f_true), counts_model=counts_model)
+    _, g1 = orc.objective(w.geom, w.spectra, c, st.x, counts_model=counts_model)
     assert np.linalg.norm(g1) < 1e-3 * np.linalg.norm(g0)
 
 

@@ -139,3 +139,70 @@ def test_ray_gradient_matches_dtpl_finite_difference(orc, spectra):
         dp = orc.dtpl(c, orc.ray_terms(spectra, 4, gp, c)["chat"])
         dm = orc.dtpl(c, orc.ray_terms(spectra, 4, gm, c)["chat"])
         assert abs((dp - dm) / (2 * h) - t["grad"][m]) <= 1e-6 * np.abs(t["grad"]).max()
+
+
+# ---------------------------------------------------------------- the standard exp model (Eq. fullModel)
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_exp_model_delta_spectrum_closed_form(orc, sign):
+    """One-hot s: c^_w = N_w exp(-p_j) for either sign of p_j, and A = B = the one-hot
+    response (exp' = exp'' = exp), so alpha_w = mu_j (Eq. fullModel, Eq. aeq)."""
+    j = 37
+    sp = _delta_spectra(101, j)
+    g = sign * np.array([3.0, 0.4, 0.01])
+    p = float(sp.mu[:, j] @ g)
+    t = orc.ray_terms(sp, 1, g, with_AB=True, counts_model="exp")
+    np.testing.assert_allclose(t["chat"], sp.N[1] * math.exp(-p), rtol=1e-14)
+    np.testing.assert_allclose(t["alpha"], np.tile(sp.mu[:, j], (4, 1)), rtol=1e-14)
+    np.testing.assert_allclose(t["A"], t["B"], rtol=0, atol=1e-15)
+
+
+def test_models_agree_where_line_integrals_are_nonnegative(orc, spectra):
+    """softexp(x) = exp(x) for x <= 0: with p_i >= 0 for every energy both models give
+    the same counts, alpha and Hessian; with some p_i < 0 they differ."""
+    g = np.array([12.0, 0.7, 0.01])
+    c = spectra.N[2] * 0.3
+    a = orc.ray_terms(spectra, 2, g, c)
+    b = orc.ray_terms(spectra, 2, g, c, counts_model="exp")
+    for k in ("chat", "alpha", "H"):
+        np.testing.assert_array_equal(a[k], b[k])
+    gn = -g
+    a = orc.ray_terms(spectra, 2, gn, c)
+    b = orc.ray_terms(spectra, 2, gn, c, counts_model="exp")
+    assert np.all(b["chat"] > a["chat"])   # exp(x) > 1 + x for x > 0
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_exp_model_hessian_matches_finite_differences(orc, spectra, seed):
+    """The per-ray Hessian -Z^T diag(B^T r) Z + Z^T A^T diag(c^ + r) A Z under exp, where
+    B = A (so C = A - B = 0), against central differences of the gradient."""
+    rng = np.random.default_rng(seed)
+    g = np.array([20.0, 1.0, 0.02]) * rng.uniform(-0.2, 1.0, size=3)
+    c = spectra.N[3] * rng.uniform(0.05, 0.6, size=4)
+    t = orc.ray_terms(spectra, 3, g, c, with_AB=True, counts_model="exp")
+    np.testing.assert_allclose(t["A"], t["B"], rtol=0, atol=1e-15)
+    fd = np.zeros((3, 3))
+    for m in range(3):
+        h = 1e-6 * max(1.0, abs(g[m]))
+        gp = g.copy(); gp[m] += h
+        gm = g.copy(); gm[m] -= h
+        fd[:, m] = (orc.ray_terms(spectra, 3, gp, c, counts_model="exp")["grad"]
+                    - orc.ray_terms(spectra, 3, gm, c, counts_model="exp")["grad"]) / (2 * h)
+    np.testing.assert_allclose(t["H"], fd, rtol=0, atol=2e-6 * np.abs(t["H"]).max())
+
+
+def test_exp_model_gradient_matches_dtpl_finite_differences(orc):
+    geom, sp, f_true, rng, _ = _tiny_problem()
+    c = inputs.poisson_counts(orc.counts(geom, sp, f_true, counts_model="exp"), 9)
+    f = f_true + rng.normal(scale=0.05, size=f_true.shape) * np.array([1.0, 0.3, 0.002])
+    f[0] = -0.2   # a pixel with negative values, so that some p_i < 0
+    d0, grad = orc.objective(geom, sp, c, f, counts_model="exp")
+    fd = np.zeros_like(f)
+    for k in range(geom.n_pixels):
+        for m in range(3):
+            h = 1e-6 * max(1.0, abs(f[k, m]))
+            fp = f.copy(); fp[k, m] += h
+            fm = f.copy(); fm[k, m] -= h
+            fd[k, m] = (orc.objective(geom, sp, c, fp, with_grad=False, counts_model="exp")
+                        - orc.objective(geom, sp, c, fm, with_grad=False, counts_model="exp")) / (2 * h)
+    np.testing.assert_allclose(grad, fd, rtol=0, atol=1e-6 * np.abs(grad).max())
