@@ -84,13 +84,18 @@ typedef struct {
  * m-block-diagonal step-preconditioner of Sec. 2; spc = 1 the diagonal one of
  * Pock and Chambolle that it replaces (Sigma_wl = (1/lambda) / sum_mk |K|,
  * T_mk = lambda / sum_wl |K|, Sec. 2) — with a material basis orthogonalised
- * over energy by the caller this is the mu-PC of Sec. 2. */
+ * over energy by the caller this is the mu-PC of Sec. 2.  counts_model = 0 is
+ * the softexp counts model of Eq. (finalModel); counts_model = 1 the standard
+ * model of Eq. (fullModel) with exp for every energy (the paper's softexp
+ * replaces it so that negative line integrals do not make the counts blow up);
+ * it applies to osscir_simulate and osscir_dtpl as well as to the iteration. */
 typedef struct {
     double lambda;
     int model;
     int use_box;
     float lo[3], hi[3];
     int spc;
+    int counts_model;
 } osscir_params;
 
 /* Human-readable name of a status code (static string). */

@@ -23,13 +23,14 @@ class Reconstructor:
     ray fields [L, 4] (four windows or four channels).
     """
 
-    def __init__(self, geom, spectra, lam: float, *, model: int = 0, box=None, mu=None, spc: int = 0):
+    def __init__(self, geom, spectra, lam: float, *, model: int = 0, box=None, mu=None, spc: int = 0,
+                 counts_model: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
         self.geom = geom
         self.handle = osscir_create(geom, spectra.s, spectra.N, spectra.mu if mu is None else mu, lam,
-                                    model=model, box=box, spc=spc)
+                                    model=model, box=box, spc=spc, counts_model=counts_model)
         self.n_pixels, self.n_rays, self.n_fp64_pairs = osscir_info(self.handle)
 
     # -- tensors

@@ -86,6 +86,7 @@ osscir_status validate(const osscir_geometry* g, const osscir_spectra* sp, const
     if (!finite_pos(pa->lambda) || !(pa->lambda < 3.0e38)) return OSSCIR_E_INVALID;
     if (pa->model != 0 && pa->model != 1) return OSSCIR_E_INVALID;
     if (pa->spc != 0 && pa->spc != 1) return OSSCIR_E_INVALID;
+    if (pa->counts_model != 0 && pa->counts_model != 1) return OSSCIR_E_INVALID;
     if (pa->use_box)
         for (int m = 0; m < 3; ++m)
             if (!std::isfinite(pa->lo[m]) || !std::isfinite(pa->hi[m]) || !(pa->lo[m] <= pa->hi[m]))
@@ -126,6 +127,7 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     h->params.lambda = (float)pa->lambda;
     h->params.model = pa->model;
     h->params.spc = pa->spc;
+    h->exp_model = pa->counts_model;
     h->params.use_box = pa->use_box;
     for (int m = 0; m < 3; ++m) {
         h->params.lo[m] = pa->lo[m];

@@ -89,9 +89,10 @@ __device__ __forceinline__ void load_mu_smem(const SpecD& S, float* sm) {
     }
 }
 
-// softexp(x), softexp'(x), softexp''(x) (Sec. 2): exp below 0, x + 1 above.
-__device__ __forceinline__ void sexp3(float x, float& e0, float& e1, float& e2) {
-    if (x <= 0.0f) {
+// softexp(x), softexp'(x), softexp''(x) (Sec. 2): exp below 0, x + 1 above;
+// with expm the standard model's exp everywhere (Eq. fullModel).
+__device__ __forceinline__ void sexp3(float x, bool expm, float& e0, float& e1, float& e2) {
+    if (x <= 0.0f || expm) {
         e0 = expf(x);
         e1 = e0;
         e2 = e0;
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_counts(GeomC C, ExcTable E, con
             const float* q = sm + kSmemStride * i;
             const float p = fmaf(q[2], g2, fmaf(q[1], g1, q[0] * g0));
             float e0, e1, e2;
-            sexp3(-p, e0, e1, e2);
+            sexp3(-p, S.exp_model != 0, e0, e1, e2);
             const float4 s = __ldg(S.s4 + (size_t)i * nb + b);
             neumaier(Ds[0], Dc[0], s.x * e0);
             neumaier(Ds[1], Dc[1], s.y * e0);
@@ -587,7 +588,7 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
             const float4 qa = *reinterpret_cast<const float4*>(sm + kSmemStride * i);
             const float p = fmaf(qa.z, g2, fmaf(qa.y, g1, qa.x * g0));
             float e0, e1, e2;
-            sexp3(-p, e0, e1, e2);
+            sexp3(-p, S.exp_model != 0, e0, e1, e2);
             const float4 s4 = __ldg(S.s4 + (size_t)i * nb + b);
             const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
@@ -636,7 +637,7 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
             for (int i = 0; i < nE; ++i) {
                 const float4 qa = *reinterpret_cast<const float4*>(sm + kSmemStride * i);
                 const float p = fmaf(qa.z, g2, fmaf(qa.y, g1, qa.x * g0));
-                if (p < 0.0f) continue;   // softexp'' = 0 where -p > 0
+                if (p < 0.0f && !S.exp_model) continue;   // softexp'' = 0 where -p > 0
                 const float e2 = expf(-p);
                 const float4 s4 = __ldg(S.s4 + (size_t)i * nb + b);
                 const float beta = e2 * fmaf(qw[3], s4.w, fmaf(qw[2], s4.z, fmaf(qw[1], s4.y, qw[0] * s4.x)));

@@ -36,6 +36,7 @@ struct osscir_ctx {
     double* dtpl_part = nullptr;
     double* dtpl_out = nullptr;   // [0]: at x (on request), [1]: at the last expansion point
     int n_part = 0;
+    int exp_model = 0;   // counts model: 0 softexp (Eq. finalModel), 1 exp (Eq. fullModel)
     int iter = 0;
     // per-iteration graph
     cudaStream_t cap_stream = nullptr;
@@ -46,7 +47,7 @@ struct osscir_ctx {
     cudaEvent_t fork = nullptr, join = nullptr;
 
     osscir::ExcTable exc() const { return osscir::ExcTable{exc_off, exc_ent}; }
-    osscir::SpecD spec() const { return osscir::SpecD{nE, s4, N4, mu}; }
+    osscir::SpecD spec() const { return osscir::SpecD{nE, s4, N4, mu, exp_model}; }
     osscir::SolveD solve() const { return osscir::SolveD{g, c, y, x, xbar, chord, dtpl_part}; }
 };
 

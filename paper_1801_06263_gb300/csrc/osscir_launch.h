@@ -26,6 +26,7 @@ struct SpecD {
     const float4* s4;   // [nE][n_bins]: (s_{1..4,b,i})
     const float4* N4;   // [n_bins]
     const float* mu;    // [3][nE]
+    int exp_model;      // 0: softexp (Eq. finalModel), 1: exp for every energy (Eq. fullModel)
 };
 
 // MOCCA per-solve parameters.

@@ -41,6 +41,7 @@ struct Config {
     bool same(const Config& o) const {
         return std::memcmp(&geom, &o.geom, sizeof geom) == 0 && nE == o.nE && s == o.s && N == o.N && mu == o.mu &&
                params.lambda == o.params.lambda && params.model == o.params.model && params.spc == o.params.spc &&
+               params.counts_model == o.params.counts_model &&
                params.use_box == o.params.use_box && std::memcmp(params.lo, o.params.lo, sizeof params.lo) == 0 &&
                std::memcmp(params.hi, o.params.hi, sizeof params.hi) == 0;
     }
@@ -57,6 +58,7 @@ struct Config {
         mix(&params.lambda, sizeof params.lambda);
         mix(&params.model, sizeof params.model);
         mix(&params.spc, sizeof params.spc);
+        mix(&params.counts_model, sizeof params.counts_model);
         return h;
     }
 };

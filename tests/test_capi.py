@@ -69,6 +69,8 @@ def test_create_rejects_bad_lambda(lib, lam):
 def test_create_rejects_bad_box_and_model(lib):
     g, sp = _args()
     with pytest.raises(_lib.OsscirError):
+        _lib.osscir_create(g, sp.s, sp.N, sp.mu, 1e-6, counts_model=2)
+    with pytest.raises(_lib.OsscirError):
         _lib.osscir_create(g, sp.s, sp.N, sp.mu, 1e-6, box=((0, 0, 1), (1, 1, 0)))
     with pytest.raises(_lib.OsscirError):
         _lib.osscir_create(g, sp.s, sp.N, sp.mu, 1e-6, model=7)

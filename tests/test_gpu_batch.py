@@ -6,7 +6,8 @@ what its own context gives alone (the batched kernels run the same per-ray and
 per-pixel arithmetic), for every launch configuration and after autotuning.
 The solves cover every back-projection view-group count (8, 4, 2 and 1 thread
 groups per pixel), the box-constrained and zero-curvature variants, and the
-diagonal SPC; one plain solve is also checked against the FP64 oracle.
+diagonal SPC and the exp counts model; one plain solve is also checked against
+the FP64 oracle.
 """
 import numpy as np
 import pytest
@@ -25,6 +26,7 @@ SOLVES = [
     (730, 0.05, 8, 16, 1e-7, {}),            # 532,900 pixels: 2 view groups
     (20, 0.9, 1, 9, 1e-7, {}),               # one view: 1 view group
     (33, 0.5, 45, 50, 1e-7, {"spc": 1}),     # diagonal SPC
+    (36, 0.5, 50, 60, 1e-7, {"counts_model": 1}),   # the exp counts model
 ]
 
 
