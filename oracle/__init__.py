@@ -21,7 +21,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "mocca_oracle.c")
+_SRCS = [os.path.join(_HERE, "mocca_oracle.c"), os.path.join(_HERE, "noise_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
@@ -48,11 +48,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, OpenMP over rays/pixels)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB) >= os.path.getmtime(s) for s in _SRCS)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off",
-                           "-fno-fast-math", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+                           "-fno-fast-math", "-fPIC", "-shared", *_SRCS, "-o", tmp, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -91,6 +91,10 @@ def lib():
                                 _dp, _dp, _dp, ct.c_int, _dp]
         L.orc_mocca.restype = ct.c_int
         L.orc_set_threads.argtypes = [ct.c_int]
+        L.orc_philox4x32_10.argtypes = [ct.POINTER(ct.c_uint32), ct.POINTER(ct.c_uint32), ct.POINTER(ct.c_uint32)]
+        L.orc_poisson_draw.argtypes = [ct.c_double, ct.c_uint32, ct.POINTER(ct.c_uint32)]
+        L.orc_poisson_draw.restype = ct.c_double
+        L.orc_poisson_noise.argtypes = [ct.c_int, _dp, ct.c_uint64, _dp]
         L.orc_max_threads.restype = ct.c_int
     return _lib
 
@@ -308,3 +312,23 @@ def mocca(geom, spectra, c, n_iters, lam, state=None, *, box=None, spc="block",
         raise np.linalg.LinAlgError("singular small system inside MOCCA")
     st.n += n_iters
     return st, hist
+
+
+# --------------------------------------------------------------------------- seeded Poisson noise
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of four 32-bit counter words under two key words (noise_oracle.c)."""
+    c = (ct.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ct.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    out = (ct.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, out)
+    return [int(v) for v in out]
+
+
+def poisson_noise(chat, seed: int):
+    """c ~ Poisson(chat) elementwise (any shape), sample i (in C order) drawn from
+    counter (i, t, 0, 0) under key (seed mod 2^32, seed / 2^32)."""
+    chat = _f64(chat)
+    out = np.zeros_like(chat)
+    lib().orc_poisson_noise(int(chat.size), _ptr(chat), ct.c_uint64(int(seed)), _ptr(out))
+    return out
