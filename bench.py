@@ -253,9 +253,7 @@ def run_gpu(args):
     f4 = torch.zeros((w.geom.n_pixels, 4), dtype=torch.float32, device="cuda")
     f4[:, :3] = torch.tensor(w.f_true, dtype=torch.float32, device="cuda")
     chat = R.simulate(f4)
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(w.noise_seed + rank)
-    c = torch.poisson(chat, generator=gen).contiguous()
+    c = _lib.osscir_poisson_noise(chat, w.noise_seed + (rank << 32))
     R.set_counts(c)
     # footprint size: number of (ray, pixel) pairs, the unit of the projector work
     cnt = torch.zeros(w.geom.n_rays, dtype=torch.int32, device="cuda")
@@ -383,9 +381,7 @@ def run_batched(args, rank):
         R = Reconstructor(w.geom, w.spectra, inputs.step_ratio(w.geom.n, w.photons_per_ray))
         f4 = torch.zeros((w.geom.n_pixels, 4), dtype=torch.float32, device="cuda")
         f4[:, :3] = torch.tensor(w.f_true, dtype=torch.float32, device="cuda")
-        gen = torch.Generator(device="cuda")
-        gen.manual_seed(w.noise_seed + 7919 * rank)
-        R.set_counts(torch.poisson(R.simulate(f4), generator=gen).contiguous())
+        R.set_counts(_lib.osscir_poisson_noise(R.simulate(f4), w.noise_seed + (rank << 32)))
         recs.append(R)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -456,9 +452,7 @@ def run_served(args, w, R, chat, rank):
     from paper_1801_06263_gb300 import _lib
     counts = []
     for k in range(args.served):
-        gen = torch.Generator(device="cuda")
-        gen.manual_seed(3000 + 17 * rank + k)
-        counts.append(torch.poisson(chat, generator=gen).cpu().numpy())
+        counts.append(_lib.osscir_poisson_noise(chat, 3000 + k + (rank << 32)).cpu().numpy())
     sp = w.spectra
 
     def run(gaps):
@@ -512,9 +506,7 @@ def run_served_mixed(args, rank):
         R = Reconstructor(w.geom, w.spectra, lam)
         f4 = torch.zeros((w.geom.n_pixels, 4), dtype=torch.float32, device="cuda")
         f4[:, :3] = torch.tensor(w.f_true, dtype=torch.float32, device="cuda")
-        gen = torch.Generator(device="cuda")
-        gen.manual_seed(w.noise_seed)
-        counts.append(torch.poisson(R.simulate(f4), generator=gen).cpu().numpy())
+        counts.append(_lib.osscir_poisson_noise(R.simulate(f4), w.noise_seed + (rank << 32)).cpu().numpy())
         R.close()
     lams = [inputs.step_ratio(w.geom.n, w.photons_per_ray) for w in reqs]
     total_iters = sum(w.n_iters for w in reqs)

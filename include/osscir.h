@@ -185,6 +185,17 @@ osscir_status osscir_footprint_rays(osscir_t h, int l0, int n, int cap, int *cnt
 osscir_status osscir_footprint_pixels(osscir_t h, int k0, int n, int cap, int *cnt, int *idx, float *wt,
                                       void *stream);
 
+/* Seeded Poisson noise: c[i] ~ Poisson(chat[i]) for i < n, the noise of the
+ * paper's simulated data (Sec. 3), drawn on the device without a context.
+ * chat, c: device float[n] (for example [L][4] counts, n = 4 L); chat >= 0
+ * (0, negative or NaN means give 0); counts are exact below 2^24.  Sample i
+ * depends only on (seed, i, chat[i]): uniforms from Philox4x32-10 (Salmon et
+ * al. 2011) at counter (i, t, 0, 0) under key (seed mod 2^32, seed / 2^32);
+ * means below 10 by inversion, larger by the transformed rejection of Hormann
+ * (1993).  Asynchronous on stream.  Errors: OSSCIR_E_INVALID (n < 0, NULL
+ * buffers), OSSCIR_E_CUDA. */
+osscir_status osscir_poisson_noise(const float *chat, int n, uint64_t seed, float *c, void *stream);
+
 /* ------------------------------------------------------------------ batched form
  * Many independent solves, each its own context (any geometry, spectra, mu,
  * parameters; counts loaded with osscir_set_counts), advanced together: each

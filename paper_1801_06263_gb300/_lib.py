@@ -31,7 +31,7 @@ EXPORTS = (
     "osscir_footprint_pixels", "osscir_reconstruct", "osscir_last_kernel_ms", "osscir_dtpl_counts_static",
     "osscir_server_create", "osscir_server_destroy", "osscir_submit", "osscir_poll", "osscir_server_info",
     "osscir_batch_create", "osscir_batch_destroy", "osscir_batch_step", "osscir_batch_get_config",
-    "osscir_batch_set_config", "osscir_batch_last_kernel_ms",
+    "osscir_batch_set_config", "osscir_batch_last_kernel_ms", "osscir_poisson_noise",
 )
 
 
@@ -124,6 +124,7 @@ def load(build_if_missing: bool = True):
         "osscir_batch_get_config": ([vp, ct.POINTER(BatchConfig)], ct.c_int),
         "osscir_batch_set_config": ([vp, ct.POINTER(BatchConfig)], ct.c_int),
         "osscir_batch_last_kernel_ms": ([vp, ct.POINTER(ct.c_float), vp], ct.c_int),
+        "osscir_poisson_noise": ([vp, ct.c_int, ct.c_uint64, vp, vp], ct.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -357,3 +358,15 @@ def osscir_batch_last_kernel_ms(batch, stream=None):
     _check("osscir_batch_last_kernel_ms", load().osscir_batch_last_kernel_ms(ct.c_void_p(batch), ms,
                                                                              _stream(stream)))
     return tuple(ms)
+
+
+def osscir_poisson_noise(chat, seed, out=None, stream=None):
+    """Seeded Poisson draws of the expected counts chat (contiguous float32 CUDA tensor)
+    into out (same shape, allocated if None); returns out."""
+    import torch
+    out = torch.empty_like(chat) if out is None else out
+    if out.shape != chat.shape:
+        raise ValueError("out must have the shape of chat")
+    _check("osscir_poisson_noise", load().osscir_poisson_noise(_ptr(chat), int(chat.numel()), ct.c_uint64(int(seed)),
+                                                               _ptr(out), _stream(stream)))
+    return out

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libosscir.so")
-SOURCES = ["batch.cu", "capi.cu", "geometry.cu", "mocca.cu", "noalloc.cu", "server.cu"]
+SOURCES = ["batch.cu", "capi.cu", "geometry.cu", "mocca.cu", "noalloc.cu", "noise.cu", "server.cu"]
 HEADERS = ["osscir_internal.cuh", "osscir_launch.h", "osscir_ctx.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -102,3 +102,9 @@ def test_batch_calls_reject_invalid_arguments(lib):
     assert lib.osscir_batch_get_config(null, ct.byref(cfg)) == _lib.OSSCIR_E_INVALID
     assert lib.osscir_batch_set_config(null, ct.byref(cfg)) == _lib.OSSCIR_E_INVALID
     assert lib.osscir_batch_destroy(null) == _lib.OSSCIR_OK
+
+
+def test_poisson_noise_rejects_invalid_arguments(lib):
+    assert lib.osscir_poisson_noise(None, -1, 0, None, None) == _lib.OSSCIR_E_INVALID
+    assert lib.osscir_poisson_noise(None, 4, 0, None, None) == _lib.OSSCIR_E_INVALID
+    assert lib.osscir_poisson_noise(None, 0, 0, None, None) == _lib.OSSCIR_OK
