@@ -513,7 +513,8 @@ int orc_dual_update(const double alpha[12], const double Hp[9], const double r[4
 /* Primal step of one pixel: x' = argmin_{x in C} 1/2 ||x - t||^2_{Tinv}, with
  * t = x - T v (T = Tinv^-1).  C is R^3 or the box [lo, hi]; the box problem is
  * solved by trying every active set (free / at lo / at hi per material) and
- * keeping the feasible candidate of least objective.  A pixel with Tinv = 0 is
+ * keeping the feasible candidate of least objective.  Bounds may be infinite
+ * (nonnegativity is lo = 0, hi = +inf); no active set sits at an infinite one.  A pixel with Tinv = 0 is
  * seen by no ray and keeps x.  A tiny multiple of the trace is added to Tinv,
  * which keeps the step condition M >= 0 (Sec. 2). */
 int orc_primal_update(const double Tinv_in[9], const double v[3], const double x[3], int use_box,
@@ -537,12 +538,14 @@ int orc_primal_update(const double Tinv_in[9], const double v[3], const double x
     for (int code = 0; code < 27; ++code) {
         int st[3] = {code % 3, (code / 3) % 3, code / 9}; /* 0 free, 1 lo, 2 hi */
         double xc[3];
-        int fr[3], nf = 0;
+        int fr[3], nf = 0, unbounded = 0;
         for (int m = 0; m < 3; ++m) {
             if (st[m] == 1) xc[m] = lo[m];
             else if (st[m] == 2) xc[m] = hi[m];
             else fr[nf++] = m;
+            if (st[m] != 0 && isinf(xc[m])) unbounded = 1; /* no point sits at an infinite bound */
         }
+        if (unbounded) continue;
         if (nf > 0) {
             /* Tinv_FF (x_F - t_F) = -Tinv_FB (x_B - t_B) */
             double Mf[9], rhs[3], sol[3];
@@ -558,7 +561,8 @@ int orc_primal_update(const double Tinv_in[9], const double v[3], const double x
             for (int a = 0; a < nf; ++a) {
                 int m = fr[a];
                 double val = t[m] + sol[a];
-                double tol = 1e-12 * (1.0 + fabs(hi[m] - lo[m]));
+                double span = hi[m] - lo[m];
+                double tol = 1e-12 * (1.0 + (isfinite(span) ? fabs(span) : fabs(val)));
                 if (val < lo[m] - tol || val > hi[m] + tol) ok = 0;
                 xc[m] = fmin(fmax(val, lo[m]), hi[m]);
             }

@@ -105,19 +105,28 @@ def test_primal_step_unseen_pixel_keeps_x(orc):
     np.testing.assert_array_equal(orc.primal_update(np.zeros((3, 3)), np.ones(3), x), x)
 
 
+BOXES = {
+    "unit": (np.zeros(3), np.ones(3)),
+    "nonnegative": (np.zeros(3), np.full(3, np.inf)),
+    "half_open_mixed": (np.array([-np.inf, 0.0, -0.5]), np.array([0.5, np.inf, np.inf])),
+}
+
+
+@pytest.mark.parametrize("box", list(BOXES))
 @pytest.mark.parametrize("seed", range(8))
-def test_primal_step_box_matches_bounded_qp(orc, seed):
+def test_primal_step_box_matches_bounded_qp(orc, seed, box):
     rng = np.random.default_rng(100 + seed)
     T = _sym(rng, (50.0, 2.0, 0.1))
     v = rng.normal(scale=3.0, size=3)
     x = rng.uniform(0, 1, size=3)
-    lo, hi = np.zeros(3), np.ones(3)
+    lo, hi = BOXES[box]
     got = orc.primal_update(T, v, x, box=(lo, hi))
     Tr = T + 1e-12 * np.trace(T) * np.eye(3)
     t = x - np.linalg.solve(Tr, v)
     obj = lambda z: 0.5 * (z - t) @ Tr @ (z - t)
     res = scipy.optimize.minimize(obj, np.clip(t, lo, hi), jac=lambda z: Tr @ (z - t),
-                                  bounds=list(zip(lo, hi)), method="L-BFGS-B",
+                                  bounds=[(None if np.isinf(a) else a, None if np.isinf(b) else b)
+                                          for a, b in zip(lo, hi)], method="L-BFGS-B",
                                   options=dict(ftol=1e-15, gtol=1e-12, maxiter=1000))
     assert (got >= lo).all() and (got <= hi).all()
     assert obj(got) <= obj(res.x) + 1e-10

@@ -144,10 +144,11 @@ def test_noiseless_inverse_crime_converges(orc, counts_model):
     assert np.linalg.norm(g1) < 1e-3 * np.linalg.norm(g0)
 
 
-def test_box_constraint_holds_every_iteration(orc):
+@pytest.mark.parametrize("lo,hi", [((0.0, 0.0, 0.0), (1.0, 0.8, 0.012)),
+                                   ((0.0, 0.0, 0.0), (np.inf, np.inf, np.inf))])   # a box; nonnegativity
+def test_box_constraint_holds_every_iteration(orc, lo, hi):
     geom, sp, f = _tiny(3, n=6, views=6, bins=8)
     c = inputs.poisson_counts(orc.counts(geom, sp, f), 8)
-    lo, hi = (0.0, 0.0, 0.0), (1.0, 0.8, 0.012)
     st = None
     for _ in range(30):
         st, _ = orc.mocca(geom, sp, c, 1, 1e-6, st, box=(lo, hi))
