@@ -79,8 +79,9 @@ typedef struct {
  * its negative eigenvalues removed as the curvature of the local quadratic;
  * model = 1 uses zero curvature (a preconditioned gradient step).  use_box = 1
  * constrains every iterate to lo <= f <= hi per material (the convex constraint
- * set of the one-step framework, Sec. 1); 0 leaves f unconstrained (Sec. 2: the
- * softexp model avoids the need for constraints).  spc = 0 selects the
+ * set of the one-step framework, Sec. 1); bounds may be infinite, so lo = 0,
+ * hi = +inf is nonnegativity; 0 leaves f unconstrained (Sec. 2: the softexp
+ * model avoids the need for constraints).  spc = 0 selects the
  * m-block-diagonal step-preconditioner of Sec. 2; spc = 1 the diagonal one of
  * Pock and Chambolle that it replaces (Sigma_wl = (1/lambda) / sum_mk |K|,
  * T_mk = lambda / sum_wl |K|, Sec. 2) — with a material basis orthogonalised

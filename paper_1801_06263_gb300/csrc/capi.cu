@@ -89,7 +89,8 @@ osscir_status validate(const osscir_geometry* g, const osscir_spectra* sp, const
     if (pa->counts_model != 0 && pa->counts_model != 1) return OSSCIR_E_INVALID;
     if (pa->use_box)
         for (int m = 0; m < 3; ++m)
-            if (!std::isfinite(pa->lo[m]) || !std::isfinite(pa->hi[m]) || !(pa->lo[m] <= pa->hi[m]))
+            if (std::isnan(pa->lo[m]) || std::isnan(pa->hi[m]) || !(pa->lo[m] <= pa->hi[m]) ||
+                pa->lo[m] == INFINITY || pa->hi[m] == -INFINITY)
                 return OSSCIR_E_INVALID;
     return OSSCIR_OK;
 }

@@ -699,6 +699,7 @@ __global__ void __launch_bounds__(kFwdThreads, 6) k_mocca_ray(GeomC C, RayRec* r
 
 // Box-constrained primal step: argmin over lo <= x <= hi of 1/2 (x - t)^T Q (x - t),
 // by trying every active set and keeping the feasible candidate of least objective.
+// Bounds may be infinite (nonnegativity: lo = 0, hi = +inf).
 __device__ void box_prox3(const double Q[3][3], const double t[3], const float lo[3], const float hi[3],
                           double xo[3]) {
     double best = 1e308;
@@ -709,12 +710,15 @@ __device__ void box_prox3(const double Q[3][3], const double t[3], const float l
         const int st[3] = {code % 3, (code / 3) % 3, code / 9};
         double xc[3];
         int fr[3], nf = 0;
+        bool unbounded = false;
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
             if (st[m] == 1) xc[m] = lo[m];
             else if (st[m] == 2) xc[m] = hi[m];
             else fr[nf++] = m;
+            if (st[m] != 0 && isinf(xc[m])) unbounded = true;   // no point sits at an infinite bound
         }
+        if (unbounded) continue;
         bool ok = true;
         if (nf > 0) {
             double Mf[3][3], rhs[3];
@@ -744,7 +748,8 @@ __device__ void box_prox3(const double Q[3][3], const double t[3], const float l
             for (int a = 0; a < nf; ++a) {
                 const int m = fr[a];
                 const double val = t[m] + sol[a];
-                const double tol = 1e-12 * (1.0 + fabs((double)hi[m] - (double)lo[m]));
+                const double span = (double)hi[m] - (double)lo[m];
+                const double tol = 1e-12 * (1.0 + (isfinite(span) ? fabs(span) : fabs(val)));
                 if (val < lo[m] - tol || val > hi[m] + tol) ok = false;
                 xc[m] = fmin(fmax(val, (double)lo[m]), (double)hi[m]);
             }

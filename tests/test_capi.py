@@ -72,6 +72,10 @@ def test_create_rejects_bad_box_and_model(lib):
         _lib.osscir_create(g, sp.s, sp.N, sp.mu, 1e-6, counts_model=2)
     with pytest.raises(_lib.OsscirError):
         _lib.osscir_create(g, sp.s, sp.N, sp.mu, 1e-6, box=((0, 0, 1), (1, 1, 0)))
+    inf, nan = float("inf"), float("nan")
+    for box in (((0, 0, inf), (1, 1, inf)), ((0, 0, 0), (1, -inf, 1)), ((0, nan, 0), (1, 1, 1))):
+        with pytest.raises(_lib.OsscirError):
+            _lib.osscir_create(g, sp.s, sp.N, sp.mu, 1e-6, box=box)
     with pytest.raises(_lib.OsscirError):
         _lib.osscir_create(g, sp.s, sp.N, sp.mu, 1e-6, model=7)
 

@@ -92,9 +92,11 @@ def test_small_64_iterates_match_oracle(orc, small, model):
     assert abs(d_gpu - hist[-1]) <= 1e-5 * hist[-1]
 
 
-def test_box_constrained_iterates(orc, small):
+@pytest.mark.parametrize("lo,hi", [((0.0, 0.0, 0.0), (1.05, 1.05, 0.012)),
+                                   ((0.0, 0.0, 0.0), (np.inf, np.inf, np.inf)),        # nonnegativity
+                                   ((-np.inf, 0.0, 0.0), (1.05, np.inf, 0.012))])     # half-open mix
+def test_box_constrained_iterates(orc, small, lo, hi):
     w, s32, c = small
-    lo, hi = (0.0, 0.0, 0.0), (1.05, 1.05, 0.012)
     lam, n_it = 1e-7, 60
     R = _recon(w, lam, box=(lo, hi))
     R.set_counts(torch.tensor(c, device="cuda"))
@@ -103,6 +105,7 @@ def test_box_constrained_iterates(orc, small):
     R.close()
     assert (x >= np.array(lo, np.float32)).all() and (x <= np.array(hi, np.float32)).all()
     st, _ = orc.mocca(w.geom, s32, c.astype(np.float64), n_it, lam, box=(lo, hi))
+    assert np.mean(st.x == 0.0) > 0.05   # the constraint binds
     assert max(_rel(x, st.x)) < REL_L2
 
 
