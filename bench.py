@@ -38,6 +38,9 @@ WORKLOAD_DESC = ("256x256 (0.5 mm), 512 views x 512 bins, 4 windows, 101 energie
                  "(PMMA/Al/Gd), ellipse phantom 4 Al + 6 Gd, Poisson 1e5 photons/ray")
 LAMBDA = 10.0 ** -7.5   # tuned with the oracle: tests/golden/lambda_sweeps.json
 SOLVE_ITERS = 500
+# the larger single solve, for profiling at a size whose working set exceeds L2 (--workload large_512)
+LARGE = ("large_512", "512x512 (0.5 mm), 1024 views x 1024 bins, 4 windows, 101 energies, 3 materials "
+         "(PMMA/Al/Gd), ellipse phantom 4 Al + 6 Gd, Poisson 1e6 photons/ray", 10.0 ** -8.5, 1000)
 def _hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -54,9 +57,9 @@ L1_PEAK_TBPS = 152 * 128 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of each per-iteration kernel, from one
 # ncu --set full capture (cold cache), valid only for the kernel sources it was taken on
 TRAFFIC = {
-    "k_mocca_proj": {"bytes_per_launch": 18874880, "source_sha": "bcda296a3f65f7ea"},
-    "k_mocca_ray": {"bytes_per_launch": 31450880 + 201216, "source_sha": "bcda296a3f65f7ea"},
-    "k_mocca_bp": {"bytes_per_launch": 16078336 + 1024, "source_sha": "bcda296a3f65f7ea"},
+    "k_mocca_proj": {"bytes_per_launch": 18874880, "source_sha": "a5a91d922c89c49b"},
+    "k_mocca_ray": {"bytes_per_launch": 32006144 + 3669248, "source_sha": "a5a91d922c89c49b"},
+    "k_mocca_bp": {"bytes_per_launch": 16079360 + 256, "source_sha": "a5a91d922c89c49b"},
 }
 
 
@@ -564,6 +567,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="medium_256", choices=["medium_256", "large_512"],
+                    help="the 256x256 headline workload, or the 512x512 solve for profiling")
     ap.add_argument("--e2e", type=int, default=3, help="full reconstructions for the end-to-end rate")
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle iterations for the CPU baseline")
     ap.add_argument("--served", type=int, default=16, help="requests for the served measurement (0: skip)")
@@ -575,6 +580,9 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5, help="timed iterations of the batched measurement")
     ap.add_argument("--rate", type=float, default=1.5, help="Poisson request arrival rate, requests/s")
     args = ap.parse_args()
+    if args.workload == "large_512":
+        global WORKLOAD, WORKLOAD_DESC, LAMBDA, SOLVE_ITERS
+        WORKLOAD, WORKLOAD_DESC, LAMBDA, SOLVE_ITERS = LARGE
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
