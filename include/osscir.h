@@ -75,7 +75,7 @@ typedef struct {
 } osscir_spectra;
 
 /* Solver parameters.  lambda is the step-size ratio of the step-preconditioner
- * (Sec. 2, "must be tuned").  model = 0 uses the per-ray Hessian of Sec. 2 with
+ * (Sec. 2 leaves it to tuning).  model = 0 uses the per-ray Hessian of Sec. 2 with
  * its negative eigenvalues removed as the curvature of the local quadratic;
  * model = 1 uses zero curvature (a preconditioned gradient step).  use_box = 1
  * constrains every iterate to lo <= f <= hi per material (the convex constraint

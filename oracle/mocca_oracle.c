@@ -62,7 +62,7 @@ typedef struct {
 } orc_spectra;
 
 typedef struct {
-    double lambda; /* step-size ratio of the SPC (Sec. 2, "must be tuned") */
+    double lambda; /* step-size ratio of the SPC (Sec. 2 leaves it to tuning) */
     int use_box;   /* 0: C = R^3, 1: box lo <= x <= hi                     */
     double lo[3], hi[3];
     int spc;   /* 0: m-block-diagonal SPC (Sec. 2); 1: diagonal SPC (Pock-Chambolle) */
