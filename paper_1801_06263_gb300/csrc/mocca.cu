@@ -564,8 +564,15 @@ __device__ __forceinline__ void proj_ray(const GeomC& C, const ExcTable& E, cons
     D.g[l] = make_float4(gs.x, gs.y, gs.z, 0.f);
 }
 
+// Blocks run views fastest and bin groups centre-out: the long central rays are
+// scheduled first and the short edge rays fill the tail of the grid.
+__device__ __forceinline__ int centre_out(int i, int n) {
+    const int c = (n - 1) / 2;
+    return (i & 1) ? c + (i + 1) / 2 : c - i / 2;
+}
+
 __global__ void __launch_bounds__(kFwdThreads, 8) k_mocca_proj(GeomC C, ExcTable E, const RayRec* rec, SolveD D) {
-    const int l = ray_of_thread(C);
+    const int l = ray_at(C, centre_out(blockIdx.y, gridDim.y), blockIdx.x, kFwdThreads / 32);
     if (l >= 0) proj_ray(C, E, rec, D, l);
 }
 
@@ -905,8 +912,9 @@ __global__ void __launch_bounds__(kBatchProjMaxThreads) k_batch_proj(const Solve
         const int2 w = __ldg(items + it);
         const SolveDesc& d = sd[w.x];
         const GeomC C = d.C;
-        const int nbx = (C.n_bins + 31) >> 5;
-        const int l = ray_at(C, w.y % nbx, w.y / nbx, vb);
+        const int nbx = (C.n_bins + 31) >> 5, nby = (C.n_views + vb - 1) / vb;
+        // views fastest, bin groups centre-out (long central rays first), as in k_mocca_proj
+        const int l = ray_at(C, centre_out(w.y / nby, nbx), w.y % nby, vb);
         if (l >= 0) proj_ray(C, d.E, d.rec, d.D, l);
     }
 }
@@ -985,7 +993,8 @@ cudaError_t launch_counts(const GeomC& C, const ExcTable& E, const RayRec* rec, 
 
 cudaError_t launch_mocca_proj(const GeomC& C, const ExcTable& E, const RayRec* rec, const SolveD& D,
                               cudaStream_t st) {
-    k_mocca_proj<<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, E, rec, D);
+    const dim3 fg = fwd_grid(C.n_bins, C.n_views);
+    k_mocca_proj<<<dim3(fg.y, fg.x), kFwdThreads, 0, st>>>(C, E, rec, D);
     return cudaGetLastError();
 }
 
