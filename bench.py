@@ -57,9 +57,9 @@ L1_PEAK_TBPS = 152 * 128 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of each per-iteration kernel, from one
 # ncu --set full capture (cold cache), valid only for the kernel sources it was taken on
 TRAFFIC = {
-    "k_mocca_proj": {"bytes_per_launch": 18874880, "source_sha": "a5a91d922c89c49b"},
-    "k_mocca_ray": {"bytes_per_launch": 32006144 + 3669248, "source_sha": "a5a91d922c89c49b"},
-    "k_mocca_bp": {"bytes_per_launch": 16079360 + 256, "source_sha": "a5a91d922c89c49b"},
+    "k_mocca_proj": {"bytes_per_launch": 18875904, "source_sha": "fb56752dc9f173e3"},
+    "k_mocca_ray": {"bytes_per_launch": 31977216 + 3606016, "source_sha": "fb56752dc9f173e3"},
+    "k_mocca_bp": {"bytes_per_launch": 16079360 + 256, "source_sha": "fb56752dc9f173e3"},
 }
 
 
