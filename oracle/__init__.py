@@ -41,7 +41,7 @@ class _Spectra(ct.Structure):
 
 class _Params(ct.Structure):
     _fields_ = [("lambda_", ct.c_double), ("use_box", ct.c_int), ("lo", ct.c_double * 3),
-                ("hi", ct.c_double * 3), ("spc", ct.c_int), ("model", ct.c_int)]
+                ("hi", ct.c_double * 3), ("spc", ct.c_int), ("model", ct.c_int), ("inner", ct.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -123,9 +123,9 @@ class _SpecHolder:
                           {"softexp": 0, "exp": 1}[counts_model])
 
 
-def _params(lam, use_box=False, lo=(0, 0, 0), hi=(0, 0, 0), spc="block", model="hessian"):
+def _params(lam, use_box=False, lo=(0, 0, 0), hi=(0, 0, 0), spc="block", model="hessian", inner=1):
     return _Params(float(lam), int(bool(use_box)), (ct.c_double * 3)(*lo), (ct.c_double * 3)(*hi),
-                   {"block": 0, "diagonal": 1}[spc], {"hessian": 0, "gradient": 1}[model])
+                   {"block": 0, "diagonal": 1}[spc], {"hessian": 0, "gradient": 1}[model], int(inner))
 
 
 def set_threads(n: int) -> None:
@@ -294,14 +294,16 @@ class State:
 
 
 def mocca(geom, spectra, c, n_iters, lam, state=None, *, box=None, spc="block",
-          model="hessian", mu=None, counts_model="softexp"):
+          model="hessian", mu=None, counts_model="softexp", inner=1):
     """Run n_iters MOCCA iterations from `state` (zeros if None); returns
     (state, dtpl_history) with dtpl_history[i] = D_TPL(c, c^(xbar_i)).
-    counts_model="exp" replaces softexp by exp (the standard model, Eq. fullModel)."""
+    counts_model="exp" replaces softexp by exp (the standard model, Eq. fullModel).
+    inner=k > 1: nested MOCCA, a new local model every k iterations of this call
+    (the first iteration of a call is always an outer one; see orc_mocca)."""
     sh = _SpecHolder(spectra, mu, counts_model)
     st = State(geom) if state is None else state
     lo, hi = (box if box is not None else ((0, 0, 0), (0, 0, 0)))
-    P = _params(lam, box is not None, tuple(lo), tuple(hi), spc, model)
+    P = _params(lam, box is not None, tuple(lo), tuple(hi), spc, model, inner)
     c = _f64(c)
     hist = np.zeros(n_iters)
     for arr in (st.x, st.xbar, st.y):

@@ -67,6 +67,7 @@ typedef struct {
     double lo[3], hi[3];
     int spc;   /* 0: m-block-diagonal SPC (Sec. 2); 1: diagonal SPC (Pock-Chambolle) */
     int model; /* 0: eigen-clipped Hessian; 1: W = 0 (preconditioned gradient step) */
+    int inner; /* iterations per local model: 1 single-loop MOCCA; k > 1 nested (see orc_mocca) */
 } orc_params;
 
 static const double PI = 3.14159265358979323846;
@@ -667,6 +668,18 @@ void orc_step_matrices(const orc_geometry *G, const orc_spectra *sp, const orc_p
 /* n_iters MOCCA iterations.  State: x = x_n, xbar = 2 x_n - x_{n-1}, y = y_n
  * (all updated in place; start from zeros).  dtpl_hist[it] (if not NULL)
  * receives D_TPL(c, c^(xbar_n)) at the expansion point of iteration it.
+ *
+ * With P->inner = k > 1 the loop is nested (the inner/outer form the paper
+ * mentions and sets aside, Sec. 3): iterations 0, k, 2k, ... of the call are
+ * outer ones, exactly the single-loop iteration above, and they keep each
+ * ray's local model (alpha, the clipped Hessian, r, Sigma^-1 and g0 = X xbar);
+ * the k - 1 iterations after each take one primal-dual step on that fixed
+ * convex model: with g = X xbar, the dual prox acts on
+ *   u = y + Sigma alpha (g - g0)
+ * (the prox argument y + Sigma K xbar, measured from the expansion point
+ * K f0 = alpha g0), y' = u - Sigma (W + Sigma)^-1 (u - r), and K = alpha X keeps
+ * the stored alpha in the back-projection and the step matrix T.  An outer
+ * iteration has g = g0, so u = y and k = 1 is the single-loop method.
  * Returns 0, or -1 if a small system was singular. */
 int orc_mocca(const orc_geometry *G, const orc_spectra *sp, const orc_params *P, const double *c,
               double *x, double *xbar, double *y, int n_iters, double *dtpl_hist) {
@@ -678,8 +691,17 @@ int orc_mocca(const orc_geometry *G, const orc_spectra *sp, const orc_params *P,
     double *Tinv = (double *)malloc(sizeof(double) * (size_t)Pn * 9);
     int *pix = (int *)malloc(sizeof(int) * cap);
     double *len = (double *)malloc(sizeof(double) * cap);
+    const int inner = P->inner > 1 ? P->inner : 1;
+    double *mHp = NULL, *mr = NULL, *msinv = NULL, *mg0 = NULL;   /* the stored local models */
+    if (inner > 1) {
+        mHp = (double *)malloc(sizeof(double) * (size_t)L * 9);
+        mr = (double *)malloc(sizeof(double) * (size_t)L * NW);
+        msinv = (double *)malloc(sizeof(double) * (size_t)L * NW);
+        mg0 = (double *)malloc(sizeof(double) * (size_t)L * NM);
+    }
     int status = 0;
     for (int it = 0; it < n_iters && status == 0; ++it) {
+        const int outer = it % inner == 0;
         /* forward projection at the expansion point f0 = xbar */
         orc_forward(G, xbar, NM, g);
         /* per-ray model, local quadratic and dual step */
@@ -690,18 +712,39 @@ int orc_mocca(const orc_geometry *G, const orc_spectra *sp, const orc_params *P,
 #pragma omp for schedule(static)
             for (int l = 0; l < L; ++l) {
                 const int b = l % G->n_bins;
-                double chat[4], r[4], H[9], Hp[9], sinv[4], yn[4];
+                double chat[4], r[4], H[9], Hp[9], sinv[4], yn[4], u[4];
                 const double *cl = c + (size_t)l * NW;
-                orc_ray_terms(sp, b, g + (size_t)l * NM, cl, chat, r, al + (size_t)l * 12, NULL, H,
-                              NULL, NULL);
+                double *all = al + (size_t)l * 12;
+                if (outer) {
+                    orc_ray_terms(sp, b, g + (size_t)l * NM, cl, chat, r, all, NULL, H, NULL, NULL);
+                    if (P->model == 0) orc_clip_psd3(H, Hp);
+                    else memset(Hp, 0, sizeof Hp);
+                    int cnt = orc_siddon(G, l / G->n_bins, b, pp, ll, cap);
+                    ray_sigma_inv(P, all, cnt, ll, sinv);
+                    memcpy(u, y + (size_t)l * NW, sizeof u);
+                    if (inner > 1) {
+                        memcpy(mHp + (size_t)l * 9, Hp, sizeof Hp);
+                        memcpy(mr + (size_t)l * NW, r, sizeof r);
+                        memcpy(msinv + (size_t)l * NW, sinv, sizeof sinv);
+                        memcpy(mg0 + (size_t)l * NM, g + (size_t)l * NM, sizeof(double) * NM);
+                    }
+                } else {
+                    double dummy[12];   /* D_TPL at xbar as a diagnostic; the model stays fixed */
+                    orc_ray_terms(sp, b, g + (size_t)l * NM, cl, chat, NULL, dummy, NULL, NULL, NULL, NULL);
+                    memcpy(Hp, mHp + (size_t)l * 9, sizeof Hp);
+                    memcpy(r, mr + (size_t)l * NW, sizeof r);
+                    memcpy(sinv, msinv + (size_t)l * NW, sizeof sinv);
+                    const double *gl = g + (size_t)l * NM, *g0 = mg0 + (size_t)l * NM;
+                    for (int w = 0; w < NW; ++w) {
+                        double kz = 0.0;   /* (K (xbar - f0))_w = alpha_w . (g - g0) */
+                        for (int m = 0; m < NM; ++m) kz += all[w * NM + m] * (gl[m] - g0[m]);
+                        u[w] = y[(size_t)l * NW + w] + (sinv[w] > 0.0 ? kz / sinv[w] : 0.0);
+                    }
+                }
                 double d = 0.0;
                 for (int w = 0; w < NW; ++w) d += dtpl_term(chat[w], cl[w]);
                 dt[l] = d;
-                if (P->model == 0) orc_clip_psd3(H, Hp);
-                else memset(Hp, 0, sizeof Hp);
-                int cnt = orc_siddon(G, l / G->n_bins, b, pp, ll, cap);
-                ray_sigma_inv(P, al + (size_t)l * 12, cnt, ll, sinv);
-                if (orc_dual_update(al + (size_t)l * 12, Hp, r, sinv, P->model, y + (size_t)l * NW, yn)) {
+                if (orc_dual_update(all, Hp, r, sinv, P->model, u, yn)) {
 #pragma omp atomic write
                     status = -1;
                 }
@@ -744,5 +787,9 @@ int orc_mocca(const orc_geometry *G, const orc_spectra *sp, const orc_params *P,
     free(Tinv);
     free(pix);
     free(len);
+    free(mHp);
+    free(mr);
+    free(msinv);
+    free(mg0);
     return status;
 }

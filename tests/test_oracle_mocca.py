@@ -169,3 +169,77 @@ def test_thread_count_does_not_change_results(orc):
     np.testing.assert_array_equal(a.x, b.x)
     np.testing.assert_array_equal(a.y, b.y)
     np.testing.assert_array_equal(ha, hb)
+
+
+# ---------------------------------------------------------------- nested (inner/outer) MOCCA
+
+def _convex_case(orc):
+    geom = inputs.make_geometry(4, 1.0, 16, 12)
+    base = inputs.make_spectra(geom.n_bins, 5e3)
+    E = base.energies
+    s = np.zeros_like(base.s)
+    idx = [int(np.argmin(np.abs(E - e))) for e in (28.0, 45.0, 58.0, 85.0)]
+    for w, i in enumerate(idx):
+        s[:, i, w] = 1.0
+    mu = np.zeros_like(base.mu)
+    mu[:, idx] = [[0.30, 0.22, 0.18, 0.15], [0.60, 0.20, 0.10, 0.06], [0.20, 0.10, 0.60, 0.30]]
+    sp = inputs.Spectra(E, s, base.N, mu)
+    f_true = np.tile(np.array([[0.9, 0.4, 0.3]]), (geom.n_pixels, 1))
+    c = inputs.poisson_counts(orc.counts(geom, sp, f_true), 21)
+    return geom, sp, f_true, c
+
+
+@pytest.mark.parametrize("inner", [2, 5])
+def test_nested_mocca_reaches_the_minimiser(orc, inner):
+    """Nested MOCCA (a new local model every `inner` iterations) reaches the same
+    convex D_TPL minimiser that scipy's BFGS finds from the truth."""
+    geom, sp, f_true, c = _convex_case(orc)
+    fun = lambda v: orc.objective(geom, sp, c, v.reshape(-1, 3))
+    res = scipy.optimize.minimize(lambda v: fun(v)[0], f_true.ravel(), jac=lambda v: fun(v)[1].ravel(),
+                                  method="BFGS", options=dict(gtol=1e-10, maxiter=5000))
+    d_star = fun(res.x)[0]
+    f_star = res.x.reshape(-1, 3)
+    st, hist = orc.mocca(geom, sp, c, 2000, 1e-3, inner=inner)
+    assert np.all(np.isfinite(hist))
+    assert abs(orc.objective(geom, sp, c, st.x, with_grad=False) - d_star) <= 1e-10 * d_star
+    assert np.linalg.norm(st.x - f_star) <= 1e-7 * np.linalg.norm(f_star)
+
+
+def test_frozen_model_solves_the_local_quadratic(orc):
+    """With a single outer iteration (inner = all iterations) the primal-dual steps
+    minimise the local convex model built at f0 = 0: D(f0) + r^T K f + 1/2 f^T K^T W K f
+    with the per-ray W = G^T H+ G, i.e. f = -(K^T W K)^-1 K^T r.  K, r and W come from
+    the dense restatement (tests/_dense.py), not from the oracle."""
+    geom, sp, f_true, c = _convex_case(orc)
+    X = _dense.dense_X(geom)
+    L, P, nE = geom.n_rays, geom.n_pixels, sp.s.shape[1]
+    M = _dense.model_matrices(geom, sp, X, np.zeros((P, 3)), c)
+    K, r, A, B = M["K"], M["r"], M["A"], M["B"]
+    Btr = B.T @ r
+    cvec = M["chat"] + r
+    W = np.zeros((4 * L, 4 * L))
+    for l in range(L):
+        rows = [w * L + l for w in range(4)]
+        if not np.any(X[l]):
+            continue
+        k0 = int(np.flatnonzero(X[l])[0])
+        alpha = K[rows][:, [m * P + k0 for m in range(3)]] / X[l, k0]
+        Zl = sp.mu.T
+        seg = slice(l * nE, (l + 1) * nE)
+        Al = A[rows][:, seg]
+        H = -Zl.T @ np.diag(Btr[seg]) @ Zl + Zl.T @ Al.T @ np.diag(cvec[rows]) @ Al @ Zl
+        lamH, V = np.linalg.eigh(H)
+        G = np.linalg.pinv(alpha)
+        W[np.ix_(rows, rows)] = G.T @ (V @ np.diag(np.maximum(lamH, 0)) @ V.T) @ G
+    f_q = np.linalg.solve(K.T @ W @ K, -K.T @ r).reshape(3, P).T
+    n = 2000
+    st, _ = orc.mocca(geom, sp, c, n, 1e-3, inner=n)
+    assert np.linalg.norm(st.x - f_q) <= 1e-8 * np.linalg.norm(f_q)
+
+
+def test_inner_one_is_the_single_loop(orc):
+    geom, sp, f = _tiny(2)
+    c = inputs.poisson_counts(orc.counts(geom, sp, f), 4)
+    a, ha = orc.mocca(geom, sp, c, 25, 1e-6)
+    b, hb = orc.mocca(geom, sp, c, 25, 1e-6, inner=1)
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.y, b.y) and np.array_equal(ha, hb)
