@@ -298,6 +298,7 @@ def run_gpu(args):
     e2e_rate, _ = whole_job_rate(ws, e2e_steps * SOLVE_ITERS, time.perf_counter() - t0)
     finite = bool(torch.isfinite(maps_host).all().item())
 
+    nested = run_nested(args, w, c) if args.nested else None
     served = run_served(args, w, R, chat, rank) if args.served > 0 else None
     batched = run_batched(args, rank) if args.batch > 0 else None
     mixed = run_served_mixed(args, rank) if args.mixed > 0 else None
@@ -355,6 +356,7 @@ def run_gpu(args):
                 "step": f"one {SOLVE_ITERS}-iteration reconstruction via osscir_reconstruct (pinned host buffers)",
                 "recon_per_s": e2e_rate / SOLVE_ITERS},
         "plain_recon_per_s": e2e_rate / SOLVE_ITERS,
+        "nested": nested,
         "served": served,
         "batched": batched,
         "served_mixed": mixed,
@@ -366,6 +368,36 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
     R.close()
     return 0
+
+
+def run_nested(args, w, c):
+    """Nested MOCCA (a new local model every k iterations; k = 1 is the single
+    loop) on the headline workload: device time of the iterations and D_TPL at
+    the maps x after 50, 100, 200 and SOLVE_ITERS iterations from zero."""
+    import torch
+    from paper_1801_06263_gb300 import Reconstructor
+
+    marks = [m for m in (50, 100, 200) if m < SOLVE_ITERS] + [SOLVE_ITERS]
+    stream = torch.cuda.current_stream()
+    out = {}
+    for k in args.nested:
+        R = Reconstructor(w.geom, w.spectra, LAMBDA, inner=k)
+        R.set_counts(c)
+        R.step(2 * k)                                   # warm-up (both graphs)
+        R.set_counts(c)
+        done, ms, rows = 0, 0.0, []
+        for m in marks:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            R.step(m - done)
+            b.record(stream)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+            done = m
+            rows.append({"iterations": m, "ms": ms, "dtpl_at_x": R.dtpl(0)})
+        R.close()
+        out[str(k)] = {"ms_per_iteration": ms / done, "trajectory": rows}
+    return out
 
 
 def run_batched(args, rank):
@@ -579,6 +611,8 @@ def main():
                     help="Poisson arrival rates of the mixed served sweep, requests/s")
     ap.add_argument("--batch-steps", type=int, default=5, help="timed iterations of the batched measurement")
     ap.add_argument("--rate", type=float, default=1.5, help="Poisson request arrival rate, requests/s")
+    ap.add_argument("--nested", type=int, nargs="*", default=[1, 2, 4, 8],
+                    help="iterations per local model for the nested MOCCA leg (none: skip)")
     args = ap.parse_args()
     if args.workload == "large_512":
         global WORKLOAD, WORKLOAD_DESC, LAMBDA, SOLVE_ITERS

@@ -89,7 +89,15 @@ typedef struct {
  * the softexp counts model of Eq. (finalModel); counts_model = 1 the standard
  * model of Eq. (fullModel) with exp for every energy (the paper's softexp
  * replaces it so that negative line integrals do not make the counts blow up);
- * it applies to osscir_simulate and osscir_dtpl as well as to the iteration. */
+ * it applies to osscir_simulate and osscir_dtpl as well as to the iteration.
+ * inner = k > 1 (at most 1e6; 0 means 1) runs the nested inner/outer form that
+ * Sec. 3 mentions and sets aside: one outer iteration, the single-loop
+ * iteration, builds each ray's local convex model (alpha, the clipped Hessian,
+ * the residual r, Sigma^-1 and g0 = X xbar) and keeps it; the next k - 1 inner
+ * iterations are primal-dual steps on that fixed model (the dual prox at
+ * u = y + Sigma alpha (X xbar - g0); the stored alpha in K and in T), without
+ * evaluating the spectral model.  k = 1 is the single-loop method.  Nested
+ * solves are stepped with osscir_mocca_step only (not in a batch or server). */
 typedef struct {
     double lambda;
     int model;
@@ -97,6 +105,7 @@ typedef struct {
     float lo[3], hi[3];
     int spc;
     int counts_model;
+    int inner;
 } osscir_params;
 
 /* Human-readable name of a status code (static string). */
@@ -141,7 +150,10 @@ osscir_status osscir_set_counts(osscir_t h, const float *c, void *stream);
 
 /* Run n_iters MOCCA iterations (Sec. 1: local convex quadratic, removal of
  * negative curvature, one preconditioned CPPD step; Sec. 2: the m-block-diagonal
- * Sigma and T).  Library-owned state; asynchronous on the stream. */
+ * Sigma and T).  Library-owned state; asynchronous on the stream.  With
+ * params.inner = k > 1 the iterations continue the nested cycle across calls:
+ * the first after osscir_create, osscir_set_counts, osscir_set_state or
+ * osscir_reconstruct is an outer one, then every k-th. */
 osscir_status osscir_mocca_step(osscir_t h, int n_iters, void *stream);
 
 /* End-to-end reconstruction with host buffers: copies the counts c (host
@@ -165,15 +177,17 @@ osscir_status osscir_get_maps(osscir_t h, float *x_out, void *stream);
 /* Checkpoint / resume of the solver state (x_n, xbar_n, y_n, n).  All arrays
  * are device pointers: x, xbar float[P][4], y float[L][4].  get copies out,
  * set copies in; resuming from a saved state reproduces the uninterrupted
- * iterates bit for bit.  iter: host int. */
+ * iterates bit for bit.  iter: host int.  The kept local models of a nested
+ * solve are not part of the state: the first iteration after set is an outer one. */
 osscir_status osscir_get_state(osscir_t h, float *x, float *xbar, float *y, int *iter, void *stream);
 osscir_status osscir_set_state(osscir_t h, const float *x, const float *xbar, const float *y, int iter,
                                void *stream);
 
 /* D_TPL (Eq. DTPL) of the loaded counts: which = 0 evaluates it at the current
  * maps x_n (one extra forward projection); which = 1 returns the value the last
- * iteration computed at its expansion point xbar.  Synchronises the stream;
- * out: host double. */
+ * iteration computed at its expansion point xbar (for a nested solve, the last
+ * outer iteration: inner iterations do not evaluate the counts model).
+ * Synchronises the stream; out: host double. */
 osscir_status osscir_dtpl(osscir_t h, int which, double *out, void *stream);
 
 /* Footprint dumps for verification: for rays [l0, l0+n) (or pixels [k0, k0+n))

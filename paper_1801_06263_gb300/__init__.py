@@ -24,13 +24,14 @@ class Reconstructor:
     """
 
     def __init__(self, geom, spectra, lam: float, *, model: int = 0, box=None, mu=None, spc: int = 0,
-                 counts_model: int = 0):
+                 counts_model: int = 0, inner: int = 1):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
         self.geom = geom
         self.handle = osscir_create(geom, spectra.s, spectra.N, spectra.mu if mu is None else mu, lam,
-                                    model=model, box=box, spc=spc, counts_model=counts_model)
+                                    model=model, box=box, spc=spc, counts_model=counts_model,
+                                    inner=inner)
         self.n_pixels, self.n_rays, self.n_fp64_pairs = osscir_info(self.handle)
 
     # -- tensors

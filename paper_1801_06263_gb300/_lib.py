@@ -53,7 +53,8 @@ class Spectra(ct.Structure):
 
 class Params(ct.Structure):
     _fields_ = [("lambda_", ct.c_double), ("model", ct.c_int), ("use_box", ct.c_int),
-                ("lo", ct.c_float * 3), ("hi", ct.c_float * 3), ("spc", ct.c_int), ("counts_model", ct.c_int)]
+                ("lo", ct.c_float * 3), ("hi", ct.c_float * 3), ("spc", ct.c_int), ("counts_model", ct.c_int),
+                ("inner", ct.c_int)]
 
 
 class Request(ct.Structure):
@@ -172,13 +173,13 @@ def _geometry(geom):
                     float(geom.sdd_mm))
 
 
-def _params(lam, model=0, box=None, spc=0, counts_model=0):
+def _params(lam, model=0, box=None, spc=0, counts_model=0, inner=1):
     lo, hi = (box if box is not None else ((0.0,) * 3, (0.0,) * 3))
     return Params(float(lam), int(model), int(box is not None), (ct.c_float * 3)(*lo), (ct.c_float * 3)(*hi),
-                  int(spc), int(counts_model))
+                  int(spc), int(counts_model), int(inner))
 
 
-def osscir_create(geom, s, N, mu, lam, model=0, box=None, spc=0, counts_model=0):
+def osscir_create(geom, s, N, mu, lam, model=0, box=None, spc=0, counts_model=0, inner=1):
     """geom: object with the osscir_geometry fields; s [n_bins, nE, 4], N [n_bins, 4],
     mu [3, nE] host arrays (copied).  Returns the handle (int)."""
     L = load()
@@ -188,7 +189,7 @@ def osscir_create(geom, s, N, mu, lam, model=0, box=None, spc=0, counts_model=0)
     g = _geometry(geom)
     sp = Spectra(int(s32.shape[1]), s32.ctypes.data_as(ct.POINTER(ct.c_float)),
                  N32.ctypes.data_as(ct.POINTER(ct.c_float)))
-    p = _params(lam, model, box, spc, counts_model)
+    p = _params(lam, model, box, spc, counts_model, inner)
     h = ct.c_void_p()
     _check("osscir_create", L.osscir_create(ct.byref(g), ct.byref(sp),
                                             mu32.ctypes.data_as(ct.POINTER(ct.c_float)), ct.byref(p),
@@ -293,7 +294,8 @@ def osscir_server_destroy(server):
     _check("osscir_server_destroy", load().osscir_server_destroy(ct.c_void_p(server)))
 
 
-def osscir_submit(server, geom, s, N, mu, lam, counts, n_iters, model=0, box=None, spc=0, counts_model=0):
+def osscir_submit(server, geom, s, N, mu, lam, counts, n_iters, model=0, box=None, spc=0, counts_model=0,
+                  inner=1):
     """Host numpy arrays (copied by the call): s [n_bins, nE, 4], N [n_bins, 4], mu [3, nE],
     counts [L, 4].  Returns the ticket."""
     s32 = np.ascontiguousarray(s, dtype=np.float32)
@@ -302,7 +304,7 @@ def osscir_submit(server, geom, s, N, mu, lam, counts, n_iters, model=0, box=Non
     c32 = np.ascontiguousarray(counts, dtype=np.float32)
     fptr = lambda a: a.ctypes.data_as(ct.POINTER(ct.c_float))
     req = Request(_geometry(geom), Spectra(int(s32.shape[1]), fptr(s32), fptr(N32)), fptr(mu32),
-                  _params(lam, model, box, spc, counts_model), fptr(c32), int(n_iters))
+                  _params(lam, model, box, spc, counts_model, inner), fptr(c32), int(n_iters))
     t = ct.c_uint64()
     _check("osscir_submit", load().osscir_submit(ct.c_void_p(server), ct.byref(req), ct.byref(t)))
     return t.value

@@ -42,6 +42,8 @@ void free_ctx(osscir_ctx* h) {
     cudaDeviceSynchronize();
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->gexec_in) cudaGraphExecDestroy(h->gexec_in);
+    if (h->graph_in) cudaGraphDestroy(h->graph_in);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->side_stream) cudaStreamDestroy(h->side_stream);
     for (cudaEvent_t e : h->ev)
@@ -49,7 +51,7 @@ void free_ctx(osscir_ctx* h) {
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->join) cudaEventDestroy(h->join);
     void* ptrs[] = {h->rec, h->r64, h->views, h->chord, h->exc_off, h->exc_ent, h->s4, h->N4, h->mu,
-                    h->g, h->c, h->y, h->x, h->xbar, h->dtpl_part, h->dtpl_out};
+                    h->g, h->c, h->y, h->x, h->xbar, h->dtpl_part, h->dtpl_out, h->model};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -87,6 +89,7 @@ osscir_status validate(const osscir_geometry* g, const osscir_spectra* sp, const
     if (pa->model != 0 && pa->model != 1) return OSSCIR_E_INVALID;
     if (pa->spc != 0 && pa->spc != 1) return OSSCIR_E_INVALID;
     if (pa->counts_model != 0 && pa->counts_model != 1) return OSSCIR_E_INVALID;
+    if (pa->inner < 0 || pa->inner > 1000000) return OSSCIR_E_INVALID;
     if (pa->use_box)
         for (int m = 0; m < 3; ++m)
             if (std::isnan(pa->lo[m]) || std::isnan(pa->hi[m]) || !(pa->lo[m] <= pa->hi[m]) ||
@@ -129,6 +132,7 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     h->params.model = pa->model;
     h->params.spc = pa->spc;
     h->exp_model = pa->counts_model;
+    h->inner = pa->inner > 1 ? pa->inner : 1;
     h->params.use_box = pa->use_box;
     for (int m = 0; m < 3; ++m) {
         h->params.lo[m] = pa->lo[m];
@@ -152,6 +156,7 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     CK(dalloc(&h->xbar, P));
     CK(dalloc(&h->dtpl_part, h->n_part));
     CK(dalloc(&h->dtpl_out, 2));
+    if (h->inner > 1) CK(dalloc(&h->model, (size_t)kModelStride * L));
     CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
     for (cudaEvent_t& e : h->ev) CK(cudaEventCreate(&e));
@@ -201,15 +206,27 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
 // One MOCCA iteration as launches on a stream (captured into a graph once).
 // One iteration on st: projection, per-ray step, back-projection; the D_TPL
 // reduction needs only the per-ray partials, so it runs on a side branch
-// beside the back-projection and joins before the iteration ends.
-cudaError_t enqueue_iteration(osscir_ctx* h, cudaStream_t st) {
+// beside the back-projection and joins before the iteration ends.  For a
+// nested solve the outer iteration also keeps the rays' models, and an inner
+// one (inner_step) replaces the per-ray step by the dual step on them.
+cudaError_t enqueue_iteration(osscir_ctx* h, cudaStream_t st, bool inner_step) {
     cudaError_t e = cudaEventRecordWithFlags(h->ev[0], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
     e = launch_mocca_proj(h->gc, h->exc(), h->rec, h->solve(), st);
     if (e != cudaSuccess) return e;
     e = cudaEventRecordWithFlags(h->ev[1], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
-    e = launch_mocca_ray(h->gc, h->rec, h->spec(), h->params, h->solve(), st);
+    if (inner_step) {
+        e = launch_mocca_ray_inner(h->gc, h->rec, h->solve(), st);
+        if (e != cudaSuccess) return e;
+        e = cudaEventRecordWithFlags(h->ev[2], st, cudaEventRecordExternal);
+        if (e != cudaSuccess) return e;
+        e = launch_mocca_bp(h->gc, h->exc(), h->rec, h->views, h->params, h->solve(), st);
+        if (e != cudaSuccess) return e;
+        return cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal);
+    }
+    e = h->inner > 1 ? launch_mocca_ray_keep(h->gc, h->rec, h->spec(), h->params, h->solve(), st)
+                     : launch_mocca_ray(h->gc, h->rec, h->spec(), h->params, h->solve(), st);
     if (e != cudaSuccess) return e;
     e = cudaEventRecord(h->fork, st);
     if (e != cudaSuccess) return e;
@@ -228,10 +245,9 @@ cudaError_t enqueue_iteration(osscir_ctx* h, cudaStream_t st) {
     return cudaStreamWaitEvent(st, h->join, 0);
 }
 
-osscir_status ensure_graph(osscir_ctx* h) {
-    if (h->gexec) return OSSCIR_OK;
+osscir_status capture(osscir_ctx* h, bool inner_step, cudaGraph_t* graph, cudaGraphExec_t* exec) {
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-    const cudaError_t e = enqueue_iteration(h, h->cap_stream);
+    const cudaError_t e = enqueue_iteration(h, h->cap_stream, inner_step);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
     if (e != cudaSuccess) {
@@ -239,8 +255,17 @@ osscir_status ensure_graph(osscir_ctx* h) {
         return from_cuda(e);
     }
     CK(e2);
-    h->graph = g;
-    CK(cudaGraphInstantiate(&h->gexec, g, 0));
+    *graph = g;
+    CK(cudaGraphInstantiate(exec, g, 0));
+    return OSSCIR_OK;
+}
+
+osscir_status ensure_graph(osscir_ctx* h) {
+    if (!h->gexec) {
+        const osscir_status s = capture(h, false, &h->graph, &h->gexec);
+        if (s != OSSCIR_OK) return s;
+    }
+    if (h->inner > 1 && !h->gexec_in) return capture(h, true, &h->graph_in, &h->gexec_in);
     return OSSCIR_OK;
 }
 
@@ -340,6 +365,7 @@ osscir_status osscir_set_counts(osscir_t h, const float* c, void* stream) {
     CK(cudaMemsetAsync(h->x, 0, sizeof(float4) * h->P, st));
     CK(cudaMemsetAsync(h->xbar, 0, sizeof(float4) * h->P, st));
     h->iter = 0;
+    h->phase = 0;
     return OSSCIR_OK;
 }
 
@@ -348,8 +374,11 @@ osscir_status osscir_mocca_step(osscir_t h, int n_iters, void* stream) {
     if (n_iters == 0) return OSSCIR_OK;
     const osscir_status s = ensure_graph(h);
     if (s != OSSCIR_OK) return s;
-    for (int i = 0; i < n_iters; ++i) CK(cudaGraphLaunch(h->gexec, as_stream(stream)));
-    h->iter += n_iters;
+    for (int i = 0; i < n_iters; ++i) {
+        CK(cudaGraphLaunch(h->phase == 0 ? h->gexec : h->gexec_in, as_stream(stream)));
+        h->iter += 1;
+        h->phase = (h->phase + 1) % h->inner;
+    }
     return OSSCIR_OK;
 }
 
@@ -362,6 +391,7 @@ osscir_status osscir_reconstruct(osscir_t h, const float* c_host, int n_iters, f
     CK(cudaMemsetAsync(h->x, 0, sizeof(float4) * h->P, st));
     CK(cudaMemsetAsync(h->xbar, 0, sizeof(float4) * h->P, st));
     h->iter = 0;
+    h->phase = 0;
     const osscir_status s = osscir_mocca_step(h, n_iters, stream);
     if (s != OSSCIR_OK) return s;
     CK(cudaMemcpyAsync(maps_out_host, h->x, sizeof(float4) * h->P, cudaMemcpyDeviceToHost, st));
@@ -401,6 +431,7 @@ osscir_status osscir_set_state(osscir_t h, const float* x, const float* xbar, co
     CK(cudaMemcpyAsync(h->xbar, xbar, sizeof(float4) * h->P, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(h->y, y, sizeof(float4) * h->L, cudaMemcpyDeviceToDevice, st));
     h->iter = iter;
+    h->phase = 0;
     return OSSCIR_OK;
 }
 

@@ -438,8 +438,9 @@ __device__ __forceinline__ bool inv_sym3(const double a[6], double o[6]) {
 // (push-through identity: the rank-3 update is solved in the 3-dim space of g).
 // The Hessian and its clip are FP64; the rest, whose Gram matrix alpha^T alpha
 // has a condition number near 1e7, is double-float.  Returns y' in yo.
+template <bool KEEP>
 __device__ void ray_dual(const float al[4][3], const float sinv[4], const double cw[4], const double rw[4],
-                         const float Bt[6], const float y[4], float yo[4]) {
+                         const float Bt[6], const float y[4], float yo[4], float Bm[4][4]) {
     const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
     double Hd[6];
     {
@@ -487,6 +488,9 @@ __device__ void ray_dual(const float al[4][3], const float sinv[4], const double
         if (!(det.hi != 0.0f) || !isfinite(det.hi)) {   // degenerate alpha: no curvature term, y' = r
 #pragma unroll
             for (int w = 0; w < 4; ++w) yo[w] = df_f(r[w]);
+            if (KEEP)
+                for (int w = 0; w < 4; ++w)
+                    for (int j = 0; j < 4; ++j) Bm[w][j] = 0.0f;
             return;
         }
         const dfl id = df_rcp(det);
@@ -550,6 +554,23 @@ __device__ void ray_dual(const float al[4][3], const float sinv[4], const double
 #pragma unroll
     for (int w = 0; w < 4; ++w)
         yo[w] = df_f(df_add(r[w], df_add(df_add(df_mul(G[0][w], z[0]), df_mul(G[1][w], z[1])), df_mul(G[2][w], z[2]))));
+    if (KEEP) {
+        // the linear map of the prox: y' = r + B (u - r), column j from the same solve with
+        // Sigma^-1 e_j in place of Sigma^-1 (y - r), i.e. right-hand side H+ Gs[:, j]
+        for (int j = 0; j < 4; ++j) {
+            dfl q[3], zj[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                q[i] = df_add(df_add(df_mul(H[sidx[i][0]], Gs[0][j]), df_mul(H[sidx[i][1]], Gs[1][j])),
+                              df_mul(H[sidx[i][2]], Gs[2][j]));
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                zj[i] = df_mul(idet, df_add(df_add(df_mul(C[i][0], q[0]), df_mul(C[i][1], q[1])), df_mul(C[i][2], q[2])));
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                Bm[w][j] = df_f(df_add(df_add(df_mul(G[0][w], zj[0]), df_mul(G[1][w], zj[1])), df_mul(G[2][w], zj[2])));
+        }
+    }
 }
 
 // ------------------------------------------------------------------ fused MOCCA kernels
@@ -578,6 +599,7 @@ __global__ void __launch_bounds__(kFwdThreads, 8) k_mocca_proj(GeomC C, ExcTable
 
 // a2-a5 and the per-ray half of a8: spectral model, curvature, dual step.
 // Returns the ray's D_TPL terms; sm holds the block's mu table (load_mu_smem).
+template <bool KEEP>
 __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const SpecD& S, const StepParams& P,
                                            const SolveD& D, const float* sm, int l) {
     double dsum = 0.0;
@@ -631,12 +653,26 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
         const float X1 = __ldg(D.chord + l);
         const float y[4] = {yy.x, yy.y, yy.z, yy.w};
         float yo[4];
+        float Bm[4][4], sinv[4];   // the prox map and Sigma^-1, kept for nested MOCCA
+        // a5: dual step matrix.  m-block SPC: (Sigma^-1)_w = lambda sum_k sqrt(sum_m K^2)
+        // = lambda |alpha_w| (X 1)_l;  diagonal SPC: lambda sum_mk |K| = lambda (sum_m |alpha_wm|) (X 1)_l
+        auto sigma_inv = [&]() {
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                sinv[w] = P.lambda * X1 *
+                          (P.spc == 0 ? nw[w] : fabsf(al[w][0]) + fabsf(al[w][1]) + fabsf(al[w][2]));
+        };
         if (!(X1 > 0.f)) {   // the ray misses the image: Sigma^-1 = 0, the dual is kept
 #pragma unroll
             for (int w = 0; w < 4; ++w) yo[w] = y[w];
         } else if (P.model == 1) {   // W = 0: y' = y - Sigma Sigma^-1 (y - r) = r
 #pragma unroll
             for (int w = 0; w < 4; ++w) yo[w] = rw[w];
+            if (KEEP) {
+                sigma_inv();
+                for (int w = 0; w < 4; ++w)
+                    for (int j = 0; j < 4; ++j) Bm[w][j] = 0.0f;
+            }
         } else {
             // second pass: sum_i beta_i mu_i mu_i^T, beta_i = softexp''(-p_i) sum_w (r_w / D_w) s_wi
             float Bt[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -657,14 +693,27 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
                 Bt[4] = fmaf(beta, qb.w, Bt[4]);
                 Bt[5] = fmaf(beta, qc.x, Bt[5]);
             }
-            // a5: dual step matrix.  m-block SPC: (Sigma^-1)_w = lambda sum_k sqrt(sum_m K^2)
-            // = lambda |alpha_w| (X 1)_l;  diagonal SPC: lambda sum_mk |K| = lambda (sum_m |alpha_wm|) (X 1)_l
-            float sinv[4];
+            sigma_inv();
+            ray_dual<KEEP>(al, sinv, cw, rw, Bt, y, yo, Bm);
+        }
+        if (KEEP) {
+            float4* M = D.model + (size_t)kModelStride * l;
 #pragma unroll
-            for (int w = 0; w < 4; ++w)
-                sinv[w] = P.lambda * X1 *
-                          (P.spc == 0 ? nw[w] : fabsf(al[w][0]) + fabsf(al[w][1]) + fabsf(al[w][2]));
-            ray_dual(al, sinv, cw, rw, Bt, y, yo);
+            for (int m = 0; m < 3; ++m) M[m] = make_float4(al[0][m], al[1][m], al[2][m], al[3][m]);
+            M[3] = make_float4(g0, g1, g2, X1 > 0.f ? 1.0f : 0.0f);
+            float rh[4], rl[4];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                rh[w] = __double2float_rn(rw[w]);
+                rl[w] = __double2float_rn(rw[w] - (double)rh[w]);
+            }
+            M[4] = make_float4(rh[0], rh[1], rh[2], rh[3]);
+            M[5] = make_float4(rl[0], rl[1], rl[2], rl[3]);
+            if (X1 > 0.f) {   // a ray outside the image (flag 0) keeps its dual: nothing more is read
+                M[6] = make_float4(sinv[0], sinv[1], sinv[2], sinv[3]);
+#pragma unroll
+                for (int w = 0; w < 4; ++w) M[7 + w] = make_float4(Bm[w][0], Bm[w][1], Bm[w][2], Bm[w][3]);
+            }
         }
         const float yf[4] = {(float)yo[0], (float)yo[1], (float)yo[2], (float)yo[3]};
         D.y[l] = make_float4(yf[0], yf[1], yf[2], yf[3]);
@@ -694,14 +743,58 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
     return dsum;
 }
 
+template <bool KEEP>
 __global__ void __launch_bounds__(kFwdThreads, 6) k_mocca_ray(GeomC C, RayRec* rec, SpecD S, StepParams P,
                                                               SolveD D) {
     __shared__ float sm[kSmemStride * kMaxEnergies];
     load_mu_smem(S, sm);
     __syncthreads();
     const int l = ray_of_thread(C);
-    const double dsum = l >= 0 ? ray_step(C, rec, S, P, D, sm, l) : 0.0;
+    const double dsum = l >= 0 ? ray_step<KEEP>(C, rec, S, P, D, sm, l) : 0.0;
     warp_partial(C, blockIdx.x, warp_view(blockIdx.y, kFwdThreads / 32), dsum, D.dtpl_part);
+}
+
+// Inner iteration of nested MOCCA: the dual prox of the kept convex model at
+// u = y + Sigma alpha (g - g0) (g = X xbar from k_mocca_proj), y' = r + B (u - r)
+// in double-float, then b = alpha^T y'; the step matrix S stays the outer one.
+__global__ void __launch_bounds__(kFwdThreads) k_mocca_ray_inner(GeomC C, RayRec* rec, SolveD D) {
+    const int l = ray_of_thread(C);
+    if (l < 0) return;
+    const float4* M = D.model + (size_t)kModelStride * l;
+    const float4 a0 = M[0], a1 = M[1], a2 = M[2], g0 = M[3];
+    const float al[4][3] = {{a0.x, a1.x, a2.x}, {a0.y, a1.y, a2.y}, {a0.z, a1.z, a2.z}, {a0.w, a1.w, a2.w}};
+    const float4 yy = D.y[l];
+    const float y[4] = {yy.x, yy.y, yy.z, yy.w};
+    float yo[4] = {y[0], y[1], y[2], y[3]};
+    if (g0.w != 0.0f) {
+        const float4 gg = D.g[l], rh = M[4], rl = M[5], si = M[6];
+        const float dg[3] = {gg.x - g0.x, gg.y - g0.y, gg.z - g0.z};
+        const float sv[4] = {si.x, si.y, si.z, si.w};
+        const dfl r[4] = {{rh.x, rl.x}, {rh.y, rl.y}, {rh.z, rl.z}, {rh.w, rl.w}};
+        dfl d[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const float kz = fmaf(al[w][2], dg[2], fmaf(al[w][1], dg[1], al[w][0] * dg[0]));
+            const float step = sv[w] > 0.0f ? kz / sv[w] : 0.0f;
+            d[w] = df_sub(df_add(dfl{y[w], 0.0f}, dfl{step, 0.0f}), r[w]);   // u - r
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const float4 B = M[7 + w];
+            const dfl t = df_add(df_add(df_mulf(d[0], B.x), df_mulf(d[1], B.y)),
+                                 df_add(df_mulf(d[2], B.z), df_mulf(d[3], B.w)));
+            yo[w] = df_f(df_add(r[w], t));
+        }
+    }
+    D.y[l] = make_float4(yo[0], yo[1], yo[2], yo[3]);
+    float bb[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) bb[m] = fmaf(al[w][m], yo[w], bb[m]);
+    const float4 r1 = rec[l].r1;
+    rec[l].r1 = make_float4(r1.x, r1.y, bb[0], bb[1]);
+    rec[l].r2.x = bb[2];
 }
 
 // Box-constrained primal step: argmin over lo <= x <= hi of 1/2 (x - t)^T Q (x - t),
@@ -935,7 +1028,7 @@ __global__ void __launch_bounds__(kFwdThreads, 6) k_batch_ray(const SolveDesc* _
         const GeomC C = d.C;
         const int nbx = (C.n_bins + 31) >> 5, bx = w.y % nbx, by = w.y / nbx;
         const int l = ray_at(C, bx, by, kFwdThreads / 32);
-        const double dsum = l >= 0 ? ray_step(C, d.rec, d.S, d.P, d.D, sm, l) : 0.0;
+        const double dsum = l >= 0 ? ray_step<false>(C, d.rec, d.S, d.P, d.D, sm, l) : 0.0;
         warp_partial(C, bx, warp_view(by, kFwdThreads / 32), dsum, d.D.dtpl_part);
     }
 }
@@ -1000,7 +1093,18 @@ cudaError_t launch_mocca_proj(const GeomC& C, const ExcTable& E, const RayRec* r
 
 cudaError_t launch_mocca_ray(const GeomC& C, RayRec* rec, const SpecD& S, const StepParams& P, const SolveD& D,
                              cudaStream_t st) {
-    k_mocca_ray<<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, rec, S, P, D);
+    k_mocca_ray<false><<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, rec, S, P, D);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mocca_ray_keep(const GeomC& C, RayRec* rec, const SpecD& S, const StepParams& P,
+                                  const SolveD& D, cudaStream_t st) {
+    k_mocca_ray<true><<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, rec, S, P, D);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mocca_ray_inner(const GeomC& C, RayRec* rec, const SolveD& D, cudaStream_t st) {
+    k_mocca_ray_inner<<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, rec, D);
     return cudaGetLastError();
 }
 

@@ -38,17 +38,23 @@ struct osscir_ctx {
     int n_part = 0;
     int exp_model = 0;   // counts model: 0 softexp (Eq. finalModel), 1 exp (Eq. fullModel)
     int iter = 0;
+    // nested MOCCA: iterations per kept local model, the position in the cycle
+    // (0: the next iteration is an outer one) and the models [L][kModelStride]
+    int inner = 1, phase = 0;
+    float4* model = nullptr;
     // per-iteration graph
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph_in = nullptr;        // inner iteration of nested MOCCA
+    cudaGraphExec_t gexec_in = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // recorded around the kernels inside the graph
     cudaStream_t side_stream = nullptr;                 // D_TPL reduction beside the back-projection
     cudaEvent_t fork = nullptr, join = nullptr;
 
     osscir::ExcTable exc() const { return osscir::ExcTable{exc_off, exc_ent}; }
     osscir::SpecD spec() const { return osscir::SpecD{nE, s4, N4, mu, exp_model}; }
-    osscir::SolveD solve() const { return osscir::SolveD{g, c, y, x, xbar, chord, dtpl_part}; }
+    osscir::SolveD solve() const { return osscir::SolveD{g, c, y, x, xbar, chord, dtpl_part, model}; }
 };
 
 namespace osscir {
@@ -60,7 +66,7 @@ osscir_status ctx_create(const osscir_geometry* geom, const osscir_spectra* spec
 void ctx_destroy(osscir_ctx* h);
 osscir_status ctx_validate(const osscir_geometry* geom, const osscir_spectra* spectra, const float* mu,
                            const osscir_params* params);
-// Capture the per-iteration graph once.
+// Capture the per-iteration graph(s) once.
 osscir_status ctx_ensure_graph(osscir_ctx* h);
 
 // Batch runner for the served form: the batched kernels over a set of contexts

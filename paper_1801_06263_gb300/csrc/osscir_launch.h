@@ -47,7 +47,14 @@ struct SolveD {
     float4* xbar;       // [P] 2 x_n - x_{n-1}
     const float* chord; // [L] (X 1)_l
     double* dtpl_part;  // [fwd blocks]
+    float4* model;      // [L][kModelStride] local models kept for nested MOCCA, or null
 };
+
+// Per-ray local model kept by an outer iteration of nested MOCCA (float4 slots):
+//   0..2 alpha_{w,m} for m = 0, 1, 2 (over w);  3 (g0, flag: 1 solve, 0 keep y);
+//   4, 5 r as the hi and lo floats of a double-float;  6 Sigma^-1;  7..10 the rows of
+//   B, the map of the dual prox y' = r + B (u - r).
+constexpr int kModelStride = 11;
 
 constexpr int kFwdThreads = 128;
 constexpr int kBpTileX = 16, kBpTileY = 8;            // plain back-projection tile
@@ -83,6 +90,11 @@ cudaError_t launch_mocca_proj(const GeomC& C, const ExcTable& E, const RayRec* r
                               cudaStream_t st);
 cudaError_t launch_mocca_ray(const GeomC& C, RayRec* rec, const SpecD& S, const StepParams& P, const SolveD& D,
                              cudaStream_t st);
+// Outer iteration of nested MOCCA: the per-ray step that also keeps each ray's model in D.model.
+cudaError_t launch_mocca_ray_keep(const GeomC& C, RayRec* rec, const SpecD& S, const StepParams& P,
+                                  const SolveD& D, cudaStream_t st);
+// Inner iteration of nested MOCCA: the dual step on the kept models.
+cudaError_t launch_mocca_ray_inner(const GeomC& C, RayRec* rec, const SolveD& D, cudaStream_t st);
 cudaError_t launch_mocca_bp(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
                             const StepParams& P, const SolveD& D, cudaStream_t st);
 cudaError_t launch_dtpl_reduce(const double* part, int n, double* out, cudaStream_t st);

@@ -438,6 +438,7 @@ osscir_status osscir_submit(osscir_server_t s, const osscir_request* req, uint64
     if (!s || !req || !ticket || !req->counts || req->n_iters < 0) return OSSCIR_E_INVALID;
     const osscir_status v = osscir::ctx_validate(&req->geom, &req->spectra, req->mu, &req->params);
     if (v != OSSCIR_OK) return v;
+    if (req->params.inner > 1) return OSSCIR_E_INVALID;   // nested solves are not served
     Ticket* t = new (std::nothrow) Ticket();
     if (!t) return OSSCIR_E_NOMEM;
     const osscir_geometry& g = req->geom;
@@ -449,6 +450,7 @@ osscir_status osscir_submit(osscir_server_t s, const osscir_request* req, uint64
         t->cfg.N.assign(req->spectra.N, req->spectra.N + (size_t)g.n_bins * 4);
         t->cfg.mu.assign(req->mu, req->mu + 3 * nE);
         t->cfg.params = req->params;
+        t->cfg.params.inner = 1;
         t->counts.assign(req->counts, req->counts + L * 4);
     } catch (...) {
         delete t;

@@ -78,6 +78,9 @@ def test_create_rejects_bad_box_and_model(lib):
             _lib.osscir_create(g, sp.s, sp.N, sp.mu, 1e-6, box=box)
     with pytest.raises(_lib.OsscirError):
         _lib.osscir_create(g, sp.s, sp.N, sp.mu, 1e-6, model=7)
+    for inner in (-1, 1000001):   # iterations per kept local model of nested MOCCA
+        with pytest.raises(_lib.OsscirError):
+            _lib.osscir_create(g, sp.s, sp.N, sp.mu, 1e-6, inner=inner)
 
 
 def test_null_handle_calls_are_rejected(lib):
