@@ -141,7 +141,7 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
 
     const int L = h->L, P = h->P, nE = h->nE;
     h->n_part = dtpl_partials(g->n_bins, g->n_views);
-    CK(dalloc(&h->rec, L));
+    CK(dalloc(&h->rec, 2 * (size_t)L));   // weight halves, then step halves
     CK(dalloc(&h->r64, L));
     CK(dalloc(&h->views, g->n_views));
     CK(dalloc(&h->chord, L));

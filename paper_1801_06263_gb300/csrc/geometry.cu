@@ -67,9 +67,10 @@ __global__ void k_ray_setup(GeomD G, double r_img, RayRec* rec, Ray64* r64, int 
     RayRec q;
     q.r0 = make_float4((float)R.x, (float)R.y, idx, idy);
     q.r1 = make_float4(ex, ey, 0.f, 0.f);
-    q.r2 = make_float4(0.f, 0.f, 0.f, 0.f);
-    q.r3 = make_float4(0.f, 0.f, 0.f, 0.f);
     rec[l] = q;
+    RayStep z;
+    z.s0 = z.s1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    ray_steps(rec, L)[l] = z;
 }
 
 __global__ void k_view_setup(GeomD G, ViewF* views) {

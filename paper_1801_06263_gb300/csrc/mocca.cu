@@ -737,8 +737,9 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
             }
         }
         rec[l].r1 = make_float4(r1.x, r1.y, bb[0], bb[1]);
-        rec[l].r2 = make_float4(bb[2], Sm[0], Sm[1], Sm[2]);
-        rec[l].r3 = make_float4(Sm[3], Sm[4], Sm[5], 0.f);
+        RayStep* st = ray_steps(rec, C.n_views * C.n_bins) + l;
+        st->s0 = make_float4(bb[2], Sm[0], Sm[1], Sm[2]);
+        st->s1 = make_float4(Sm[3], Sm[4], Sm[5], 0.f);
     }
     return dsum;
 }
@@ -794,7 +795,7 @@ __global__ void __launch_bounds__(kFwdThreads) k_mocca_ray_inner(GeomC C, RayRec
         for (int m = 0; m < 3; ++m) bb[m] = fmaf(al[w][m], yo[w], bb[m]);
     const float4 r1 = rec[l].r1;
     rec[l].r1 = make_float4(r1.x, r1.y, bb[0], bb[1]);
-    rec[l].r2.x = bb[2];
+    ray_steps(rec, C.n_views * C.n_bins)[l].s0.x = bb[2];
 }
 
 // Box-constrained primal step: argmin over lo <= x <= hi of 1/2 (x - t)^T Q (x - t),
@@ -879,6 +880,7 @@ __device__ __forceinline__ void bp_pixel(const GeomC& C, const ExcTable& E, cons
     if (valid) {
         const int per = (C.n_views + G - 1) / G;
         const int v0 = g * per, v1 = min(C.n_views, v0 + per);
+        const RayStep* steps = ray_steps(rec, C.n_views * C.n_bins);
         for (int v = v0; v < v1; ++v) {
             int blo, bhi;
             pixel_bin_range(C, views[v], ix, iy, blo, bhi);
@@ -892,7 +894,7 @@ __device__ __forceinline__ void bp_pixel(const GeomC& C, const ExcTable& E, cons
                 const float wa = x_weight(A.a, A.b.x, A.b.y, C.grid, E, l, ix, iy);
                 const float wb = two ? x_weight(B.a, B.b.x, B.b.y, C.grid, E, l + 1, ix, iy) : 0.0f;
                 if (wa != 0.0f) {
-                    const RecHalf A2 = ldg_half(&rec[l].r2);
+                    const RecHalf A2 = ldg_half(&steps[l].s0);
                     acc[0] = fmaf(wa, A.b.z, acc[0]);
                     acc[1] = fmaf(wa, A.b.w, acc[1]);
                     acc[2] = fmaf(wa, A2.a.x, acc[2]);
@@ -904,7 +906,7 @@ __device__ __forceinline__ void bp_pixel(const GeomC& C, const ExcTable& E, cons
                     acc[8] = fmaf(wa, A2.b.z, acc[8]);
                 }
                 if (wb != 0.0f) {
-                    const RecHalf B2 = ldg_half(&rec[l + 1].r2);
+                    const RecHalf B2 = ldg_half(&steps[l + 1].s0);
                     acc[0] = fmaf(wb, B.b.z, acc[0]);
                     acc[1] = fmaf(wb, B.b.w, acc[1]);
                     acc[2] = fmaf(wb, B2.a.x, acc[2]);

@@ -28,16 +28,29 @@ __device__ __forceinline__ float grid_plane(const GridF& G, int i) {
     return __fmaf_rn(static_cast<float>(i), G.h, G.x0);
 }
 
-// Per-ray record, 4 x float4 = 64 bytes, one per ray l = v * n_bins + b.
-//   r0 = (bx, by, idx, idy)  foot point of the ray line nearest the origin and
-//                            the reciprocal unit-direction components (inf if 0)
-//   r1 = (ex, ey, b0, b1)    FP32 error bounds on t for x- and y-planes; b = alpha^T y'
-//   r2 = (b2, S00, S01, S02) b and the block step matrix S = sum_w alpha_w alpha_w^T / |alpha_w|
-//   r3 = (S11, S12, S22, -)
+// Per-ray record, 64 bytes per ray l = v * n_bins + b, stored as two arrays of
+// 32-byte halves in one allocation of 2 L RayRec: the weight half rec[l] and the
+// step half ray_steps(rec, L)[l].  Consecutive rays' halves are contiguous, so a
+// warp gathering the weight halves of neighbouring rays touches half as many
+// cache lines as with whole records.
+//   rec[l].r0 = (bx, by, idx, idy)    foot point of the ray line nearest the origin and
+//                                     the reciprocal unit-direction components (inf if 0)
+//   rec[l].r1 = (ex, ey, b0, b1)      FP32 error bounds on t for x- and y-planes; b = alpha^T y'
+//   step.s0   = (b2, S00, S01, S02)   b and the block step matrix S = sum_w alpha_w alpha_w^T / |alpha_w|
+//   step.s1   = (S11, S12, S22, -)
 // r0 and r1.xy are written once per geometry; the rest once per MOCCA iteration.
-struct __align__(16) RayRec {
-    float4 r0, r1, r2, r3;
+struct __align__(32) RayRec {
+    float4 r0, r1;
 };
+struct __align__(32) RayStep {
+    float4 s0, s1;
+};
+__host__ __device__ __forceinline__ RayStep* ray_steps(RayRec* rec, int L) {
+    return reinterpret_cast<RayStep*>(rec + L);
+}
+__host__ __device__ __forceinline__ const RayStep* ray_steps(const RayRec* rec, int L) {
+    return reinterpret_cast<const RayStep*>(rec + L);
+}
 
 // t(X) for the x-plane X along the unit direction from the foot point (mm).
 __device__ __forceinline__ float t_plane(float X, float b, float inv_d) {
