@@ -430,42 +430,43 @@ __device__ __forceinline__ bool inv_sym3(const double a[6], double o[6]) {
 
 // Dual step of one ray that meets the image (see the file header).
 //   al: window-effective attenuations alpha (FP32), sinv: Sigma^-1 (FP32),
-//   cw: counts, rw: residuals, Bt: sum_i beta_i mu_i mu_i^T with
-//   beta_i = softexp''_i sum_w r_w s_wi / D_w (FP32, packed), y: dual.
+//   cw: counts (FP32, exact), r: residuals (double-float), Bt: sum_i beta_i mu_i mu_i^T
+//   with beta_i = softexp''_i sum_w r_w s_wi / D_w (FP32, packed), y: dual.
 // With G = (alpha^T alpha)^-1 alpha^T and W = G^T H+ G, the prox
 //   y' = y - Sigma (W + Sigma)^-1 (y - r)
 // equals r + G^T z with (I + H+ F) z = H+ G Sigma^-1 (y - r), F = G Sigma^-1 G^T
 // (push-through identity: the rank-3 update is solved in the 3-dim space of g).
-// The Hessian and its clip are FP64; the rest, whose Gram matrix alpha^T alpha
-// has a condition number near 1e7, is double-float.  Returns y' in yo.
+// Everything is double-float (the Gram matrix alpha^T alpha has a condition
+// number near 1e7): the Hessian H = sum_w c_w alpha_w alpha_w^T - Bt from exact
+// products, its Sylvester test, and the algebra after the clip; only a Hessian
+// that fails the test goes through the FP64 eigen-clip.  Returns y' in yo.
 template <bool KEEP>
-__device__ void ray_dual(const float al[4][3], const float sinv[4], const double cw[4], const double rw[4],
+__device__ void ray_dual(const float al[4][3], const float sinv[4], const float cw[4], const dfl r[4],
                          const float Bt[6], const float y[4], float yo[4], float Bm[4][4]) {
     const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
-    double Hd[6];
+    dfl H[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+        dfl acc = {-Bt[e], 0.0f};
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc = df_add(acc, df_mulf(df_2prod(al[w][ij[e][0]], al[w][ij[e][1]]), cw[w]));
+        H[e] = acc;
+    }
     {
-        double a[4][3], ca[4][3];   // alpha and c_w alpha_w
+        // Sylvester's criterion in double-float; otherwise the FP64 clip
+        const dfl m2 = df_sub(df_mul(H[0], H[3]), df_mul(H[1], H[1]));
+        const dfl det = df_add(df_sub(df_mul(H[0], df_sub(df_mul(H[3], H[5]), df_mul(H[4], H[4]))),
+                                      df_mul(H[1], df_sub(df_mul(H[1], H[5]), df_mul(H[4], H[2])))),
+                               df_mul(H[2], df_sub(df_mul(H[1], H[4]), df_mul(H[3], H[2]))));
+        if (!(H[0].hi > 0.0f && m2.hi > 0.0f && det.hi > 0.0f)) {
+            double Hd[6];
 #pragma unroll
-        for (int w = 0; w < 4; ++w)
+            for (int e = 0; e < 6; ++e) Hd[e] = (double)H[e].hi + (double)H[e].lo;
+            clip_psd3(Hd);
 #pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                a[w][m] = (double)al[w][m];
-                ca[w][m] = cw[w] * a[w][m];
-            }
-#pragma unroll
-        for (int e = 0; e < 6; ++e) {
-            double acc = -(double)Bt[e];
-#pragma unroll
-            for (int w = 0; w < 4; ++w) acc += ca[w][ij[e][0]] * a[w][ij[e][1]];
-            Hd[e] = acc;
+            for (int e = 0; e < 6; ++e) H[e] = df_of(Hd[e]);
         }
     }
-    clip_psd3(Hd);
-    dfl H[6], r[4];
-#pragma unroll
-    for (int e = 0; e < 6; ++e) H[e] = df_of(Hd[e]);
-#pragma unroll
-    for (int w = 0; w < 4; ++w) r[w] = df_of(rw[w]);
     // A = alpha^T alpha (the products of two floats are exact)
     dfl A[6];
 #pragma unroll
@@ -634,7 +635,7 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
         const float4 yy = D.y[l];
         const float Nv[4] = {N.x, N.y, N.z, N.w}, cv[4] = {cc.x, cc.y, cc.z, cc.w};
         float al[4][3], qw[4], nw[4];
-        double cw[4], rw[4];
+        dfl rw[4];   // r = c - N D exactly to double-float precision (N D is an exact product)
         float dt = 0.f;
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
@@ -643,11 +644,10 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
 #pragma unroll
             for (int m = 0; m < 3; ++m) al[w][m] = An[w][m] * invD;
             nw[w] = sqrtf(al[w][0] * al[w][0] + al[w][1] * al[w][1] + al[w][2] * al[w][2]);
-            const double chat = (double)Nv[w] * (double)Dw;
-            cw[w] = (double)cv[w];
-            rw[w] = cw[w] - chat;
-            qw[w] = (float)rw[w] * invD;
-            dt += dtpl_term((float)chat, cv[w]);
+            const dfl chat = df_2prod(Nv[w], Dw);
+            rw[w] = df_sub(dfl{cv[w], 0.0f}, chat);
+            qw[w] = df_f(rw[w]) * invD;
+            dt += dtpl_term(chat.hi, cv[w]);
         }
         dsum = (double)dt;
         const float X1 = __ldg(D.chord + l);
@@ -667,7 +667,7 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
             for (int w = 0; w < 4; ++w) yo[w] = y[w];
         } else if (P.model == 1) {   // W = 0: y' = y - Sigma Sigma^-1 (y - r) = r
 #pragma unroll
-            for (int w = 0; w < 4; ++w) yo[w] = rw[w];
+            for (int w = 0; w < 4; ++w) yo[w] = df_f(rw[w]);
             if (KEEP) {
                 sigma_inv();
                 for (int w = 0; w < 4; ++w)
@@ -694,21 +694,15 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
                 Bt[5] = fmaf(beta, qc.x, Bt[5]);
             }
             sigma_inv();
-            ray_dual<KEEP>(al, sinv, cw, rw, Bt, y, yo, Bm);
+            ray_dual<KEEP>(al, sinv, cv, rw, Bt, y, yo, Bm);
         }
         if (KEEP) {
             float4* M = D.model + (size_t)kModelStride * l;
 #pragma unroll
             for (int m = 0; m < 3; ++m) M[m] = make_float4(al[0][m], al[1][m], al[2][m], al[3][m]);
             M[3] = make_float4(g0, g1, g2, X1 > 0.f ? 1.0f : 0.0f);
-            float rh[4], rl[4];
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                rh[w] = __double2float_rn(rw[w]);
-                rl[w] = __double2float_rn(rw[w] - (double)rh[w]);
-            }
-            M[4] = make_float4(rh[0], rh[1], rh[2], rh[3]);
-            M[5] = make_float4(rl[0], rl[1], rl[2], rl[3]);
+            M[4] = make_float4(rw[0].hi, rw[1].hi, rw[2].hi, rw[3].hi);
+            M[5] = make_float4(rw[0].lo, rw[1].lo, rw[2].lo, rw[3].lo);
             if (X1 > 0.f) {   // a ray outside the image (flag 0) keeps its dual: nothing more is read
                 M[6] = make_float4(sinv[0], sinv[1], sinv[2], sinv[3]);
 #pragma unroll
