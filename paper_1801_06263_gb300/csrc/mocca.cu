@@ -608,26 +608,38 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
         const float4 r1 = rec[l].r1;
         const float4 gg = D.g[l];
         const float g0 = gg.x, g1 = gg.y, g2 = gg.z;
-        // a2/a3, first pass over energies: D_w (compensated) and alpha_w numerators
+        // a2/a3, one pass over energies: D_w (compensated), the alpha_w numerators and
+        // per window U_w = sum_i softexp''(-p_i) s_wi mu_i mu_i^T, so that the curvature
+        // term sum_i beta_i mu_i mu_i^T with beta_i = softexp''_i sum_w (r_w / D_w) s_wi
+        // is sum_w (r_w / D_w) U_w once r and D are known
         const int b = l % C.n_bins, nb = C.n_bins, nE = S.n_energies;
-        float Ds[4] = {0.f, 0.f, 0.f, 0.f}, Dc[4] = {0.f, 0.f, 0.f, 0.f}, An[4][3];
+        float Ds[4] = {0.f, 0.f, 0.f, 0.f}, Dc[4] = {0.f, 0.f, 0.f, 0.f}, An[4][3], U[4][6];
 #pragma unroll
-        for (int w = 0; w < 4; ++w) An[w][0] = An[w][1] = An[w][2] = 0.f;
+        for (int w = 0; w < 4; ++w) {
+            An[w][0] = An[w][1] = An[w][2] = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) U[w][k] = 0.f;
+        }
 #pragma unroll 2   // two energies in flight: the s-table loads overlap
         for (int i = 0; i < nE; ++i) {
             const float4 qa = *reinterpret_cast<const float4*>(sm + kSmemStride * i);
+            const float4 qb = *reinterpret_cast<const float4*>(sm + kSmemStride * i + 4);
+            const float4 qc = *reinterpret_cast<const float4*>(sm + kSmemStride * i + 8);
             const float p = fmaf(qa.z, g2, fmaf(qa.y, g1, qa.x * g0));
             float e0, e1, e2;
             sexp3(-p, S.exp_model != 0, e0, e1, e2);
             const float4 s4 = __ldg(S.s4 + (size_t)i * nb + b);
             const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+            const float mm[6] = {qa.w, qb.x, qb.y, qb.z, qb.w, qc.x};
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 neumaier(Ds[w], Dc[w], sv[w] * e0);
-                const float a = sv[w] * e1;
+                const float a = sv[w] * e1, c2 = sv[w] * e2;
                 An[w][0] = fmaf(a, qa.x, An[w][0]);
                 An[w][1] = fmaf(a, qa.y, An[w][1]);
                 An[w][2] = fmaf(a, qa.z, An[w][2]);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) U[w][k] = fmaf(c2, mm[k], U[w][k]);
             }
         }
         const float4 N = __ldg(S.N4 + b);
@@ -674,25 +686,11 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
                     for (int j = 0; j < 4; ++j) Bm[w][j] = 0.0f;
             }
         } else {
-            // second pass: sum_i beta_i mu_i mu_i^T, beta_i = softexp''(-p_i) sum_w (r_w / D_w) s_wi
-            float Bt[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 2
-            for (int i = 0; i < nE; ++i) {
-                const float4 qa = *reinterpret_cast<const float4*>(sm + kSmemStride * i);
-                const float p = fmaf(qa.z, g2, fmaf(qa.y, g1, qa.x * g0));
-                if (p < 0.0f && !S.exp_model) continue;   // softexp'' = 0 where -p > 0
-                const float e2 = expf(-p);
-                const float4 s4 = __ldg(S.s4 + (size_t)i * nb + b);
-                const float beta = e2 * fmaf(qw[3], s4.w, fmaf(qw[2], s4.z, fmaf(qw[1], s4.y, qw[0] * s4.x)));
-                const float4 qb = *reinterpret_cast<const float4*>(sm + kSmemStride * i + 4);
-                const float4 qc = *reinterpret_cast<const float4*>(sm + kSmemStride * i + 8);
-                Bt[0] = fmaf(beta, qa.w, Bt[0]);
-                Bt[1] = fmaf(beta, qb.x, Bt[1]);
-                Bt[2] = fmaf(beta, qb.y, Bt[2]);
-                Bt[3] = fmaf(beta, qb.z, Bt[3]);
-                Bt[4] = fmaf(beta, qb.w, Bt[4]);
-                Bt[5] = fmaf(beta, qc.x, Bt[5]);
-            }
+            // sum_i beta_i mu_i mu_i^T = sum_w (r_w / D_w) U_w
+            float Bt[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                Bt[k] = fmaf(qw[3], U[3][k], fmaf(qw[2], U[2][k], fmaf(qw[1], U[1][k], qw[0] * U[0][k])));
             sigma_inv();
             ray_dual<KEEP>(al, sinv, cv, rw, Bt, y, yo, Bm);
         }
@@ -739,7 +737,7 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
 }
 
 template <bool KEEP>
-__global__ void __launch_bounds__(kFwdThreads, 6) k_mocca_ray(GeomC C, RayRec* rec, SpecD S, StepParams P,
+__global__ void __launch_bounds__(kFwdThreads, 4) k_mocca_ray(GeomC C, RayRec* rec, SpecD S, StepParams P,
                                                               SolveD D) {
     __shared__ float sm[kSmemStride * kMaxEnergies];
     load_mu_smem(S, sm);
@@ -1008,7 +1006,7 @@ __global__ void __launch_bounds__(kBatchProjMaxThreads) k_batch_proj(const Solve
     }
 }
 
-__global__ void __launch_bounds__(kFwdThreads, 6) k_batch_ray(const SolveDesc* __restrict__ sd,
+__global__ void __launch_bounds__(kFwdThreads, 4) k_batch_ray(const SolveDesc* __restrict__ sd,
                                                               const int2* __restrict__ items, int n_items) {
     __shared__ float sm[kSmemStride * kMaxEnergies];
     int cur = -1;
