@@ -57,9 +57,9 @@ L1_PEAK_TBPS = 152 * 128 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of each per-iteration kernel, from one
 # ncu --set full capture (cold cache), valid only for the kernel sources it was taken on
 TRAFFIC = {
-    "k_mocca_proj": {"bytes_per_launch": 18875904, "source_sha": "fb56752dc9f173e3"},
-    "k_mocca_ray": {"bytes_per_launch": 31977216 + 3606016, "source_sha": "fb56752dc9f173e3"},
-    "k_mocca_bp": {"bytes_per_launch": 16079360 + 256, "source_sha": "fb56752dc9f173e3"},
+    "k_mocca_proj": {"bytes_per_launch": 10486784, "source_sha": "d66d5618c5c16fd7"},
+    "k_mocca_ray": {"bytes_per_launch": 23005952 + 3072, "source_sha": "d66d5618c5c16fd7"},
+    "k_mocca_bp": {"bytes_per_launch": 16141568 + 512, "source_sha": "d66d5618c5c16fd7"},
 }
 
 
