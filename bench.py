@@ -55,7 +55,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # L1 to register-file bandwidth from unit counts: 152 SMs x 128 B per clock x 2.07 GHz
 L1_PEAK_TBPS = 152 * 128 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of each per-iteration kernel, from one
-# ncu --set full capture (cold cache), valid only for the kernel sources it was taken on
+# ncu --set full capture (cold cache) of the medium_256 workload, valid only for
+# that workload and the kernel sources it was taken on
+TRAFFIC_WORKLOAD = "medium_256"
 TRAFFIC = {
     "k_mocca_proj": {"bytes_per_launch": 10486784, "source_sha": "d66d5618c5c16fd7"},
     "k_mocca_ray": {"bytes_per_launch": 23005952 + 3072, "source_sha": "d66d5618c5c16fd7"},
@@ -329,7 +331,8 @@ def run_gpu(args):
                   "peak_source": "152 SMs x 128 B per clock from L1 to registers x 2.07 GHz (unit counts)"}
     achieved = kern[dom]["flop"] / (kern[dom]["ms"] * 1e-3) / 1e12
     tr = TRAFFIC.get(dom)
-    traffic = tr["bytes_per_launch"] if tr and tr.get("source_sha") == _source_sha() else None
+    traffic = (tr["bytes_per_launch"] if tr and WORKLOAD == TRAFFIC_WORKLOAD and tr.get("source_sha") == _source_sha()
+               else None)
     cpu = None
     if ws == 1 and args.cpu_iters > 0:
         rate, cores, dt = cpu_oracle_rate(args.cpu_iters)

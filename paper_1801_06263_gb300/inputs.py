@@ -137,9 +137,20 @@ def _erf(x):
     return np.vectorize(math.erf, otypes=[np.float64])(x)
 
 
-def window_responses(E_keV: np.ndarray, n_bins: int, seed: int = 7) -> np.ndarray:
-    """R[b, i, w]: window responses with per-bin jittered inner edges."""
+def window_responses(E_keV: np.ndarray, n_bins: int, seed: int = 7, ideal: bool = False) -> np.ndarray:
+    """R[b, i, w]: window responses with per-bin jittered inner edges and Gaussian
+    roll-off; ideal=True gives sharp windows [lo, hi) (the last one closed) with
+    the nominal edges in every bin, so each energy falls in exactly one window
+    (the ideal, non-overlapping photon-counting response the paper contrasts with
+    its realistic overlapping windows, Sec. 1)."""
     E = np.asarray(E_keV, dtype=np.float64)
+    if ideal:
+        R = np.zeros((n_bins, E.size, N_WINDOWS))
+        for w in range(N_WINDOWS):
+            lo, hi = WINDOW_EDGES_KEV[w], WINDOW_EDGES_KEV[w + 1]
+            inside = (E >= lo) & ((E < hi) if w < N_WINDOWS - 1 else (E <= hi))
+            R[:, inside, w] = 1.0
+        return R
     rng = np.random.default_rng(seed + 1)
     edges = np.tile(np.asarray(WINDOW_EDGES_KEV), (n_bins, 1))
     edges[:, 1:-1] += rng.uniform(-1.0, 1.0, size=(n_bins, len(WINDOW_EDGES_KEV) - 2))
@@ -165,10 +176,10 @@ class Spectra:
 
 
 def make_spectra(n_bins: int, photons_per_ray: float, *, seed: int = 7,
-                 E_keV: np.ndarray | None = None) -> Spectra:
+                 E_keV: np.ndarray | None = None, ideal_windows: bool = False) -> Spectra:
     E = energies_keV() if E_keV is None else np.asarray(E_keV, dtype=np.float64)
     phi = source_spectrum(E, seed)
-    R = window_responses(E, n_bins, seed)
+    R = window_responses(E, n_bins, seed, ideal=ideal_windows)
     weighted = phi[None, :, None] * R                  # [b, i, w]
     tot = weighted.sum(axis=1)                         # [b, w]
     s = weighted / tot[:, None, :]

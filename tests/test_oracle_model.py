@@ -206,3 +206,33 @@ def test_exp_model_gradient_matches_dtpl_finite_differences(orc):
             fd[k, m] = (orc.objective(geom, sp, c, fp, with_grad=False, counts_model="exp")
                         - orc.objective(geom, sp, c, fm, with_grad=False, counts_model="exp")) / (2 * h)
     np.testing.assert_allclose(grad, fd, rtol=0, atol=1e-6 * np.abs(grad).max())
+
+
+# ---------------------------------------------------------------- ideal, non-overlapping windows
+
+def test_ideal_windows_partition_the_energies():
+    """Sharp windows: each energy lies in exactly one window, s sums to 1 per window."""
+    R = inputs.window_responses(inputs.energies_keV(), 5, ideal=True)
+    assert set(np.unique(R)) == {0.0, 1.0}
+    assert (R.sum(axis=2) == 1.0).all()
+    assert np.array_equal(R[0], R[4])   # the same response in every detector bin
+    sp = inputs.make_spectra(5, 1e5, ideal_windows=True)
+    assert ((sp.s > 0).sum(axis=2) <= 1).all()
+    np.testing.assert_allclose(sp.s.sum(axis=1), 1.0, rtol=0, atol=1e-14)
+
+
+def test_overlap_worsens_the_conditioning(orc):
+    """The overlapping realistic windows make alpha^T alpha worse conditioned than
+    ideal sharp windows on the same rays (the effect the paper attributes to the
+    realistic response, Sec. 1)."""
+    geom = inputs.make_geometry(32, 0.5, 16, 48)
+    f = inputs.disk_phantom(geom, radius_mm=6.0, insert_mm=1.5)
+    g = orc.forward(geom, f)
+    real = inputs.make_spectra(geom.n_bins, 1e5)
+    ideal = inputs.make_spectra(geom.n_bins, 1e5, ideal_windows=True)
+    for l in (geom.n_bins // 2, 3 * geom.n_bins + 20, 9 * geom.n_bins + 30):
+        b = l % geom.n_bins
+        assert g[l, 0] > 0
+        cond = [np.linalg.cond(orc.ray_terms(sp, b, g[l])["alpha"].T @ orc.ray_terms(sp, b, g[l])["alpha"])
+                for sp in (real, ideal)]
+        assert cond[0] > 1.2 * cond[1], cond
