@@ -6,7 +6,8 @@
 //   k_mocca_ray (per ray):      the counts model
 //       of Eq. (finalModel) summed over energies (compensated), D_TPL of
 //       Eq. (DTPL), alpha_w = sum_i A_wi mu_i (K = alpha X, Eq. aeq), the per-ray
-//       Hessian of Sec. 2 in g with its negative eigenvalues removed (FP64),
+//       Hessian of Sec. 2 in g (double-float) with its negative eigenvalues
+//       removed (FP64, for the Hessians that are not positive definite),
 //       the dual step matrix Sigma^-1 = lambda |alpha_w| (X 1)_l, the exact
 //       preconditioned dual prox y' = y - Sigma (W + Sigma)^-1 (y - r), and the
 //       per-ray products b = alpha^T y' and S = sum_w alpha_w alpha_w^T / |alpha_w|.
