@@ -23,6 +23,7 @@ namespace {
 
 constexpr int kMaxEnergies = 256;
 constexpr int kSmemStride = 12;   // per energy: mu0 mu1 mu2 | m00 m01 m02 m11 m12 m22 | pad
+constexpr int kDFold = 16;        // energies per plain FP32 partial of D_w
 
 __device__ __forceinline__ void neumaier(float& s, float& c, float t) {
     const float u = s + t;
@@ -609,10 +610,12 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
         const float4 r1 = rec[l].r1;
         const float4 gg = D.g[l];
         const float g0 = gg.x, g1 = gg.y, g2 = gg.z;
-        // a2/a3, one pass over energies: D_w (compensated), the alpha_w numerators and
-        // per window U_w = sum_i softexp''(-p_i) s_wi mu_i mu_i^T, so that the curvature
-        // term sum_i beta_i mu_i mu_i^T with beta_i = softexp''_i sum_w (r_w / D_w) s_wi
-        // is sum_w (r_w / D_w) U_w once r and D are known
+        // a2/a3, one pass over energies: D_w, the alpha_w numerators and per window
+        // U_w = sum_i softexp''(-p_i) s_wi mu_i mu_i^T, so that the curvature term
+        // sum_i beta_i mu_i mu_i^T with beta_i = softexp''_i sum_w (r_w / D_w) s_wi
+        // is sum_w (r_w / D_w) U_w once r and D are known.  D_w (positive terms) is
+        // summed in two levels: plain FP32 over kDFold energies, the partials
+        // compensated (Neumaier)
         const int b = l % C.n_bins, nb = C.n_bins, nE = S.n_energies;
         float Ds[4] = {0.f, 0.f, 0.f, 0.f}, Dc[4] = {0.f, 0.f, 0.f, 0.f}, An[4][3], U[4][6];
 #pragma unroll
@@ -621,27 +624,33 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
 #pragma unroll
             for (int k = 0; k < 6; ++k) U[w][k] = 0.f;
         }
+        for (int i0 = 0; i0 < nE; i0 += kDFold) {
+            float Pd[4] = {0.f, 0.f, 0.f, 0.f};
+            const int i1 = min(nE, i0 + kDFold);
 #pragma unroll 2   // two energies in flight: the s-table loads overlap
-        for (int i = 0; i < nE; ++i) {
-            const float4 qa = *reinterpret_cast<const float4*>(sm + kSmemStride * i);
-            const float4 qb = *reinterpret_cast<const float4*>(sm + kSmemStride * i + 4);
-            const float4 qc = *reinterpret_cast<const float4*>(sm + kSmemStride * i + 8);
-            const float p = fmaf(qa.z, g2, fmaf(qa.y, g1, qa.x * g0));
-            float e0, e1, e2;
-            sexp3(-p, S.exp_model != 0, e0, e1, e2);
-            const float4 s4 = __ldg(S.s4 + (size_t)i * nb + b);
-            const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
-            const float mm[6] = {qa.w, qb.x, qb.y, qb.z, qb.w, qc.x};
+            for (int i = i0; i < i1; ++i) {
+                const float4 qa = *reinterpret_cast<const float4*>(sm + kSmemStride * i);
+                const float4 qb = *reinterpret_cast<const float4*>(sm + kSmemStride * i + 4);
+                const float4 qc = *reinterpret_cast<const float4*>(sm + kSmemStride * i + 8);
+                const float p = fmaf(qa.z, g2, fmaf(qa.y, g1, qa.x * g0));
+                float e0, e1, e2;
+                sexp3(-p, S.exp_model != 0, e0, e1, e2);
+                const float4 s4 = __ldg(S.s4 + (size_t)i * nb + b);
+                const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+                const float mm[6] = {qa.w, qb.x, qb.y, qb.z, qb.w, qc.x};
 #pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                neumaier(Ds[w], Dc[w], sv[w] * e0);
-                const float a = sv[w] * e1, c2 = sv[w] * e2;
-                An[w][0] = fmaf(a, qa.x, An[w][0]);
-                An[w][1] = fmaf(a, qa.y, An[w][1]);
-                An[w][2] = fmaf(a, qa.z, An[w][2]);
+                for (int w = 0; w < 4; ++w) {
+                    Pd[w] = fmaf(sv[w], e0, Pd[w]);
+                    const float a = sv[w] * e1, c2 = sv[w] * e2;
+                    An[w][0] = fmaf(a, qa.x, An[w][0]);
+                    An[w][1] = fmaf(a, qa.y, An[w][1]);
+                    An[w][2] = fmaf(a, qa.z, An[w][2]);
 #pragma unroll
-                for (int k = 0; k < 6; ++k) U[w][k] = fmaf(c2, mm[k], U[w][k]);
+                    for (int k = 0; k < 6; ++k) U[w][k] = fmaf(c2, mm[k], U[w][k]);
+                }
             }
+#pragma unroll
+            for (int w = 0; w < 4; ++w) neumaier(Ds[w], Dc[w], Pd[w]);
         }
         const float4 N = __ldg(S.N4 + b);
         const float4 cc = D.c[l];
