@@ -60,9 +60,9 @@ L1_PEAK_TBPS = 152 * 128 * 2.07e9 / 1e12
 # that workload and the kernel sources it was taken on
 TRAFFIC_WORKLOAD = "medium_256"
 TRAFFIC = {
-    "k_mocca_proj": {"bytes_per_launch": 10486784, "source_sha": "d2e75eeda1d9bddc"},
-    "k_mocca_ray": {"bytes_per_launch": 23005952 + 3072, "source_sha": "d2e75eeda1d9bddc"},
-    "k_mocca_bp": {"bytes_per_launch": 16141568 + 512, "source_sha": "d2e75eeda1d9bddc"},
+    "k_mocca_proj": {"bytes_per_launch": 10487296, "source_sha": "dfbd97d3772e3c85"},
+    "k_mocca_ray": {"bytes_per_launch": 23002368 + 3328, "source_sha": "dfbd97d3772e3c85"},
+    "k_mocca_bp": {"bytes_per_launch": 16140800 + 512, "source_sha": "dfbd97d3772e3c85"},
 }
 
 
