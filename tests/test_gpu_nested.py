@@ -157,3 +157,27 @@ def test_nested_solves_are_neither_batched_nor_served(small):
         assert e.value.status == L.OSSCIR_E_INVALID
     finally:
         L.osscir_server_destroy(srv)
+
+
+@pytest.mark.parametrize("variant", ["gradient", "nonnegative", "diagonal"])
+def test_nested_variants_match_oracle(orc, small, variant):
+    """Nested MOCCA with the zero-curvature model (inner = 3, an iteration count
+    that is not a multiple of it), with nonnegativity (inner = 4) and with the
+    diagonal SPC (inner = 2), against the oracle's nested iterates."""
+    w, s32, c = small
+    inf = float("inf")
+    gpu_kw, orc_kw, lam, n_it, inner = {
+        "gradient": ({"model": 1}, {"model": "gradient"}, 3e-8, 61, 3),
+        "nonnegative": ({"box": ((0.0, 0.0, 0.0), (inf, inf, inf))},
+                        {"box": ((0.0, 0.0, 0.0), (inf, inf, inf))}, 1e-7, 60, 4),
+        "diagonal": ({"spc": 1}, {"spc": "diagonal"}, 1e-6, 30, 2),
+    }[variant]
+    R = _recon(w.geom, w.spectra, lam, inner=inner, **gpu_kw)
+    R.set_counts(torch.tensor(c, device="cuda"))
+    R.step(n_it)
+    x = R.maps().cpu().double().numpy()[:, :3]
+    R.close()
+    st, _ = orc.mocca(w.geom, s32, c.astype(np.float64), n_it, lam, inner=inner, **orc_kw)
+    errs = _rel(x, st.x)
+    print(f"nested {variant}: rel L2 after {n_it} iterations PMMA {errs[0]:.2e} Al {errs[1]:.2e} Gd {errs[2]:.2e}")
+    assert max(errs) < REL_L2, errs
