@@ -167,7 +167,8 @@ osscir_status osscir_reconstruct(osscir_t h, const float *c_host, int n_iters, f
 /* Device time of the last MOCCA iteration's three main kernels, measured with
  * CUDA events recorded inside the iteration's graph (host float[3]): ms[0]
  * the ray-driven forward projection, ms[1] the per-ray spectral model,
- * curvature and dual step, ms[2] the pixel-driven back-projection, block
+ * curvature and dual step (after an inner iteration of a nested solve: its dual
+ * step on the kept models), ms[2] the pixel-driven back-projection, block
  * step-preconditioner and primal step.  Synchronises the stream. */
 osscir_status osscir_last_kernel_ms(osscir_t h, float *ms, void *stream);
 
