@@ -5,7 +5,7 @@
   * the block SPC iterates are invariant under a rotation of the material
     basis, the diagonal SPC iterates are not (Sec. 2);
   * with monochromatic windows D_TPL is convex and MOCCA reaches the scipy minimiser;
-  * noiseless "inverse crime" data (Sec. 3): D_TPL falls by > 1e8 and the maps
+  * noiseless data made with the reconstruction's own model (Sec. 3): D_TPL falls by > 1e8 and the maps
     approach the truth;
   * box constraints hold at every iterate; results do not depend on the thread count.
 """
