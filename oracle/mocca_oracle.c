@@ -608,13 +608,15 @@ static void ray_sigma_inv(const orc_params *P, const double alpha[12], int cnt, 
     }
 }
 
-/* Scatter of one ray into the per-pixel primal quantities:
+/* Scatter of one ray into the per-pixel primal quantities of the pixels k in
+ * [k_lo, k_hi) (the whole image, or one thread's band of rows):
  *   v_k    += sum_w K_{wl,mk} y'_{wl}                       (K^T y')
  *   block SPC:    Tinv_k[m][m'] += (1/lambda) sum_w K_m K_m' / sqrt(sum_m'' K_m''^2)
  *   diagonal SPC: Tinv_k[m][m]  += (1/lambda) sum_w |K_m|                       */
 static void ray_scatter(const orc_params *P, const double alpha[12], const double yp[4], int cnt,
-                        const int *pix, const double *len, double *v, double *Tinv) {
+                        const int *pix, const double *len, int k_lo, int k_hi, double *v, double *Tinv) {
     for (int j = 0; j < cnt; ++j) {
+        if (pix[j] < k_lo || pix[j] >= k_hi) continue;   /* another thread's pixels */
         double *vk = v + (size_t)pix[j] * 3;
         double *Tk = Tinv + (size_t)pix[j] * 9;
         for (int w = 0; w < NW; ++w) {
@@ -632,6 +634,45 @@ static void ray_scatter(const orc_params *P, const double alpha[12], const doubl
             } else {
                 for (int m = 0; m < NM; ++m) Tk[m * 3 + m] += fabs(K[m]) / P->lambda;
             }
+        }
+    }
+}
+
+/* The scatter of every ray l = 0, 1, ..., L-1 (ray_scatter) into v and Tinv,
+ * which it zeroes first.  The rays go in chunks of kScatterChunk: the threads
+ * trace a chunk's footprints (Siddon) side by side into fp_cnt / fp_pix /
+ * fp_len, then each thread scatters the whole chunk, in ray order, into the
+ * pixels of its own band of image rows only.  Every pixel therefore receives
+ * the same additions in the same order as a serial scatter over l, whatever
+ * the number of threads, and the result is bit-identical to it. */
+enum { kScatterChunk = 2048 };
+
+static void scatter_rays(const orc_geometry *G, const orc_params *P, const double *al, const double *y,
+                         double *v, double *Tinv, int *fp_cnt, int *fp_pix, double *fp_len) {
+    const int L = G->n_views * G->n_bins, Pn = G->n * G->n, cap = 2 * G->n + 4;
+    memset(v, 0, sizeof(double) * (size_t)Pn * 3);
+    memset(Tinv, 0, sizeof(double) * (size_t)Pn * 9);
+#pragma omp parallel
+    {
+        int t = 0, nt = 1;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+        nt = omp_get_num_threads();
+#endif
+        const int k_lo = (int)((long long)G->n * t / nt) * G->n;
+        const int k_hi = (int)((long long)G->n * (t + 1) / nt) * G->n;
+        for (int l0 = 0; l0 < L; l0 += kScatterChunk) {
+            const int l1 = l0 + kScatterChunk < L ? l0 + kScatterChunk : L;
+#pragma omp for schedule(static)
+            for (int l = l0; l < l1; ++l)
+                fp_cnt[l - l0] = orc_siddon(G, l / G->n_bins, l % G->n_bins, fp_pix + (size_t)(l - l0) * cap,
+                                            fp_len + (size_t)(l - l0) * cap, cap);
+            /* (the implicit barrier: the chunk's footprints are complete) */
+            for (int l = l0; l < l1; ++l)
+                ray_scatter(P, al + (size_t)l * 12, y + (size_t)l * NW, fp_cnt[l - l0],
+                            fp_pix + (size_t)(l - l0) * cap, fp_len + (size_t)(l - l0) * cap, k_lo, k_hi, v,
+                            Tinv);
+#pragma omp barrier
         }
     }
 }
@@ -654,7 +695,7 @@ void orc_step_matrices(const orc_geometry *G, const orc_spectra *sp, const orc_p
                       NULL, NULL, NULL, NULL);
         int cnt = orc_siddon(G, l / G->n_bins, l % G->n_bins, pix, len, cap);
         if (sigma_inv) ray_sigma_inv(P, al + (size_t)l * 12, cnt, len, sigma_inv + (size_t)l * NW);
-        if (Tinv) ray_scatter(P, al + (size_t)l * 12, zeros, cnt, pix, len, v, Tinv);
+        if (Tinv) ray_scatter(P, al + (size_t)l * 12, zeros, cnt, pix, len, 0, Pn, v, Tinv);
     }
     if (alpha_out) memcpy(alpha_out, al, sizeof(double) * (size_t)L * 12);
     free(g);
@@ -689,8 +730,9 @@ int orc_mocca(const orc_geometry *G, const orc_spectra *sp, const orc_params *P,
     double *dt = (double *)malloc(sizeof(double) * (size_t)L);
     double *v = (double *)malloc(sizeof(double) * (size_t)Pn * 3);
     double *Tinv = (double *)malloc(sizeof(double) * (size_t)Pn * 9);
-    int *pix = (int *)malloc(sizeof(int) * cap);
-    double *len = (double *)malloc(sizeof(double) * cap);
+    int *fp_cnt = (int *)malloc(sizeof(int) * kScatterChunk);
+    int *fp_pix = (int *)malloc(sizeof(int) * (size_t)kScatterChunk * cap);
+    double *fp_len = (double *)malloc(sizeof(double) * (size_t)kScatterChunk * cap);
     const int inner = P->inner > 1 ? P->inner : 1;
     double *mHp = NULL, *mr = NULL, *msinv = NULL, *mg0 = NULL;   /* the stored local models */
     if (inner > 1) {
@@ -758,13 +800,8 @@ int orc_mocca(const orc_geometry *G, const orc_spectra *sp, const orc_params *P,
             for (int l = 0; l < L; ++l) acc += dt[l];
             dtpl_hist[it] = acc;
         }
-        /* back-projection of K^T y' and of the block step matrix (serial scatter) */
-        memset(v, 0, sizeof(double) * (size_t)Pn * 3);
-        memset(Tinv, 0, sizeof(double) * (size_t)Pn * 9);
-        for (int l = 0; l < L; ++l) {
-            int cnt = orc_siddon(G, l / G->n_bins, l % G->n_bins, pix, len, cap);
-            ray_scatter(P, al + (size_t)l * 12, y + (size_t)l * NW, cnt, pix, len, v, Tinv);
-        }
+        /* back-projection of K^T y' and of the block step matrix */
+        scatter_rays(G, P, al, y, v, Tinv, fp_cnt, fp_pix, fp_len);
         /* per-pixel primal step and extrapolation */
 #pragma omp parallel for schedule(static)
         for (int k = 0; k < Pn; ++k) {
@@ -785,8 +822,9 @@ int orc_mocca(const orc_geometry *G, const orc_spectra *sp, const orc_params *P,
     free(dt);
     free(v);
     free(Tinv);
-    free(pix);
-    free(len);
+    free(fp_cnt);
+    free(fp_pix);
+    free(fp_len);
     free(mHp);
     free(mr);
     free(msinv);
