@@ -51,19 +51,45 @@ def _hbm_peak():
 
 
 HBM_PEAK_GBPS, HBM_PEAK_SOURCE = _hbm_peak()
-# FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# L1 to register-file bandwidth from unit counts: 152 SMs x 128 B per clock x 2.07 GHz
-L1_PEAK_TBPS = 152 * 128 * 2.07e9 / 1e12
-# DRAM bytes (read + write) per launch of each per-iteration kernel, from one
-# ncu --set full capture (cold cache) of the medium_256 workload, valid only for
-# that workload and the kernel sources it was taken on
-TRAFFIC_WORKLOAD = "medium_256"
-TRAFFIC = {
-    "k_mocca_proj": {"bytes_per_launch": 10487296, "source_sha": "dfbd97d3772e3c85"},
-    "k_mocca_ray": {"bytes_per_launch": 23002368 + 3328, "source_sha": "dfbd97d3772e3c85"},
-    "k_mocca_bp": {"bytes_per_launch": 16140800 + 512, "source_sha": "dfbd97d3772e3c85"},
+
+
+def _measured(key, default=None):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except (OSError, KeyError, ValueError, TypeError):
+        return default
+
+
+# Unit counts per SM of this GPU generation (the SM count and the clock come
+# from the device at run time): 128 FP32 lanes (one FMA = 2 flop per clock
+# each), 4 warp schedulers (one warp instruction issued per clock each), and
+# 128 bytes per clock from L1 to the register file.
+FP32_LANES_PER_SM, SCHEDULERS_PER_SM, L1_BYTES_PER_CLK_PER_SM = 128, 4, 128
+# Per launch of each per-iteration kernel, from one ncu --set full capture
+# (cold cache) of the medium_256 workload: DRAM bytes (read + write) and warp
+# instructions executed.  Valid only for that workload and for the kernel
+# sources they were taken on (source_sha, see _source_sha).
+NCU_WORKLOAD = "medium_256"
+NCU_COUNTS = {
+    "k_mocca_proj": {"dram_bytes": 10487296, "warp_instructions": 151.3e6, "source_sha": "dfbd97d3772e3c85"},
+    "k_mocca_ray": {"dram_bytes": 23002368 + 3328, "warp_instructions": 113.6e6, "source_sha": "dfbd97d3772e3c85"},
+    "k_mocca_bp": {"dram_bytes": 16140800 + 512, "warp_instructions": 205.5e6, "source_sha": "dfbd97d3772e3c85"},
 }
+
+
+def device_roofs(dev, sm_mhz):
+    """Unit-count roofs of device `dev` at SM clock sm_mhz: FP32 TFLOP/s, warp
+    instructions issued per second, L1-to-register TB/s; with how they were formed."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    ghz = sm_mhz / 1e3
+    return {"sms": sms, "sm_mhz": sm_mhz,
+            "fp32_tflops": sms * FP32_LANES_PER_SM * 2 * ghz / 1e3,
+            "issue_per_s": sms * SCHEDULERS_PER_SM * ghz * 1e9,
+            "l1_tbps": sms * L1_BYTES_PER_CLK_PER_SM * ghz / 1e3,
+            "source": f"{sms} SMs (device) x per-SM unit counts x {sm_mhz:.0f} MHz (median SM clock sampled "
+                      "during the timed steps)"}
 
 
 KERNEL_SOURCES = ("mocca.cu", "osscir_internal.cuh", "osscir_launch.h")
@@ -185,14 +211,22 @@ def _oracle_problem(n_views=None):
     return w, np.ascontiguousarray(c)
 
 
-def cpu_oracle_rate(n_iters: int):
-    """FP64 oracle MOCCA iterations/s on the host cores for n_iters iterations."""
+def cpu_oracle_rate(n_iters: int, threads: int = 0):
+    """FP64 oracle MOCCA iterations/s on the host cores for n_iters iterations
+    (threads = 0: all cores)."""
     import oracle
     w, c = _oracle_problem()
-    t0 = time.perf_counter()
-    oracle.mocca(w.geom, w.spectra, c, n_iters, LAMBDA)
-    dt = time.perf_counter() - t0
-    return n_iters / dt, oracle.max_threads(), dt
+    n_all = oracle.max_threads()
+    if threads:
+        oracle.set_threads(threads)
+    try:
+        used = oracle.max_threads()
+        t0 = time.perf_counter()
+        oracle.mocca(w.geom, w.spectra, c, n_iters, LAMBDA)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(n_all)
+    return n_iters / dt, used, dt
 
 
 REFERENCE_BUDGET_S = 150.0   # whole --impl reference run (warm-up and timed steps)
@@ -324,6 +358,24 @@ def run_gpu(args):
         "k_mocca_bp": {"ms": mean[2], "flop": 18.0 * nnz},
     }
     dom = max(kern, key=lambda k: kern[k]["ms"])
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or _measured("sm_max_mhz", 2070.0)
+    roofs = device_roofs(local, sm_mhz)
+    sha = _source_sha()
+    ncu = {k: (v if WORKLOAD == NCU_WORKLOAD and v.get("source_sha") == sha else None) for k, v in NCU_COUNTS.items()}
+    kernels = {}
+    for k, v in kern.items():
+        sec = v["ms"] * 1e-3
+        row = {"ms": v["ms"], "algorithmic_tflops": v["flop"] / sec / 1e12,
+               "alu_frac": v["flop"] / sec / 1e12 / roofs["fp32_tflops"]}
+        if ncu.get(k):
+            # issue: the warp instructions the kernel executed over the issue slots of its duration
+            row["warp_instructions"] = ncu[k]["warp_instructions"]
+            row["issue_frac"] = ncu[k]["warp_instructions"] / (sec * roofs["issue_per_s"])
+            row["dram_bytes"] = ncu[k]["dram_bytes"]
+            row["hbm_frac"] = ncu[k]["dram_bytes"] / sec / 1e9 / HBM_PEAK_GBPS
+            row["binding"] = "issue"
+        kernels[k] = row
     # bytes each footprint pair must bring from L1 to the registers: proj the float4 of
     # xbar; bp the ray's weight inputs (foot point, reciprocal direction, bounds: 24 B)
     # and its b and S (36 B)
@@ -332,17 +384,24 @@ def run_gpu(args):
     if gather_bytes:
         g_ach = gather_bytes * nnz / (kern[dom]["ms"] * 1e-3) / 1e12
         gather = {"bound": "l1", "kernel": dom, "bytes_per_pair": gather_bytes, "achieved": g_ach,
-                  "peak": L1_PEAK_TBPS, "unit": "TB/s", "frac": g_ach / L1_PEAK_TBPS,
-                  "peak_source": "152 SMs x 128 B per clock from L1 to registers x 2.07 GHz (unit counts)"}
+                  "peak": roofs["l1_tbps"], "unit": "TB/s", "frac": g_ach / roofs["l1_tbps"],
+                  "peak_source": roofs["source"] + "; 128 B per clock per SM from L1 to registers"}
     achieved = kern[dom]["flop"] / (kern[dom]["ms"] * 1e-3) / 1e12
-    tr = TRAFFIC.get(dom)
-    traffic = (tr["bytes_per_launch"] if tr and WORKLOAD == TRAFFIC_WORKLOAD and tr.get("source_sha") == _source_sha()
-               else None)
+    traffic = ncu[dom]["dram_bytes"] if ncu.get(dom) else None
+    issue = None
+    if ncu.get(dom):
+        ach_i = ncu[dom]["warp_instructions"] / (kern[dom]["ms"] * 1e-3)
+        issue = {"warp_instructions": ncu[dom]["warp_instructions"], "achieved": ach_i / 1e12,
+                 "peak": roofs["issue_per_s"] / 1e12, "unit": "T warp-instr/s", "frac": ach_i / roofs["issue_per_s"]}
     cpu = None
     if ws == 1 and args.cpu_iters > 0:
         rate, cores, dt = cpu_oracle_rate(args.cpu_iters)
         cpu = {"value": rate, "unit": "iter/s", "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_iters} full MOCCA iterations of {WORKLOAD} (FP64 C oracle, {dt:.1f} s)"}
+        if args.cpu_iters_1t > 0:
+            r1, _, dt1 = cpu_oracle_rate(args.cpu_iters_1t, threads=1)
+            cpu["one_thread"] = {"value": r1, "unit": "iter/s", "cores": 1,
+                                 "sample": f"{args.cpu_iters_1t} full MOCCA iteration(s), one thread ({dt1:.1f} s)"}
     line = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
@@ -354,9 +413,11 @@ def run_gpu(args):
         "kernel_ms": {k: v["ms"] for k, v in kern.items()},
         "footprint_pairs": nnz,
         "intersections_per_s": 2.0 * nnz / (total_s / args.steps) * ws,
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and max clock)"},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": roofs["fp32_tflops"],
+                     "unit": "TFLOP/s", "frac": achieved / roofs["fp32_tflops"], "traffic": traffic,
+                     "peak_source": roofs["source"] + "; 128 FP32 lanes x 2 flop per clock per SM",
+                     "binding": {"unit": "instruction issue", **issue} if issue else None},
+        "kernels": kernels,
         "gather_roofline": gather,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_rate, "unit": "iter/s", "h2d_bytes_per_step": int(c_host.numel() * 4),
@@ -368,7 +429,7 @@ def run_gpu(args):
         "served": served,
         "batched": batched,
         "served_mixed": mixed,
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "gpu_launches": 4 * args.steps,
         "dtpl_last": d_last,
         "maps_finite": finite,
@@ -611,11 +672,12 @@ def main():
                     help="the 256x256 headline workload, or the 512x512 solve for profiling")
     ap.add_argument("--e2e", type=int, default=3, help="full reconstructions for the end-to-end rate")
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle iterations for the CPU baseline")
+    ap.add_argument("--cpu-iters-1t", type=int, default=1, help="oracle iterations on one thread (0: skip)")
     ap.add_argument("--served", type=int, default=16, help="requests for the served measurement (0: skip)")
     ap.add_argument("--slots", type=int, default=4, help="server slots")
     ap.add_argument("--batch", type=int, default=64, help="solves in the batched measurement (0: skip)")
     ap.add_argument("--mixed", type=int, default=16, help="mixed requests in the served sweep (0: skip)")
-    ap.add_argument("--mixed-rates", type=float, nargs="+", default=[5.0, 10.0, 20.0, 50.0],
+    ap.add_argument("--mixed-rates", type=float, nargs="+", default=[2.0, 5.0, 10.0, 20.0, 50.0],
                     help="Poisson arrival rates of the mixed served sweep, requests/s")
     ap.add_argument("--batch-steps", type=int, default=5, help="timed iterations of the batched measurement")
     ap.add_argument("--rate", type=float, default=1.5, help="Poisson request arrival rate, requests/s")

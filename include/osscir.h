@@ -84,8 +84,15 @@ typedef struct {
  * model avoids the need for constraints).  spc = 0 selects the
  * m-block-diagonal step-preconditioner of Sec. 2; spc = 1 the diagonal one of
  * Pock and Chambolle that it replaces (Sigma_wl = (1/lambda) / sum_mk |K|,
- * T_mk = lambda / sum_wl |K|, Sec. 2) — with a material basis orthogonalised
- * over energy by the caller this is the mu-PC of Sec. 2.  counts_model = 0 is
+ * T_mk = lambda / sum_wl |K|, Sec. 2); spc = 2 the mu-PC of Sec. 1 and 2: the
+ * library changes the material basis to one whose attenuation curves are
+ * orthonormal over the energy grid (Euclidean inner product; the symmetric
+ * choice M = (mu mu^T)^(-1/2), computed in FP64 at creation, mu' = M mu),
+ * iterates with the diagonal SPC on f' = M^-1 f, and returns maps in the
+ * caller's basis (f = M f') from osscir_get_maps, osscir_reconstruct and the
+ * served form; osscir_simulate takes maps in the caller's basis, while the
+ * solver state of osscir_get_state / osscir_set_state stays in the iteration's
+ * basis.  mu mu^T singular to working precision is OSSCIR_E_INVALID.  counts_model = 0 is
  * the softexp counts model of Eq. (finalModel); counts_model = 1 the standard
  * model of Eq. (fullModel) with exp for every energy (the paper's softexp
  * replaces it so that negative line integrals do not make the counts blow up);
@@ -145,7 +152,11 @@ osscir_status osscir_simulate(osscir_t h, const float *f, float *chat, void *str
 
 /* Load measured counts c_{w,l} (Eq. DTPL) and reset the solver state to
  * x_0 = xbar_0 = 0, y_0 = 0, iteration 0.
- *   c: device float[L][4], c >= 0 (copied on the stream). */
+ *   c: device float[L][4], c >= 0 and finite (copied on the stream).
+ * The counts are checked on the device, on the stream, after the copy; the
+ * call itself does not wait for the check.  The next osscir_dtpl returns
+ * OSSCIR_E_INVALID if any count was negative or not finite (the iterations in
+ * between run on those counts and their results are meaningless). */
 osscir_status osscir_set_counts(osscir_t h, const float *c, void *stream);
 
 /* Run n_iters MOCCA iterations (Sec. 1: local convex quadratic, removal of
@@ -156,11 +167,41 @@ osscir_status osscir_set_counts(osscir_t h, const float *c, void *stream);
  * osscir_reconstruct is an outer one, then every k-th. */
 osscir_status osscir_mocca_step(osscir_t h, int n_iters, void *stream);
 
+/* One MOCCA iteration split by views, for one solve shared by several GPUs
+ * (the forward and back-projections, which Sec. 1 and 2 name as the cost, are
+ * sums over rays, so the rays can be partitioned).  Every GPU holds a context
+ * of the same problem (geometry, spectra, mu, parameters, counts) in the same
+ * state.  osscir_mocca_partial runs the ray side of the iteration for the rays
+ * of the views [v0, v1) only: the forward projection at xbar, the counts model,
+ * the clipped curvature and the dual step (updating the duals of those rays),
+ * then back-projects those rays' nine per-pixel channels, K^T y' and the block
+ * step matrix P_k (T^-1_k = P_k / lambda), into chan.  It does not change the
+ * maps.  The caller sums chan over a partition of the views into ranges (one
+ * all-reduce of 9 P floats per iteration); osscir_mocca_apply then takes every
+ * pixel's primal step (the FP64 3x3 solve of the m-block SPC, the optional box,
+ * the extrapolation) from the summed channels and counts the iteration.  With
+ * the views of all ranges summed, the iterates equal osscir_mocca_step's up to
+ * the order of the floating-point additions.
+ *   v0, v1: 0 <= v0 < v1 <= n_views;
+ *   chan:   device float[9][P] (channel-major: channels 0-2 K^T y' for the three
+ *           materials, 3-8 P_k packed as 00 01 02 11 12 22), written by partial,
+ *           read by apply.
+ * Asynchronous on the stream.  After osscir_mocca_partial, osscir_dtpl(h, 1)
+ * returns the D_TPL terms of the rays of [v0, v1) only (the ranges' values add
+ * up to the whole).  Errors: OSSCIR_E_INVALID (bad range, NULL chan, a nested
+ * solve: inner > 1), OSSCIR_E_CUDA. */
+osscir_status osscir_mocca_partial(osscir_t h, int v0, int v1, float *chan, void *stream);
+osscir_status osscir_mocca_apply(osscir_t h, const float *chan, void *stream);
+
 /* End-to-end reconstruction with host buffers: copies the counts c (host
  * float[L][4], c >= 0; pinned memory makes the copy asynchronous DMA) to the
  * device, resets the state as osscir_set_counts does, runs n_iters MOCCA
  * iterations and copies the maps x_n to maps_out (host float[P][4]).
- * Synchronises the stream before returning. */
+ * Synchronises the stream before returning.  Errors: OSSCIR_E_INVALID (NULL
+ * arguments, n_iters < 0, or a count that is negative or not finite, checked
+ * on the host before anything is enqueued), OSSCIR_E_DIVERGED (the D_TPL of
+ * the last iteration is not finite; maps_out holds the non-finite maps),
+ * OSSCIR_E_CUDA. */
 osscir_status osscir_reconstruct(osscir_t h, const float *c_host, int n_iters, float *maps_out_host,
                                  void *stream);
 
@@ -172,7 +213,8 @@ osscir_status osscir_reconstruct(osscir_t h, const float *c_host, int n_iters, f
  * step-preconditioner and primal step.  Synchronises the stream. */
 osscir_status osscir_last_kernel_ms(osscir_t h, float *ms, void *stream);
 
-/* Copy the current material maps x_n to x_out: device float[P][4]. */
+/* Copy the current material maps x_n to x_out: device float[P][4] (in the
+ * caller's material basis; see spc = 2). */
 osscir_status osscir_get_maps(osscir_t h, float *x_out, void *stream);
 
 /* Checkpoint / resume of the solver state (x_n, xbar_n, y_n, n).  All arrays
@@ -188,7 +230,9 @@ osscir_status osscir_set_state(osscir_t h, const float *x, const float *xbar, co
  * maps x_n (one extra forward projection); which = 1 returns the value the last
  * iteration computed at its expansion point xbar (for a nested solve, the last
  * outer iteration: inner iterations do not evaluate the counts model).
- * Synchronises the stream; out: host double. */
+ * Synchronises the stream; out: host double.  Errors: OSSCIR_E_INVALID also
+ * when the counts loaded by the last osscir_set_counts failed its check;
+ * OSSCIR_E_DIVERGED when the value is not finite. */
 osscir_status osscir_dtpl(osscir_t h, int which, double *out, void *stream);
 
 /* Footprint dumps for verification: for rays [l0, l0+n) (or pixels [k0, k0+n))
@@ -341,8 +385,9 @@ osscir_status osscir_poll(osscir_server_t s, uint64_t ticket, int timeout_ms, fl
  * (any pointer may be NULL). */
 osscir_status osscir_server_info(osscir_server_t s, int *running, int *queued, size_t *bytes_in_use);
 
-/* D_TPL (Eq. DTPL form) of expected counts chat and measured counts c, computed
- * without allocating any memory and without a context.  The paper has no
+/* The transmission-Poisson data discrepancy of expected counts chat against
+ * measured counts c, computed without allocating any memory and without a
+ * context.  The paper has no
  * counterpart: this serves callers that must not call cudaMalloc after
  * start-up, for example a server whose memory arena claims the device at
  * launch, or a latency-bound loop that cannot accept the synchronisation an

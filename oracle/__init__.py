@@ -316,6 +316,29 @@ def mocca(geom, spectra, c, n_iters, lam, state=None, *, box=None, spc="block",
     return st, hist
 
 
+# --------------------------------------------------------------------------- mu-PC basis change
+
+def mu_pc(mu):
+    """mu-PC (Sec. 1 and 2): (mu_t, M) with mu_t = M mu, whose rows are
+    orthonormal over the energy grid in the Euclidean inner product, and
+    M = (mu mu^T)^(-1/2), the symmetric choice (the paper leaves the
+    orthogonalisation to Barber et al. 2016).  numpy's eigh is the step."""
+    mu = np.asarray(mu, dtype=np.float64)
+    w, V = np.linalg.eigh(mu @ mu.T)
+    M = V @ np.diag(w ** -0.5) @ V.T
+    return M @ mu, M
+
+
+def maps_to_basis(f, M):
+    """Maps in the mu-PC basis, f' = M^-1 f per pixel (f [P, 3]), so that mu_t^T f' = mu^T f."""
+    return np.asarray(f, dtype=np.float64) @ np.linalg.inv(M).T
+
+
+def maps_from_basis(f_t, M):
+    """Maps in the original basis, f = M f' per pixel."""
+    return np.asarray(f_t, dtype=np.float64) @ np.asarray(M).T
+
+
 # --------------------------------------------------------------------------- seeded Poisson noise
 
 def philox4x32_10(ctr, key):

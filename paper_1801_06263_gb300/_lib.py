@@ -31,7 +31,8 @@ EXPORTS = (
     "osscir_footprint_pixels", "osscir_reconstruct", "osscir_last_kernel_ms", "osscir_dtpl_counts_static",
     "osscir_server_create", "osscir_server_destroy", "osscir_submit", "osscir_poll", "osscir_server_info",
     "osscir_batch_create", "osscir_batch_destroy", "osscir_batch_step", "osscir_batch_get_config",
-    "osscir_batch_set_config", "osscir_batch_last_kernel_ms", "osscir_poisson_noise",
+    "osscir_batch_set_config", "osscir_batch_last_kernel_ms", "osscir_poisson_noise", "osscir_mocca_partial",
+    "osscir_mocca_apply",
 )
 
 
@@ -126,6 +127,8 @@ def load(build_if_missing: bool = True):
         "osscir_batch_set_config": ([vp, ct.POINTER(BatchConfig)], ct.c_int),
         "osscir_batch_last_kernel_ms": ([vp, ct.POINTER(ct.c_float), vp], ct.c_int),
         "osscir_poisson_noise": ([vp, ct.c_int, ct.c_uint64, vp, vp], ct.c_int),
+        "osscir_mocca_partial": ([vp, ct.c_int, ct.c_int, vp, vp], ct.c_int),
+        "osscir_mocca_apply": ([vp, vp, vp], ct.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -260,6 +263,17 @@ def osscir_footprint_pixels(h, k0, n, cap, cnt, idx, wt, stream=None):
         ct.c_void_p(h), int(k0), int(n), int(cap), _ptr(cnt), _ptr(idx), _ptr(wt), _stream(stream)))
 
 
+def osscir_mocca_partial(h, v0, v1, chan, stream=None):
+    """Ray side of one iteration for the views [v0, v1); chan: contiguous float32 CUDA tensor [9, P]."""
+    _check("osscir_mocca_partial", load().osscir_mocca_partial(ct.c_void_p(h), int(v0), int(v1), _ptr(chan),
+                                                               _stream(stream)))
+
+
+def osscir_mocca_apply(h, chan, stream=None):
+    """Primal step of every pixel from the channels summed over all view ranges (chan [9, P])."""
+    _check("osscir_mocca_apply", load().osscir_mocca_apply(ct.c_void_p(h), _ptr(chan), _stream(stream)))
+
+
 def osscir_reconstruct(h, c_host, n_iters, maps_out_host, stream=None):
     """c_host [L, 4] and maps_out_host [P, 4]: contiguous float32 CPU tensors (pinned for DMA)."""
     if c_host.is_cuda or maps_out_host.is_cuda:
@@ -278,6 +292,14 @@ def osscir_last_kernel_ms(h, stream=None):
 def osscir_dtpl_counts_static(chat, c, out, stream=None):
     """D_TPL of expected counts chat and measured counts c (device float32 [L, 4])
     into out (device float64 [1]) without allocating memory; see include/osscir.h."""
+    import torch
+    for name, t in (("chat", chat), ("c", c)):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.dim() == 2 and t.shape[1] == 4):
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of shape [L, 4]")
+    if c.shape != chat.shape or c.device != chat.device:
+        raise ValueError("chat and c must have the same shape and device")
+    if not (out.is_cuda and out.dtype == torch.float64 and out.numel() >= 1 and out.device == chat.device):
+        raise ValueError("out must be a float64 CUDA tensor with at least one element on the device of chat")
     _check("osscir_dtpl_counts_static", load().osscir_dtpl_counts_static(
         _ptr(chat), _ptr(c), int(chat.shape[0]), _ptr(out), _stream(stream)))
 

@@ -1,5 +1,6 @@
 // C-ABI of the library (include/osscir.h): context creation, validation,
 // per-geometry tables, and the per-iteration CUDA graph.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -50,14 +51,116 @@ void free_ctx(osscir_ctx* h) {
         if (e) cudaEventDestroy(e);
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->join) cudaEventDestroy(h->join);
-    void* ptrs[] = {h->rec, h->r64, h->views, h->chord, h->exc_off, h->exc_ent, h->s4, h->N4, h->mu,
-                    h->g, h->c, h->y, h->x, h->xbar, h->dtpl_part, h->dtpl_out, h->model};
+    void* ptrs[] = {h->rec,     h->r64,    h->views,     h->chord,    h->exc_off,    h->exc_ent,  h->s4,
+                    h->N4,      h->mu,     h->mu_in,     h->g,        h->c,          h->y,        h->x,
+                    h->xbar,    h->xo,     h->dtpl_part, h->dtpl_out, h->bad_counts, h->model,    h->fwd_row,
+                    h->fwd_cnt, h->fwd_pairs, h->bp_row, h->bp_cnt,   h->bp_pairs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
 }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// Measured counts must be finite and >= 0 (Eq. DTPL takes c log c).
+bool counts_valid(const float* c, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!(c[i] >= 0.0f) || !std::isfinite(c[i])) return false;
+    return true;
+}
+
+// The same check on device counts: any invalid value sets *bad (never cleared here).
+__global__ void k_check_counts(const float4* __restrict__ c, int L, int* bad) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < L; l += gridDim.x * blockDim.x) {
+        const float4 v = c[l];
+        const bool ok = v.x >= 0.0f && v.y >= 0.0f && v.z >= 0.0f && v.w >= 0.0f && isfinite(v.x) &&
+                        isfinite(v.y) && isfinite(v.z) && isfinite(v.w);
+        if (!ok) *bad = 1;
+    }
+}
+
+// Eigen-decomposition of a symmetric 3x3 matrix A (row-major) by cyclic Jacobi
+// rotations (Golub and Van Loan, Sec. 8.5): A = V diag(w) V^T, V's columns the
+// eigenvectors.
+void sym3_eigen(const double A[9], double w[3], double V[9]) {
+    double a[3][3] = {{A[0], A[1], A[2]}, {A[3], A[4], A[5]}, {A[6], A[7], A[8]}};
+    double v[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        const double dia = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+        if (!(off > 1e-32 * dia)) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (a[p][q] == 0.0) continue;
+                const double theta = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 3; ++k) {   // A <- A J (columns p, q)
+                    const double akp = a[k][p], akq = a[k][q];
+                    a[k][p] = c * akp - s * akq;
+                    a[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {   // A <- J^T A (rows p, q)
+                    const double apk = a[p][k], aqk = a[q][k];
+                    a[p][k] = c * apk - s * aqk;
+                    a[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {   // V <- V J
+                    const double vkp = v[k][p], vkq = v[k][q];
+                    v[k][p] = c * vkp - s * vkq;
+                    v[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < 3; ++i) {
+        w[i] = a[i][i];
+        for (int j = 0; j < 3; ++j) V[i * 3 + j] = v[i][j];
+    }
+}
+
+// mu-PC (Sec. 1 and 2): a material basis whose attenuation curves are
+// orthonormal over the energy grid (Euclidean inner product), with the symmetric
+// choice M = (mu mu^T)^(-1/2), so mu' = M mu and, for unchanged line integrals
+// (mu'^T f' = mu^T f), f' = M^-1 f.  Writes M (row-major, symmetric) and mu' in
+// FP64; false if mu mu^T is singular to working precision.
+bool mu_pc_basis(const float* mu, int nE, double M[9], std::vector<double>& mu_t) {
+    double Gm[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int e = 0; e < nE; ++e) acc += (double)mu[i * nE + e] * (double)mu[j * nE + e];
+            Gm[i * 3 + j] = acc;
+        }
+    double w[3], V[9];
+    sym3_eigen(Gm, w, V);
+    const double wmax = std::max(w[0], std::max(w[1], w[2]));
+    for (int k = 0; k < 3; ++k)
+        if (!(w[k] > 1e-14 * wmax) || !std::isfinite(w[k])) return false;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += V[i * 3 + k] * V[j * 3 + k] / std::sqrt(w[k]);
+            M[i * 3 + j] = acc;
+        }
+    mu_t.assign((size_t)3 * nE, 0.0);
+    for (int i = 0; i < 3; ++i)
+        for (int e = 0; e < nE; ++e)
+            mu_t[(size_t)i * nE + e] = M[i * 3 + 0] * mu[e] + M[i * 3 + 1] * mu[nE + e] + M[i * 3 + 2] * mu[2 * nE + e];
+    return true;
+}
+
+// Maps from the mu-PC basis to the caller's: f = M f' per pixel (FP64 arithmetic).
+struct Basis3 {
+    double m[9];
+};
+__global__ void k_maps_out(const float4* __restrict__ x, Basis3 B, float4* __restrict__ out, int P) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    const float4 v = x[k];
+    const double a = v.x, b = v.y, c = v.z;
+    out[k] = make_float4((float)(B.m[0] * a + B.m[1] * b + B.m[2] * c), (float)(B.m[3] * a + B.m[4] * b + B.m[5] * c),
+                         (float)(B.m[6] * a + B.m[7] * b + B.m[8] * c), 0.f);
+}
 
 osscir_status validate(const osscir_geometry* g, const osscir_spectra* sp, const float* mu,
                        const osscir_params* pa) {
@@ -87,7 +190,12 @@ osscir_status validate(const osscir_geometry* g, const osscir_spectra* sp, const
         if (!std::isfinite(mu[i])) return OSSCIR_E_INVALID;
     if (!finite_pos(pa->lambda) || !(pa->lambda < 3.0e38)) return OSSCIR_E_INVALID;
     if (pa->model != 0 && pa->model != 1) return OSSCIR_E_INVALID;
-    if (pa->spc != 0 && pa->spc != 1) return OSSCIR_E_INVALID;
+    if (pa->spc < 0 || pa->spc > 2) return OSSCIR_E_INVALID;
+    if (pa->spc == 2) {
+        double M[9];
+        std::vector<double> mu_t;
+        if (!mu_pc_basis(mu, nE, M, mu_t)) return OSSCIR_E_INVALID;
+    }
     if (pa->counts_model != 0 && pa->counts_model != 1) return OSSCIR_E_INVALID;
     if (pa->inner < 0 || pa->inner > 1000000) return OSSCIR_E_INVALID;
     if (pa->use_box)
@@ -130,7 +238,8 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     C.margin_bins = 0.01f;
     h->params.lambda = (float)pa->lambda;
     h->params.model = pa->model;
-    h->params.spc = pa->spc;
+    h->params.spc = pa->spc == 2 ? 1 : pa->spc;   // mu-PC runs the diagonal SPC in its basis
+    h->basis = pa->spc == 2;
     h->exp_model = pa->counts_model;
     h->inner = pa->inner > 1 ? pa->inner : 1;
     h->params.use_box = pa->use_box;
@@ -149,6 +258,10 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     CK(dalloc(&h->s4, (size_t)nE * g->n_bins));
     CK(dalloc(&h->N4, g->n_bins));
     CK(dalloc(&h->mu, 3 * nE));
+    if (h->basis) {
+        CK(dalloc(&h->mu_in, 3 * nE));
+        CK(dalloc(&h->xo, P));
+    }
     CK(dalloc(&h->g, L));
     CK(dalloc(&h->c, L));
     CK(dalloc(&h->y, L));
@@ -156,6 +269,7 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     CK(dalloc(&h->xbar, P));
     CK(dalloc(&h->dtpl_part, h->n_part));
     CK(dalloc(&h->dtpl_out, 2));
+    CK(dalloc(&h->bad_counts, 2));
     if (h->inner > 1) CK(dalloc(&h->model, (size_t)kModelStride * L));
     CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
@@ -173,7 +287,15 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
                     s4[((size_t)i * g->n_bins + b) * 4 + w] = sp->s[((size_t)b * nE + i) * 4 + w];
         CK(cudaMemcpy(h->s4, s4.data(), s4.size() * sizeof(float), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(h->N4, sp->N, sizeof(float) * 4 * g->n_bins, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(h->mu, mu, sizeof(float) * 3 * nE, cudaMemcpyHostToDevice));
+        if (h->basis) {
+            std::vector<double> mu_t;
+            if (!mu_pc_basis(mu, nE, h->Mb, mu_t)) return OSSCIR_E_INVALID;
+            std::vector<float> mu32(mu_t.begin(), mu_t.end());
+            CK(cudaMemcpy(h->mu, mu32.data(), sizeof(float) * 3 * nE, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(h->mu_in, mu, sizeof(float) * 3 * nE, cudaMemcpyHostToDevice));
+        } else {
+            CK(cudaMemcpy(h->mu, mu, sizeof(float) * 3 * nE, cudaMemcpyHostToDevice));
+        }
     }
     // per-ray records, then the footprint pairs decided in FP64
     CK(launch_ray_setup(G, r_img, h->rec, h->r64, h->views, st));
@@ -199,7 +321,97 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     CK(cudaMemsetAsync(h->x, 0, sizeof(float4) * P, st));
     CK(cudaMemsetAsync(h->xbar, 0, sizeof(float4) * P, st));
     CK(cudaMemsetAsync(h->dtpl_out, 0, sizeof(double) * 2, st));
+    CK(cudaMemsetAsync(h->bad_counts, 0, 2 * sizeof(int), st));
     CK(cudaStreamSynchronize(st));
+    return OSSCIR_OK;
+}
+
+void free_tables(osscir_ctx* h) {
+    void* ptrs[] = {h->fwd_row, h->fwd_cnt, h->fwd_pairs, h->bp_row, h->bp_cnt, h->bp_pairs};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    h->fwd_row = nullptr;
+    h->fwd_cnt = nullptr;
+    h->fwd_pairs = nullptr;
+    h->bp_row = nullptr;
+    h->bp_cnt = nullptr;
+    h->bp_pairs = nullptr;
+    h->bytes -= h->fp_bytes;
+    h->fp_bytes = 0;
+}
+
+// Device array of the prefix sums of n counts (in place on the host copy), with
+// its total appended; false if the total does not fit 32 bits.
+bool prefix_rows(std::vector<uint32_t>& v, size_t n) {
+    uint64_t run = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const uint64_t c = v[i];
+        v[i] = (uint32_t)run;
+        run += c;
+    }
+    if (run > 0xffffffffull) return false;
+    v[n] = (uint32_t)run;
+    return true;
+}
+
+// Build the footprint tables (FpTables) once per context, before the first
+// iteration graph is captured.  If the device has no room for them the context
+// keeps the on-the-fly projections (the same results, computed again every
+// iteration).
+osscir_status build_tables(osscir_ctx* h) {
+    if (h->fp_state != 0) return OSSCIR_OK;
+    cudaStream_t st = h->cap_stream;
+    const GeomC& C = h->gc;
+    const size_t nbg = (C.n_bins + 31) / 32, n_fw = (size_t)C.n_views * nbg;
+    const int G = bp_view_groups(h->P, C.n_views);
+    const size_t n_bw = (size_t)fp_tiles(C.grid.n) * G;
+    size_t before = h->bytes;
+    g_dalloc_bytes = &h->bytes;
+    auto fail = [&](cudaError_t e) -> osscir_status {
+        g_dalloc_bytes = &g_dalloc_bytes_sink;
+        h->fp_bytes = h->bytes - before;
+        free_tables(h);
+        if (e == cudaErrorMemoryAllocation) {   // no room: keep the on-the-fly projections
+            cudaGetLastError();
+            h->fp_state = -1;
+            return OSSCIR_OK;
+        }
+        return from_cuda(e);
+    };
+#define CKT(expr)                                    \
+    do {                                             \
+        const cudaError_t e_ = (expr);               \
+        if (e_ != cudaSuccess) return fail(e_);      \
+    } while (0)
+    // forward: per-ray counts and per-warp rows, then the pairs
+    CKT(dalloc(&h->fwd_cnt, (size_t)h->L));
+    CKT(dalloc(&h->fwd_row, n_fw + 1));
+    CKT(launch_fp_fwd_count(C, h->exc(), h->rec, h->fwd_cnt, h->fwd_row, st));
+    std::vector<uint32_t> rows(n_fw + 1, 0);
+    CKT(cudaMemcpyAsync(rows.data(), h->fwd_row, sizeof(uint32_t) * n_fw, cudaMemcpyDeviceToHost, st));
+    CKT(cudaStreamSynchronize(st));
+    if (!prefix_rows(rows, n_fw)) return fail(cudaErrorMemoryAllocation);
+    CKT(cudaMemcpyAsync(h->fwd_row, rows.data(), sizeof(uint32_t) * (n_fw + 1), cudaMemcpyHostToDevice, st));
+    CKT(dalloc(&h->fwd_pairs, (size_t)rows[n_fw] * 32));
+    CKT(launch_fp_fwd_fill(C, h->exc(), h->rec, h->fwd_row, h->fwd_pairs, st));
+    // back-projection: per-lane counts and per-warp rows of each (tile, view group), then the pairs
+    CKT(dalloc(&h->bp_cnt, n_bw * 32));
+    CKT(dalloc(&h->bp_row, n_bw + 1));
+    CKT(launch_fp_bp_count(C, h->exc(), h->rec, h->views, G, h->bp_cnt, h->bp_row, st));
+    std::vector<uint32_t> brow(n_bw + 1, 0);
+    CKT(cudaMemcpyAsync(brow.data(), h->bp_row, sizeof(uint32_t) * n_bw, cudaMemcpyDeviceToHost, st));
+    CKT(cudaStreamSynchronize(st));
+    if (!prefix_rows(brow, n_bw)) return fail(cudaErrorMemoryAllocation);
+    CKT(cudaMemcpyAsync(h->bp_row, brow.data(), sizeof(uint32_t) * (n_bw + 1), cudaMemcpyHostToDevice, st));
+    CKT(dalloc(&h->bp_pairs, (size_t)brow[n_bw] * 32));
+    CKT(launch_fp_bp_fill(C, h->exc(), h->rec, h->views, G, h->bp_row, h->bp_pairs, st));
+    CKT(cudaStreamSynchronize(st));
+#undef CKT
+    g_dalloc_bytes = &g_dalloc_bytes_sink;
+    h->bp_groups = G;
+    h->fp_bytes = h->bytes - before;
+    h->fp_tab = h->fp();
+    h->fp_state = 1;
     return OSSCIR_OK;
 }
 
@@ -212,7 +424,7 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
 cudaError_t enqueue_iteration(osscir_ctx* h, cudaStream_t st, bool inner_step) {
     cudaError_t e = cudaEventRecordWithFlags(h->ev[0], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
-    e = launch_mocca_proj(h->gc, h->exc(), h->rec, h->solve(), st);
+    e = launch_mocca_proj(h->gc, h->exc(), h->rec, h->solve(), st, 0, -1, h->fp_or_null());
     if (e != cudaSuccess) return e;
     e = cudaEventRecordWithFlags(h->ev[1], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
@@ -221,7 +433,7 @@ cudaError_t enqueue_iteration(osscir_ctx* h, cudaStream_t st, bool inner_step) {
         if (e != cudaSuccess) return e;
         e = cudaEventRecordWithFlags(h->ev[2], st, cudaEventRecordExternal);
         if (e != cudaSuccess) return e;
-        e = launch_mocca_bp(h->gc, h->exc(), h->rec, h->views, h->params, h->solve(), st);
+        e = launch_mocca_bp(h->gc, h->exc(), h->rec, h->views, h->params, h->solve(), st, h->fp_or_null());
         if (e != cudaSuccess) return e;
         return cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal);
     }
@@ -238,7 +450,7 @@ cudaError_t enqueue_iteration(osscir_ctx* h, cudaStream_t st, bool inner_step) {
     if (e != cudaSuccess) return e;
     e = cudaEventRecordWithFlags(h->ev[2], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
-    e = launch_mocca_bp(h->gc, h->exc(), h->rec, h->views, h->params, h->solve(), st);
+    e = launch_mocca_bp(h->gc, h->exc(), h->rec, h->views, h->params, h->solve(), st, h->fp_or_null());
     if (e != cudaSuccess) return e;
     e = cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal);
     if (e != cudaSuccess) return e;
@@ -261,6 +473,8 @@ osscir_status capture(osscir_ctx* h, bool inner_step, cudaGraph_t* graph, cudaGr
 }
 
 osscir_status ensure_graph(osscir_ctx* h) {
+    const osscir_status ts = build_tables(h);   // before the capture: the launches take the tables
+    if (ts != OSSCIR_OK) return ts;
     if (!h->gexec) {
         const osscir_status s = capture(h, false, &h->graph, &h->gexec);
         if (s != OSSCIR_OK) return s;
@@ -298,6 +512,27 @@ osscir_status ctx_validate(const osscir_geometry* geom, const osscir_spectra* sp
 }
 
 osscir_status ctx_ensure_graph(osscir_ctx* h) { return ensure_graph(h); }
+
+cudaError_t ctx_maps_out(const osscir_ctx* h, const float4* x, float4* out, cudaStream_t st) {
+    if (!h->basis) return cudaMemcpyAsync(out, x, sizeof(float4) * h->P, cudaMemcpyDeviceToDevice, st);
+    Basis3 B;
+    for (int i = 0; i < 9; ++i) B.m[i] = h->Mb[i];
+    k_maps_out<<<(h->P + 255) / 256, 256, 0, st>>>(x, B, out, h->P);
+    return cudaGetLastError();
+}
+
+void ctx_maps_out_host(const osscir_ctx* h, float* maps) {
+    if (!h->basis) return;
+    const double* M = h->Mb;
+    for (int k = 0; k < h->P; ++k) {
+        float* v = maps + (size_t)4 * k;
+        const double a = v[0], b = v[1], c = v[2];
+        v[0] = (float)(M[0] * a + M[1] * b + M[2] * c);
+        v[1] = (float)(M[3] * a + M[4] * b + M[5] * c);
+        v[2] = (float)(M[6] * a + M[7] * b + M[8] * c);
+        v[3] = 0.f;
+    }
+}
 
 }  // namespace osscir
 
@@ -352,7 +587,7 @@ osscir_status osscir_backproject(osscir_t h, const float* rf, float* img, void* 
 
 osscir_status osscir_simulate(osscir_t h, const float* f, float* chat, void* stream) {
     if (!h || !f || !chat) return OSSCIR_E_INVALID;
-    CK(launch_counts(h->gc, h->exc(), h->rec, h->spec(), reinterpret_cast<const float4*>(f),
+    CK(launch_counts(h->gc, h->exc(), h->rec, h->spec_in(), reinterpret_cast<const float4*>(f),
                      reinterpret_cast<float4*>(chat), nullptr, nullptr, as_stream(stream)));
     return OSSCIR_OK;
 }
@@ -361,6 +596,9 @@ osscir_status osscir_set_counts(osscir_t h, const float* c, void* stream) {
     if (!h || !c) return OSSCIR_E_INVALID;
     cudaStream_t st = as_stream(stream);
     CK(cudaMemcpyAsync(h->c, c, sizeof(float4) * h->L, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(h->bad_counts, 0, sizeof(int), st));
+    k_check_counts<<<std::min((h->L + 255) / 256, 1024), 256, 0, st>>>(h->c, h->L, h->bad_counts);
+    CK(cudaGetLastError());
     CK(cudaMemsetAsync(h->y, 0, sizeof(float4) * h->L, st));
     CK(cudaMemsetAsync(h->x, 0, sizeof(float4) * h->P, st));
     CK(cudaMemsetAsync(h->xbar, 0, sizeof(float4) * h->P, st));
@@ -382,9 +620,32 @@ osscir_status osscir_mocca_step(osscir_t h, int n_iters, void* stream) {
     return OSSCIR_OK;
 }
 
+osscir_status osscir_mocca_partial(osscir_t h, int v0, int v1, float* chan, void* stream) {
+    if (!h || !chan || v0 < 0 || v1 > h->gc.n_views || v0 >= v1 || h->inner > 1) return OSSCIR_E_INVALID;
+    const osscir_status ts = build_tables(h);
+    if (ts != OSSCIR_OK) return ts;
+    cudaStream_t st = as_stream(stream);
+    const SolveD D = h->solve();
+    CK(launch_mocca_proj(h->gc, h->exc(), h->rec, D, st, v0, v1, h->fp_or_null()));
+    CK(launch_mocca_ray(h->gc, h->rec, h->spec(), h->params, D, st, v0, v1));
+    const int nbg = (h->gc.n_bins + 31) / 32;   // D_TPL partials per view
+    CK(launch_dtpl_reduce(h->dtpl_part + (size_t)v0 * nbg, (v1 - v0) * nbg, h->dtpl_out + 1, st));
+    CK(launch_mocca_bp_partial(h->gc, h->exc(), h->rec, h->views, h->params, D, v0, v1, chan, st,
+                               h->fp_or_null()));
+    return OSSCIR_OK;
+}
+
+osscir_status osscir_mocca_apply(osscir_t h, const float* chan, void* stream) {
+    if (!h || !chan || h->inner > 1) return OSSCIR_E_INVALID;
+    CK(launch_mocca_apply(h->gc, h->params, h->solve(), chan, as_stream(stream)));
+    h->iter += 1;
+    return OSSCIR_OK;
+}
+
 osscir_status osscir_reconstruct(osscir_t h, const float* c_host, int n_iters, float* maps_out_host,
                                  void* stream) {
     if (!h || !c_host || !maps_out_host || n_iters < 0) return OSSCIR_E_INVALID;
+    if (!counts_valid(c_host, (size_t)4 * h->L)) return OSSCIR_E_INVALID;
     cudaStream_t st = as_stream(stream);
     CK(cudaMemcpyAsync(h->c, c_host, sizeof(float4) * h->L, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(h->y, 0, sizeof(float4) * h->L, st));
@@ -394,8 +655,19 @@ osscir_status osscir_reconstruct(osscir_t h, const float* c_host, int n_iters, f
     h->phase = 0;
     const osscir_status s = osscir_mocca_step(h, n_iters, stream);
     if (s != OSSCIR_OK) return s;
-    CK(cudaMemcpyAsync(maps_out_host, h->x, sizeof(float4) * h->P, cudaMemcpyDeviceToHost, st));
+    const float4* xs = h->x;
+    if (h->basis) {
+        CK(ctx_maps_out(h, h->x, h->xo, st));
+        xs = h->xo;
+    }
+    CK(cudaMemcpyAsync(maps_out_host, xs, sizeof(float4) * h->P, cudaMemcpyDeviceToHost, st));
+    double d = 0.0;   // D_TPL at the last expansion point (the value the iterations computed)
+    int kerr = 0;
+    if (n_iters > 0) CK(cudaMemcpyAsync(&d, h->dtpl_out + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&kerr, h->bad_counts + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (kerr) return OSSCIR_E_CUDA;
+    if (!std::isfinite(d)) return OSSCIR_E_DIVERGED;
     return OSSCIR_OK;
 }
 
@@ -409,7 +681,7 @@ osscir_status osscir_last_kernel_ms(osscir_t h, float* ms, void* stream) {
 
 osscir_status osscir_get_maps(osscir_t h, float* x_out, void* stream) {
     if (!h || !x_out) return OSSCIR_E_INVALID;
-    CK(cudaMemcpyAsync(x_out, h->x, sizeof(float4) * h->P, cudaMemcpyDeviceToDevice, as_stream(stream)));
+    CK(ctx_maps_out(h, h->x, reinterpret_cast<float4*>(x_out), as_stream(stream)));
     return OSSCIR_OK;
 }
 
@@ -442,8 +714,12 @@ osscir_status osscir_dtpl(osscir_t h, int which, double* out, void* stream) {
         CK(launch_counts(h->gc, h->exc(), h->rec, h->spec(), h->x, nullptr, h->c, h->dtpl_part, st));
         CK(launch_dtpl_reduce(h->dtpl_part, h->n_part, h->dtpl_out, st));
     }
+    int bad[2] = {0, 0};
     CK(cudaMemcpyAsync(out, h->dtpl_out + which, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(bad, h->bad_counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (bad[1]) return OSSCIR_E_CUDA;
+    if (bad[0]) return OSSCIR_E_INVALID;
     if (!std::isfinite(*out)) return OSSCIR_E_DIVERGED;
     return OSSCIR_OK;
 }

@@ -71,12 +71,20 @@ __device__ __forceinline__ int ray_of_thread(const GeomC& C) {
     return ray_at(C, blockIdx.x, blockIdx.y, kFwdThreads / 32);
 }
 
+// The same tiling over the views [v0, v1) only: view v0 + (by vb + warp).
+__device__ __forceinline__ int ray_in_views(const GeomC& C, int bx, int by, int vb, int v0, int v1) {
+    const int b = bx * 32 + (threadIdx.x & 31);
+    const int v = v0 + warp_view(by, vb);
+    return (b < C.n_bins && v < v1) ? v * C.n_bins + b : -1;
+}
+
 // The warp's D_TPL partial, stored at (view, 32-bin group) whatever the block
 // shape, so the fixed-order reduction sees the same sequence for any tiling.
-__device__ __forceinline__ void warp_partial(const GeomC& C, int bx, int v, double val, double* part) {
+__device__ __forceinline__ void warp_partial(const GeomC& C, int bx, int v, double val, double* part,
+                                             int v_end = -1) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) val += __shfl_down_sync(0xffffffffu, val, o);
-    if ((threadIdx.x & 31) == 0 && v < C.n_views) part[v * ((C.n_bins + 31) >> 5) + bx] = val;
+    if ((threadIdx.x & 31) == 0 && v < (v_end < 0 ? C.n_views : v_end)) part[v * ((C.n_bins + 31) >> 5) + bx] = val;
 }
 
 __device__ __forceinline__ void load_mu_smem(const SpecD& S, float* sm) {
@@ -595,8 +603,9 @@ __device__ __forceinline__ int centre_out(int i, int n) {
     return (i & 1) ? c + (i + 1) / 2 : c - i / 2;
 }
 
-__global__ void __launch_bounds__(kFwdThreads, 8) k_mocca_proj(GeomC C, ExcTable E, const RayRec* rec, SolveD D) {
-    const int l = ray_at(C, centre_out(blockIdx.y, gridDim.y), blockIdx.x, kFwdThreads / 32);
+__global__ void __launch_bounds__(kFwdThreads, 8) k_mocca_proj(GeomC C, ExcTable E, const RayRec* rec, SolveD D,
+                                                                int v0, int v1) {
+    const int l = ray_in_views(C, centre_out(blockIdx.y, gridDim.y), blockIdx.x, kFwdThreads / 32, v0, v1);
     if (l >= 0) proj_ray(C, E, rec, D, l);
 }
 
@@ -748,13 +757,13 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
 
 template <bool KEEP>
 __global__ void __launch_bounds__(kFwdThreads, 4) k_mocca_ray(GeomC C, RayRec* rec, SpecD S, StepParams P,
-                                                              SolveD D) {
+                                                              SolveD D, int v0, int v1) {
     __shared__ float sm[kSmemStride * kMaxEnergies];
     load_mu_smem(S, sm);
     __syncthreads();
-    const int l = ray_of_thread(C);
+    const int l = ray_in_views(C, blockIdx.x, blockIdx.y, kFwdThreads / 32, v0, v1);
     const double dsum = l >= 0 ? ray_step<KEEP>(C, rec, S, P, D, sm, l) : 0.0;
-    warp_partial(C, blockIdx.x, warp_view(blockIdx.y, kFwdThreads / 32), dsum, D.dtpl_part);
+    warp_partial(C, blockIdx.x, v0 + warp_view(blockIdx.y, kFwdThreads / 32), dsum, D.dtpl_part, v1);
 }
 
 // Inner iteration of nested MOCCA: the dual prox of the kept convex model at
@@ -868,70 +877,123 @@ __device__ void box_prox3(const double Q[3][3], const double t[3], const float l
     }
 }
 
+__device__ __forceinline__ void bp_finish(const GeomC& C, const StepParams& P, const SolveD& D, int ix, int iy,
+                                          bool valid, int pix, int npix, int g, int G, float* red, float acc[9]);
+__device__ __forceinline__ void pixel_step(const GeomC& C, const StepParams& P, const SolveD& D, int k,
+                                           const float acc[9]);
+
+// The nine channels of one footprint pair (weight w != 0): K^T y' (from b in
+// r1.zw and s0.x) and the step matrix (s0.yzw, s1.xyz).
+__device__ __forceinline__ void bp_accumulate(float acc[9], float w, const float4& r1, const float4& s0,
+                                              const float4& s1) {
+    acc[0] = fmaf(w, r1.z, acc[0]);
+    acc[1] = fmaf(w, r1.w, acc[1]);
+    acc[2] = fmaf(w, s0.x, acc[2]);
+    acc[3] = fmaf(w, s0.y, acc[3]);
+    acc[4] = fmaf(w, s0.z, acc[4]);
+    acc[5] = fmaf(w, s0.w, acc[5]);
+    acc[6] = fmaf(w, s1.x, acc[6]);
+    acc[7] = fmaf(w, s1.y, acc[7]);
+    acc[8] = fmaf(w, s1.z, acc[8]);
+}
+
+// Pixel-driven back-projection of pixel (ix, iy) over the views [v0, v1):
+// for each view in order, the candidate bins of the pixel's corner shadow in
+// ascending order, each weight from x_weight, the nine channels added for the
+// nonzero ones.  Every form of the back-projection adds in this order.
+__device__ __forceinline__ void bp_pixel_sum(const GeomC& C, const ExcTable& E, const RayRec* rec,
+                                             const ViewF* views, int ix, int iy, int v0, int v1, float acc[9]) {
+    const RayStep* steps = ray_steps(rec, C.n_views * C.n_bins);
+    for (int v = v0; v < v1; ++v) {
+        int blo, bhi;
+        pixel_bin_range(C, views[v], ix, iy, blo, bhi);
+        // two candidate rays per step: both records' first halves are loaded before either is used
+        for (int b = blo; b <= bhi; b += 2) {
+            const int l = v * C.n_bins + b;
+            const bool two = b < bhi;
+            const RecHalf A = ldg_half(&rec[l].r0);
+            RecHalf B = A;
+            if (two) B = ldg_half(&rec[l + 1].r0);
+            const float wa = x_weight(A.a, A.b.x, A.b.y, C.grid, E, l, ix, iy);
+            const float wb = two ? x_weight(B.a, B.b.x, B.b.y, C.grid, E, l + 1, ix, iy) : 0.0f;
+            if (wa != 0.0f) {
+                const RecHalf A2 = ldg_half(&steps[l].s0);
+                bp_accumulate(acc, wa, A.b, A2.a, A2.b);
+            }
+            if (wb != 0.0f) {
+                const RecHalf B2 = ldg_half(&steps[l + 1].s0);
+                bp_accumulate(acc, wb, B.b, B2.a, B2.b);
+            }
+        }
+    }
+}
+
+// The views of group g of G when [V0, V1) is split into contiguous ranges.
+__device__ __forceinline__ void group_views(int V0, int V1, int g, int G, int& v0, int& v1) {
+    const int per = (V1 - V0 + G - 1) / G;
+    v0 = V0 + g * per;
+    v1 = min(V1, v0 + per);
+}
+
 // Pixel-driven back-projection with the views split over blockDim.z thread
 // groups per pixel (contiguous view ranges); the groups' partial sums are
 // added in a fixed order in shared memory, so results are deterministic.
-// One pixel's share of the tile: thread group g of G handles views
-// [g per, (g + 1) per).  red holds the tile's [G - 1][9][kBpPix] partials; every
-// thread of the block must call this (it contains a block barrier).
+// red holds the tile's [G - 1][9][kBpPix] partials; every thread of the block
+// must call this (it contains a block barrier).
 __device__ __forceinline__ void bp_pixel(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
                                          const StepParams& P, const SolveD& D, int ix, int iy, int pix, int g, int G,
                                          float* red) {
     const bool valid = ix < C.grid.n && iy < C.grid.n;
     float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (valid) {
-        const int per = (C.n_views + G - 1) / G;
-        const int v0 = g * per, v1 = min(C.n_views, v0 + per);
-        const RayStep* steps = ray_steps(rec, C.n_views * C.n_bins);
-        for (int v = v0; v < v1; ++v) {
-            int blo, bhi;
-            pixel_bin_range(C, views[v], ix, iy, blo, bhi);
-            // two candidate rays per step: both records' first halves are loaded before either is used
-            for (int b = blo; b <= bhi; b += 2) {
-                const int l = v * C.n_bins + b;
-                const bool two = b < bhi;
-                const RecHalf A = ldg_half(&rec[l].r0);
-                RecHalf B = A;
-                if (two) B = ldg_half(&rec[l + 1].r0);
-                const float wa = x_weight(A.a, A.b.x, A.b.y, C.grid, E, l, ix, iy);
-                const float wb = two ? x_weight(B.a, B.b.x, B.b.y, C.grid, E, l + 1, ix, iy) : 0.0f;
-                if (wa != 0.0f) {
-                    const RecHalf A2 = ldg_half(&steps[l].s0);
-                    acc[0] = fmaf(wa, A.b.z, acc[0]);
-                    acc[1] = fmaf(wa, A.b.w, acc[1]);
-                    acc[2] = fmaf(wa, A2.a.x, acc[2]);
-                    acc[3] = fmaf(wa, A2.a.y, acc[3]);
-                    acc[4] = fmaf(wa, A2.a.z, acc[4]);
-                    acc[5] = fmaf(wa, A2.a.w, acc[5]);
-                    acc[6] = fmaf(wa, A2.b.x, acc[6]);
-                    acc[7] = fmaf(wa, A2.b.y, acc[7]);
-                    acc[8] = fmaf(wa, A2.b.z, acc[8]);
-                }
-                if (wb != 0.0f) {
-                    const RecHalf B2 = ldg_half(&steps[l + 1].s0);
-                    acc[0] = fmaf(wb, B.b.z, acc[0]);
-                    acc[1] = fmaf(wb, B.b.w, acc[1]);
-                    acc[2] = fmaf(wb, B2.a.x, acc[2]);
-                    acc[3] = fmaf(wb, B2.a.y, acc[3]);
-                    acc[4] = fmaf(wb, B2.a.z, acc[4]);
-                    acc[5] = fmaf(wb, B2.a.w, acc[5]);
-                    acc[6] = fmaf(wb, B2.b.x, acc[6]);
-                    acc[7] = fmaf(wb, B2.b.y, acc[7]);
-                    acc[8] = fmaf(wb, B2.b.z, acc[8]);
-                }
-            }
-        }
+        int v0, v1;
+        group_views(0, C.n_views, g, G, v0, v1);
+        bp_pixel_sum(C, E, rec, views, ix, iy, v0, v1, acc);
     }
+    bp_finish(C, P, D, ix, iy, valid, pix, kBpPix, g, G, red, acc);
+}
+
+// Group g > 0 stores its partial sums in red ([G - 1][9][npix]); group 0 adds
+// them in group order and writes the nine summed channels of pixel k to
+// chan ([9][P]) for a sum over view ranges.  Contains a block barrier.
+__device__ __forceinline__ void bp_partial_out(int P_, int k, bool valid, int pix, int npix, int g, int G,
+                                               float* red, float acc[9], float* chan) {
     if (g > 0) {
 #pragma unroll
-        for (int c = 0; c < 9; ++c) red[((g - 1) * 9 + c) * kBpPix + pix] = acc[c];
+        for (int c = 0; c < 9; ++c) red[((g - 1) * 9 + c) * npix + pix] = acc[c];
     }
     __syncthreads();
     if (g != 0 || !valid) return;
     for (int gg = 1; gg < G; ++gg)
 #pragma unroll
-        for (int c = 0; c < 9; ++c) acc[c] += red[((gg - 1) * 9 + c) * kBpPix + pix];
-    const int k = iy * C.grid.n + ix;
+        for (int c = 0; c < 9; ++c) acc[c] += red[((gg - 1) * 9 + c) * npix + pix];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) chan[(size_t)c * P_ + k] = acc[c];
+}
+
+// The end of a pixel's back-projection: group g of G stores its nine partial
+// sums in red ([G - 1][9][npix]); group 0 adds the others' in group order, then
+// solves T_k v = K^T y' in FP64 and takes the primal step.  Every thread of the
+// block must call this (it contains a block barrier).
+__device__ __forceinline__ void bp_finish(const GeomC& C, const StepParams& P, const SolveD& D, int ix, int iy,
+                                          bool valid, int pix, int npix, int g, int G, float* red, float acc[9]) {
+    if (g > 0) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) red[((g - 1) * 9 + c) * npix + pix] = acc[c];
+    }
+    __syncthreads();
+    if (g != 0 || !valid) return;
+    for (int gg = 1; gg < G; ++gg)
+#pragma unroll
+        for (int c = 0; c < 9; ++c) acc[c] += red[((gg - 1) * 9 + c) * npix + pix];
+    pixel_step(C, P, D, iy * C.grid.n + ix, acc);
+}
+
+// a7 for pixel k from its nine back-projected channels: acc[0..2] = v_k = (K^T y')_k,
+// acc[3..8] = P_k (packed 00 01 02 11 12 22), T^-1_k = P_k / lambda; FP64 solve,
+// primal step (optionally onto the box) and the extrapolation xbar' = 2 x' - x.
+__device__ __forceinline__ void pixel_step(const GeomC& C, const StepParams& P, const SolveD& D, int k,
+                                           const float acc[9]) {
     const float4 x = D.x[k];
     const double il = 1.0 / (double)P.lambda;
     double T[6] = {acc[3] * il, acc[4] * il, acc[5] * il, acc[6] * il, acc[7] * il, acc[8] * il};
@@ -963,11 +1025,224 @@ __device__ __forceinline__ void bp_pixel(const GeomC& C, const ExcTable& E, cons
     D.xbar[k] = make_float4(2.f * xn.x - x.x, 2.f * xn.y - x.y, 2.f * xn.z - x.z, 0.f);
 }
 
+// The back-projection and primal step of every pixel over the views [V0, V1);
+// PARTIAL: the summed channels go to chan ([9][P]) instead of the primal step.
+template <bool PARTIAL>
 __global__ void __launch_bounds__(kBpMaxThreads) k_mocca_bp(GeomC C, ExcTable E, const RayRec* rec,
-                                                           const ViewF* views, StepParams P, SolveD D) {
+                                                           const ViewF* views, StepParams P, SolveD D, int V0,
+                                                           int V1, float* chan) {
     extern __shared__ float red[];   // [blockDim.z - 1][9][kBpPix]
     const int ix = blockIdx.x * kBpPixX + threadIdx.x, iy = blockIdx.y * kBpPixY + threadIdx.y;
-    bp_pixel(C, E, rec, views, P, D, ix, iy, threadIdx.y * kBpPixX + threadIdx.x, threadIdx.z, blockDim.z, red);
+    const int pix = threadIdx.y * kBpPixX + threadIdx.x, g = threadIdx.z, G = blockDim.z;
+    const bool valid = ix < C.grid.n && iy < C.grid.n;
+    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+        int v0, v1;
+        group_views(V0, V1, g, G, v0, v1);
+        bp_pixel_sum(C, E, rec, views, ix, iy, v0, v1, acc);
+    }
+    if (PARTIAL)
+        bp_partial_out(C.grid.n * C.grid.n, iy * C.grid.n + ix, valid, pix, kBpPix, g, G, red, acc, chan);
+    else
+        bp_finish(C, P, D, ix, iy, valid, pix, kBpPix, g, G, red, acc);
+}
+
+// a7 alone, from channels summed over view ranges (chan [9][P]).
+__global__ void k_mocca_apply(GeomC C, StepParams P, SolveD D, const float* __restrict__ chan) {
+    const int P_ = C.grid.n * C.grid.n;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P_) return;
+    float acc[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc[c] = chan[(size_t)c * P_ + k];
+    pixel_step(C, P, D, k, acc);
+}
+
+// ------------------------------------------------------------------ footprint tables
+//
+// X depends only on the geometry, so its pairs are written once per context in
+// the order in which each projector visits them, and the per-iteration
+// projections stream them instead of tracing rays and testing pixels again:
+// about 8 bytes per pair read (forward) and about 10 bytes per pixel and view
+// (back-projection) against roughly a hundred instructions of recomputation per
+// pair.  The weights are x_weight's own values and the order of additions is
+// the on-the-fly kernels' (k_mocca_proj, k_mocca_bp), so the results are bit
+// for bit the same.  See FpTables for the layout.
+
+// Forward table, pass 1: the footprint size of every ray, and per warp (view,
+// 32-bin group) the largest one: its number of slot rows.
+__global__ void __launch_bounds__(kFwdThreads) k_fp_fwd_count(GeomC C, ExcTable E, const RayRec* rec, int* cnt,
+                                                              uint32_t* warp_rows) {
+    const int l = ray_of_thread(C);
+    int n = 0;
+    if (l >= 0) {
+        const float4 r0 = rec[l].r0, r1 = rec[l].r1;
+        ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int, float) { ++n; });
+        cnt[l] = n;
+    }
+    n = __reduce_max_sync(0xffffffffu, n);
+    const int v = warp_view(blockIdx.y, kFwdThreads / 32);
+    if ((threadIdx.x & 31) == 0 && v < C.n_views) warp_rows[v * ((C.n_bins + 31) >> 5) + blockIdx.x] = (uint32_t)n;
+}
+
+// Forward table, pass 2: lane r of warp w writes its j-th pair (pixel, weight)
+// in visiting order at slot row fwd_row[w] + j.
+__global__ void __launch_bounds__(kFwdThreads) k_fp_fwd_fill(GeomC C, ExcTable E, const RayRec* rec,
+                                                             const uint32_t* __restrict__ fwd_row, int2* pairs) {
+    const int l = ray_of_thread(C);
+    if (l < 0) return;
+    const int v = warp_view(blockIdx.y, kFwdThreads / 32);
+    const size_t row = fwd_row[v * ((C.n_bins + 31) >> 5) + blockIdx.x];
+    const int lane = threadIdx.x & 31;
+    const float4 r0 = rec[l].r0, r1 = rec[l].r1;
+    int j = 0;
+    ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) {
+        pairs[(row + j) * 32 + lane] = make_int2(k, __float_as_int(w));
+        ++j;
+    });
+}
+
+// The pixel of lane `lane` in back-projection table tile t (kFpTX x kFpTY pixels).
+__device__ __forceinline__ void fp_tile_pixel(int n, int t, int lane, int& ix, int& iy) {
+    const int ntx = (n + kFpTX - 1) / kFpTX;
+    ix = (t % ntx) * kFpTX + lane % kFpTX;
+    iy = (t / ntx) * kFpTY + lane / kFpTX;
+}
+
+// The footprint pairs of pixel (ix, iy) in the views [v0, v1), in the order
+// bp_pixel_sum adds them (views ascending, candidate bins ascending, nonzero
+// weights only): visit(l, w).
+template <class Visit>
+__device__ __forceinline__ void pixel_pairs(const GeomC& C, const ExcTable& E, const RayRec* rec,
+                                            const ViewF* views, int ix, int iy, int v0, int v1, Visit&& visit) {
+    for (int v = v0; v < v1; ++v) {
+        int blo, bhi;
+        pixel_bin_range(C, views[v], ix, iy, blo, bhi);
+        for (int b = blo; b <= bhi; ++b) {
+            const int l = v * C.n_bins + b;
+            const float4 r0 = rec[l].r0, r1 = rec[l].r1;
+            const float w = x_weight(r0, r1.x, r1.y, C.grid, E, l, ix, iy);
+            if (w != 0.0f) visit(l, w);
+        }
+    }
+}
+
+// Back-projection table, pass 1: warp (tile t = blockIdx.x, view group g =
+// warp index of G): each lane's pair count and the warp's slot rows (the largest).
+__global__ void k_fp_bp_count(GeomC C, ExcTable E, const RayRec* rec, const ViewF* views, int* cnt,
+                              uint32_t* warp_rows) {
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, G = blockDim.x >> 5, t = blockIdx.x;
+    int ix, iy;
+    fp_tile_pixel(C.grid.n, t, lane, ix, iy);
+    int n = 0;
+    if (ix < C.grid.n && iy < C.grid.n) {
+        int v0, v1;
+        group_views(0, C.n_views, g, G, v0, v1);
+        pixel_pairs(C, E, rec, views, ix, iy, v0, v1, [&](int, float) { ++n; });
+    }
+    const int wi = t * G + g;
+    cnt[(size_t)wi * 32 + lane] = n;
+    n = __reduce_max_sync(0xffffffffu, n);
+    if (lane == 0) warp_rows[wi] = (uint32_t)n;
+}
+
+// Back-projection table, pass 2: lane r of warp wi writes its j-th pair (ray,
+// weight) at slot row bp_row[wi] + j.
+__global__ void k_fp_bp_fill(GeomC C, ExcTable E, const RayRec* rec, const ViewF* views,
+                             const uint32_t* __restrict__ bp_row, int2* pairs) {
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, G = blockDim.x >> 5, t = blockIdx.x;
+    int ix, iy;
+    fp_tile_pixel(C.grid.n, t, lane, ix, iy);
+    if (ix >= C.grid.n || iy >= C.grid.n) return;
+    int v0, v1;
+    group_views(0, C.n_views, g, G, v0, v1);
+    const size_t row = bp_row[t * G + g];
+    int j = 0;
+    pixel_pairs(C, E, rec, views, ix, iy, v0, v1, [&](int l, float w) {
+        pairs[(row + j) * 32 + lane] = make_int2(l, __float_as_int(w));
+        ++j;
+    });
+}
+
+// a1 from the forward table: the same line sums as proj_ray, in the same order,
+// with four pairs (and their gathers of xbar) in flight per step.
+__global__ void __launch_bounds__(kFwdThreads, 8) k_fp_proj(GeomC C, FpTables T, SolveD D, int v0, int v1) {
+    const int bx = centre_out(blockIdx.y, gridDim.y);
+    const int l = ray_in_views(C, bx, blockIdx.x, kFwdThreads / 32, v0, v1);
+    if (l < 0) return;
+    const int v = l / C.n_bins, lane = threadIdx.x & 31;
+    const int2* p = T.fwd_pairs + (size_t)T.fwd_row[v * ((C.n_bins + 31) >> 5) + bx] * 32 + lane;
+    const int n = __ldg(T.fwd_cnt + l);
+    LineSum acc;
+    int j = 0;
+    for (; j + 3 < n; j += 4) {
+        int2 a[4];
+        float4 x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = __ldg(p + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = __ldg(D.xbar + a[u].x);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc.add(__int_as_float(a[u].y), x[u]);
+        p += 128;
+    }
+    for (; j < n; ++j, p += 32) {
+        const int2 a = __ldg(p);
+        acc.add(__int_as_float(a.y), __ldg(D.xbar + a.x));
+    }
+    const float4 gs = acc.sum();
+    D.g[l] = make_float4(gs.x, gs.y, gs.z, 0.f);
+}
+
+// a6 (+ a7) from the back-projection table: warp (tile, view group) streams its
+// lanes' pair lists (the order of bp_pixel_sum) with four pairs and their ray
+// gathers in flight per step; the view groups are combined as in k_mocca_bp.
+// With a view range [V0, V1) other than all views (PARTIAL, one GPU's share of
+// a split solve) the pairs of other views are skipped and the summed channels
+// go to chan ([9][P]).
+template <bool PARTIAL>
+__global__ void __launch_bounds__(kFpBpMaxThreads, 4) k_fp_bp(GeomC C, FpTables T, const RayRec* rec, StepParams P,
+                                                              SolveD D, int V0, int V1, float* chan) {
+    __shared__ float red[7 * 9 * 32];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, G = blockDim.x >> 5;
+    const int t = blockIdx.x, wi = t * G + g, nb = C.n_bins;
+    int ix, iy;
+    fp_tile_pixel(C.grid.n, t, lane, ix, iy);
+    const bool valid = ix < C.grid.n && iy < C.grid.n;
+    const RayStep* steps = ray_steps(rec, C.n_views * nb);
+    const int2* p = T.bp_pairs + (size_t)__ldg(T.bp_row + wi) * 32 + lane;
+    const int n = __ldg(T.bp_cnt + (size_t)wi * 32 + lane);
+    const int l_lo = V0 * nb, l_hi = V1 * nb;   // the rays of the views [V0, V1)
+    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int j = 0;
+    for (; j + 3 < n; j += 4) {
+        int2 a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = __ldg(p + 32 * u);
+        float4 r1[4];
+        RecHalf st[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            r1[u] = __ldg(&rec[a[u].x].r1);
+            st[u] = ldg_half(&steps[a[u].x].s0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (!PARTIAL || (a[u].x >= l_lo && a[u].x < l_hi))
+                bp_accumulate(acc, __int_as_float(a[u].y), r1[u], st[u].a, st[u].b);
+        p += 128;
+    }
+    for (; j < n; ++j, p += 32) {
+        const int2 a = __ldg(p);
+        if (PARTIAL && (a.x < l_lo || a.x >= l_hi)) continue;
+        const float4 r1 = __ldg(&rec[a.x].r1);
+        const RecHalf st = ldg_half(&steps[a.x].s0);
+        bp_accumulate(acc, __int_as_float(a.y), r1, st.a, st.b);
+    }
+    if (PARTIAL)
+        bp_partial_out(C.grid.n * C.grid.n, iy * C.grid.n + ix, valid, lane, 32, g, G, red, acc, chan);
+    else
+        bp_finish(C, P, D, ix, iy, valid, lane, 32, g, G, red, acc);
 }
 
 constexpr int kReduceThreads = 1024;
@@ -1089,21 +1364,24 @@ cudaError_t launch_counts(const GeomC& C, const ExcTable& E, const RayRec* rec, 
 }
 
 cudaError_t launch_mocca_proj(const GeomC& C, const ExcTable& E, const RayRec* rec, const SolveD& D,
-                              cudaStream_t st) {
-    const dim3 fg = fwd_grid(C.n_bins, C.n_views);
-    k_mocca_proj<<<dim3(fg.y, fg.x), kFwdThreads, 0, st>>>(C, E, rec, D);
+                              cudaStream_t st, int v0, int v1, const FpTables* T) {
+    if (v1 < 0) v1 = C.n_views;
+    const dim3 fg = fwd_grid(C.n_bins, v1 - v0);
+    if (T) k_fp_proj<<<dim3(fg.y, fg.x), kFwdThreads, 0, st>>>(C, *T, D, v0, v1);
+    else k_mocca_proj<<<dim3(fg.y, fg.x), kFwdThreads, 0, st>>>(C, E, rec, D, v0, v1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mocca_ray(const GeomC& C, RayRec* rec, const SpecD& S, const StepParams& P, const SolveD& D,
-                             cudaStream_t st) {
-    k_mocca_ray<false><<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, rec, S, P, D);
+                             cudaStream_t st, int v0, int v1) {
+    if (v1 < 0) v1 = C.n_views;
+    k_mocca_ray<false><<<fwd_grid(C.n_bins, v1 - v0), kFwdThreads, 0, st>>>(C, rec, S, P, D, v0, v1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mocca_ray_keep(const GeomC& C, RayRec* rec, const SpecD& S, const StepParams& P,
                                   const SolveD& D, cudaStream_t st) {
-    k_mocca_ray<true><<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, rec, S, P, D);
+    k_mocca_ray<true><<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, rec, S, P, D, 0, C.n_views);
     return cudaGetLastError();
 }
 
@@ -1113,11 +1391,59 @@ cudaError_t launch_mocca_ray_inner(const GeomC& C, RayRec* rec, const SolveD& D,
 }
 
 cudaError_t launch_mocca_bp(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
-                            const StepParams& P, const SolveD& D, cudaStream_t st) {
+                            const StepParams& P, const SolveD& D, cudaStream_t st, const FpTables* T) {
     const int G = bp_view_groups(C.grid.n * C.grid.n, C.n_views);
+    if (T) {
+        k_fp_bp<false><<<fp_tiles(C.grid.n), 32 * T->bp_groups, 0, st>>>(C, *T, rec, P, D, 0, C.n_views, nullptr);
+        return cudaGetLastError();
+    }
     dim3 grid(blocks(C.grid.n, kBpPixX), blocks(C.grid.n, kBpPixY)), blk(kBpPixX, kBpPixY, G);
     const size_t smem = sizeof(float) * (size_t)(G - 1) * 9 * kBpPix;
-    k_mocca_bp<<<grid, blk, smem, st>>>(C, E, rec, views, P, D);
+    k_mocca_bp<false><<<grid, blk, smem, st>>>(C, E, rec, views, P, D, 0, C.n_views, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mocca_bp_partial(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
+                                    const StepParams& P, const SolveD& D, int v0, int v1, float* chan,
+                                    cudaStream_t st, const FpTables* T) {
+    if (T) {
+        k_fp_bp<true><<<fp_tiles(C.grid.n), 32 * T->bp_groups, 0, st>>>(C, *T, rec, P, D, v0, v1, chan);
+        return cudaGetLastError();
+    }
+    const int G = bp_view_groups(C.grid.n * C.grid.n, v1 - v0);
+    dim3 grid(blocks(C.grid.n, kBpPixX), blocks(C.grid.n, kBpPixY)), blk(kBpPixX, kBpPixY, G);
+    const size_t smem = sizeof(float) * (size_t)(G - 1) * 9 * kBpPix;
+    k_mocca_bp<true><<<grid, blk, smem, st>>>(C, E, rec, views, P, D, v0, v1, chan);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp_fwd_count(const GeomC& C, const ExcTable& E, const RayRec* rec, int* cnt,
+                                uint32_t* warp_rows, cudaStream_t st) {
+    k_fp_fwd_count<<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, E, rec, cnt, warp_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp_fwd_fill(const GeomC& C, const ExcTable& E, const RayRec* rec, const uint32_t* fwd_row,
+                               int2* pairs, cudaStream_t st) {
+    k_fp_fwd_fill<<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, E, rec, fwd_row, pairs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp_bp_count(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views, int G,
+                               int* cnt, uint32_t* warp_rows, cudaStream_t st) {
+    k_fp_bp_count<<<fp_tiles(C.grid.n), 32 * G, 0, st>>>(C, E, rec, views, cnt, warp_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp_bp_fill(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views, int G,
+                              const uint32_t* bp_row, int2* pairs, cudaStream_t st) {
+    k_fp_bp_fill<<<fp_tiles(C.grid.n), 32 * G, 0, st>>>(C, E, rec, views, bp_row, pairs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mocca_apply(const GeomC& C, const StepParams& P, const SolveD& D, const float* chan,
+                               cudaStream_t st) {
+    k_mocca_apply<<<blocks(C.grid.n * C.grid.n, 128), 128, 0, st>>>(C, P, D, chan);
     return cudaGetLastError();
 }
 

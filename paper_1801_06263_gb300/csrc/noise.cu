@@ -98,7 +98,12 @@ __global__ void k_poisson_noise(const float* __restrict__ chat, int n, uint32_t 
 extern "C" osscir_status osscir_poisson_noise(const float* chat, int n, uint64_t seed, float* c, void* stream) {
     if (n < 0 || (n > 0 && (!chat || !c))) return OSSCIR_E_INVALID;
     if (n == 0) return OSSCIR_OK;
-    const int threads = 256, blocks = (n + threads - 1) / threads < 152 * 64 ? (n + threads - 1) / threads : 152 * 64;
+    // a grid-stride loop over at most 64 blocks per SM of the current device
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return OSSCIR_E_CUDA;
+    const int threads = 256, need = (n + threads - 1) / threads, blocks = need < sms * 64 ? need : sms * 64;
     k_poisson_noise<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
         chat, n, (uint32_t)seed, (uint32_t)(seed >> 32), c);
     return cudaGetLastError() == cudaSuccess ? OSSCIR_OK : OSSCIR_E_CUDA;

@@ -26,7 +26,13 @@ struct osscir_ctx {
     // spectral tables
     float4* s4 = nullptr;
     float4* N4 = nullptr;
-    float* mu = nullptr;
+    float* mu = nullptr;      // [3][nE] the curves the iteration uses (mu-PC: the transformed ones)
+    float* mu_in = nullptr;   // [3][nE] the caller's curves, kept apart only for mu-PC (else null)
+    // mu-PC (spc = 2): the iteration runs in the basis f' = M^-1 f with M = (mu mu^T)^(-1/2)
+    // (symmetric); maps leave the library as f = M f'.  xo: [P] staging for the maps.
+    int basis = 0;
+    double Mb[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    float4* xo = nullptr;
     // solver state
     float4* g = nullptr;
     float4* c = nullptr;
@@ -35,6 +41,8 @@ struct osscir_ctx {
     float4* xbar = nullptr;
     double* dtpl_part = nullptr;
     double* dtpl_out = nullptr;   // [0]: at x (on request), [1]: at the last expansion point
+    int* bad_counts = nullptr;    // [0]: set by the check of the counts osscir_set_counts loads (0: valid);
+                                  // [1]: set by a kernel whose bounded wait for its own copies ran out
     int n_part = 0;
     int exp_model = 0;   // counts model: 0 softexp (Eq. finalModel), 1 exp (Eq. fullModel)
     int iter = 0;
@@ -42,6 +50,21 @@ struct osscir_ctx {
     // (0: the next iteration is an outer one) and the models [L][kModelStride]
     int inner = 1, phase = 0;
     float4* model = nullptr;
+    // footprint tables (built before the first plain iteration; see FpTables)
+    int fp_state = 0;   // 0 not built yet, 1 built, -1 not used (no room on the device)
+    uint32_t* fwd_row = nullptr;
+    int* fwd_cnt = nullptr;
+    int2* fwd_pairs = nullptr;
+    uint32_t* bp_row = nullptr;
+    int* bp_cnt = nullptr;
+    int2* bp_pairs = nullptr;
+    int bp_groups = 1;
+    size_t fp_bytes = 0;
+    osscir::FpTables fp() const {
+        return osscir::FpTables{fwd_row, fwd_cnt, fwd_pairs, bp_row, bp_cnt, bp_pairs, bp_groups};
+    }
+    const osscir::FpTables* fp_or_null() const { return fp_state == 1 ? &fp_tab : nullptr; }
+    osscir::FpTables fp_tab{};
     // per-iteration graph
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
@@ -54,7 +77,11 @@ struct osscir_ctx {
 
     osscir::ExcTable exc() const { return osscir::ExcTable{exc_off, exc_ent}; }
     osscir::SpecD spec() const { return osscir::SpecD{nE, s4, N4, mu, exp_model}; }
-    osscir::SolveD solve() const { return osscir::SolveD{g, c, y, x, xbar, chord, dtpl_part, model}; }
+    // the spectral tables with the caller's attenuation curves (for maps in the caller's basis)
+    osscir::SpecD spec_in() const { return osscir::SpecD{nE, s4, N4, mu_in ? mu_in : mu, exp_model}; }
+    osscir::SolveD solve() const {
+        return osscir::SolveD{g, c, y, x, xbar, chord, dtpl_part, model, bad_counts ? bad_counts + 1 : nullptr};
+    }
 };
 
 namespace osscir {
@@ -66,6 +93,11 @@ osscir_status ctx_create(const osscir_geometry* geom, const osscir_spectra* spec
 void ctx_destroy(osscir_ctx* h);
 osscir_status ctx_validate(const osscir_geometry* geom, const osscir_spectra* spectra, const float* mu,
                            const osscir_params* params);
+// Maps x (the iteration's basis, device [P]) to the caller's basis in out (device [P]);
+// a plain copy unless the context runs mu-PC.
+cudaError_t ctx_maps_out(const osscir_ctx* h, const float4* x, float4* out, cudaStream_t st);
+// The same on host maps [P][4] in place (FP64 arithmetic).
+void ctx_maps_out_host(const osscir_ctx* h, float* maps);
 // Capture the per-iteration graph(s) once.
 osscir_status ctx_ensure_graph(osscir_ctx* h);
 

@@ -130,13 +130,18 @@ __device__ __forceinline__ float member_weight(float w, float txl, float txh, fl
     return exc_lookup(E, l, key);   // also reached by NaN (axis-parallel rays)
 }
 
-// X_{l,k}: the weight both projectors use.
+// X_{l,k}: the weight both projectors use.  The entry and exit parameters of
+// each axis are the min and max of its two plane parameters: t is monotone in
+// the plane position for a finite reciprocal direction, so this is the
+// direction-sign choice of chord_from_planes; only an axis-parallel ray
+// (reciprocal infinite, possibly a NaN parameter) can differ, and such a ray
+// has infinite error bounds, so its weight comes from the FP64 table either way.
 __device__ __forceinline__ float x_weight(const float4& r0, float ex, float ey, const GridF& G,
                                           const ExcTable& E, int l, int ix, int iy) {
     const float tx0 = t_plane(grid_plane(G, ix), r0.x, r0.z), tx1 = t_plane(grid_plane(G, ix + 1), r0.x, r0.z);
     const float ty0 = t_plane(grid_plane(G, iy), r0.y, r0.w), ty1 = t_plane(grid_plane(G, iy + 1), r0.y, r0.w);
-    const float txl = r0.z >= 0.0f ? tx0 : tx1, txh = r0.z >= 0.0f ? tx1 : tx0;
-    const float tyl = r0.w >= 0.0f ? ty0 : ty1, tyh = r0.w >= 0.0f ? ty1 : ty0;
+    const float txl = fminf(tx0, tx1), txh = fmaxf(tx0, tx1);
+    const float tyl = fminf(ty0, ty1), tyh = fmaxf(ty0, ty1);
     const float w = __fsub_rn(fminf(txh, tyh), fmaxf(txl, tyl));
     return member_weight(w, txl, txh, tyl, tyh, ex, ey, E, l, exc_key(ray_rows(r0), G.n, ix, iy));
 }

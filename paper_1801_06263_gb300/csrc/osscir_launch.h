@@ -48,6 +48,7 @@ struct SolveD {
     const float* chord; // [L] (X 1)_l
     double* dtpl_part;  // [fwd blocks]
     float4* model;      // [L][kModelStride] local models kept for nested MOCCA, or null
+    int* err;           // set to 1 by a kernel whose bounded wait for its own copies ran out (else untouched)
 };
 
 // Per-ray local model kept by an outer iteration of nested MOCCA (float4 slots):
@@ -61,6 +62,32 @@ constexpr int kBpTileX = 16, kBpTileY = 8;            // plain back-projection t
 constexpr int kBpPixX = 2, kBpPixY = 32;              // MOCCA back-projection pixel tile (2 x 32: measured fastest)
 constexpr int kBpPix = kBpPixX * kBpPixY;
 constexpr int kBpMaxThreads = 512;                    // kBpPix x up to 8 view groups
+// Footprint tables: the back-projection table's pixel tile (one pixel per lane
+// of a warp) and the table-driven back-projection's block (one warp per view group).
+constexpr int kFpTX = 8, kFpTY = 4;
+constexpr int kFpBpMaxThreads = 256;
+inline int fp_tiles(int n) { return ((n + kFpTX - 1) / kFpTX) * ((n + kFpTY - 1) / kFpTY); }
+
+// Footprint tables of one geometry: the pairs (l, k) of X with their weights,
+// in the order each projector visits them.  Both are lists per warp with the
+// lanes interleaved: lane r's j-th entry of warp w is at (row[w] + j) 32 + r,
+// row[w] the prefix sum of the warps' largest counts, cnt the lanes' counts.
+//   Forward (ray-major): warp w = (view v, 32-bin group bx), w = v nbg + bx with
+//   nbg = ceil(n_bins / 32), lane r = bin 32 bx + r; entries (pixel k, weight
+//   bits) in the visiting order of ray_weights.
+//   Back-projection (pixel-major): warp w = t G + g (tile t of kFpTX x kFpTY
+//   pixels, lane r = pixel (r mod kFpTX, r div kFpTX) of the tile; view group g
+//   of bp_groups, the split of k_mocca_bp); entries (ray l, weight bits) of the
+//   group's views in the order of bp_pixel_sum.
+struct FpTables {
+    const uint32_t* fwd_row;   // [n_views nbg + 1]
+    const int* fwd_cnt;        // [L]
+    const int2* fwd_pairs;
+    const uint32_t* bp_row;    // [fp_tiles(n) bp_groups + 1]
+    const int* bp_cnt;         // [fp_tiles(n) bp_groups 32]
+    const int2* bp_pairs;
+    int bp_groups;
+};
 
 // View groups per pixel for the MOCCA back-projection: enough threads to fill
 // the GPU several times over, at most 8, and at least one view per group.
@@ -86,18 +113,38 @@ cudaError_t launch_backproject4(const GeomC& C, const ExcTable& E, const RayRec*
                                 const float4* rf, float4* img, cudaStream_t st);
 cudaError_t launch_counts(const GeomC& C, const ExcTable& E, const RayRec* rec, const SpecD& S, const float4* f,
                           float4* chat, const float4* c, double* dtpl_part, cudaStream_t st);
+// The ray-driven kernels over the views [v0, v1) (v1 < 0: all views); with
+// footprint tables T the projections stream them (same results bit for bit).
 cudaError_t launch_mocca_proj(const GeomC& C, const ExcTable& E, const RayRec* rec, const SolveD& D,
-                              cudaStream_t st);
+                              cudaStream_t st, int v0 = 0, int v1 = -1, const FpTables* T = nullptr);
 cudaError_t launch_mocca_ray(const GeomC& C, RayRec* rec, const SpecD& S, const StepParams& P, const SolveD& D,
-                             cudaStream_t st);
+                             cudaStream_t st, int v0 = 0, int v1 = -1);
 // Outer iteration of nested MOCCA: the per-ray step that also keeps each ray's model in D.model.
 cudaError_t launch_mocca_ray_keep(const GeomC& C, RayRec* rec, const SpecD& S, const StepParams& P,
                                   const SolveD& D, cudaStream_t st);
 // Inner iteration of nested MOCCA: the dual step on the kept models.
 cudaError_t launch_mocca_ray_inner(const GeomC& C, RayRec* rec, const SolveD& D, cudaStream_t st);
 cudaError_t launch_mocca_bp(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
-                            const StepParams& P, const SolveD& D, cudaStream_t st);
+                            const StepParams& P, const SolveD& D, cudaStream_t st, const FpTables* T = nullptr);
 cudaError_t launch_dtpl_reduce(const double* part, int n, double* out, cudaStream_t st);
+// View split of one iteration: the back-projection of the views [v0, v1) into
+// the nine per-pixel channels chan [9][P] (no primal step), and the primal step
+// from channels summed over all view ranges.
+cudaError_t launch_mocca_bp_partial(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
+                                    const StepParams& P, const SolveD& D, int v0, int v1, float* chan,
+                                    cudaStream_t st, const FpTables* T = nullptr);
+// Footprint table construction: counts (forward: per ray, and per warp the slot
+// rows; back-projection: slot rows per entry), then the fills from the row offsets.
+cudaError_t launch_fp_fwd_count(const GeomC& C, const ExcTable& E, const RayRec* rec, int* cnt,
+                                uint32_t* warp_rows, cudaStream_t st);
+cudaError_t launch_fp_fwd_fill(const GeomC& C, const ExcTable& E, const RayRec* rec, const uint32_t* fwd_row,
+                               int2* pairs, cudaStream_t st);
+cudaError_t launch_fp_bp_count(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views, int G,
+                               int* cnt, uint32_t* warp_rows, cudaStream_t st);
+cudaError_t launch_fp_bp_fill(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views, int G,
+                              const uint32_t* bp_row, int2* pairs, cudaStream_t st);
+cudaError_t launch_mocca_apply(const GeomC& C, const StepParams& P, const SolveD& D, const float* chan,
+                               cudaStream_t st);
 
 // Ray-driven kernels: blocks of 32 bins x (kFwdThreads / 32) views.
 inline dim3 fwd_grid(int n_bins, int n_views) {

@@ -104,8 +104,9 @@ struct Slot {
 size_t estimate_bytes(const Config& c) {
     const size_t L = (size_t)c.geom.n_views * c.geom.n_bins, P = (size_t)c.geom.n * c.geom.n;
     const size_t per_ray = 64 + 32 + 4 + 4 + 16 + 16 + 8 * 4 / 128 + 2;   // records, FP64 rays, chord, offsets, c, y, partials
+    const size_t mu_pc = c.params.spc == 2 ? P * 16 + 12 * c.nE : 0;   // the caller's curves and a maps buffer
     return L * per_ray + P * 32 + (size_t)c.nE * c.geom.n_bins * 16 + c.geom.n_bins * 16 + 12 * c.nE +
-           c.geom.n_views * 8 + (L / 8) * 8 + (1 << 16);
+           c.geom.n_views * 8 + (L / 8) * 8 + mu_pc + (1 << 16);
 }
 
 void release_slot(Slot* s) {
@@ -125,7 +126,20 @@ struct osscir_server {
     size_t budget = 0;
     int max_slots = 1;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_done;
+    // Wake-ups of the worker: bumped by submissions, by destroy and by a host
+    // callback that each stream runs when a round or a request's results are
+    // done on the GPU, so an idle worker sleeps instead of polling its events.
+    std::mutex mu_sig;
+    std::condition_variable cv_sig;
+    uint64_t sig = 0;
+    void signal() {
+        {
+            std::lock_guard<std::mutex> g(mu_sig);
+            ++sig;
+        }
+        cv_sig.notify_all();
+    }
     std::deque<Ticket*> queue;
     std::unordered_map<uint64_t, Ticket*> tickets;
     std::list<Slot*> slots;
@@ -192,6 +206,9 @@ Slot* osscir_server::acquire(Ticket* t) {
 }
 
 // Copy the counts in and reset the state (the iterations follow in rounds).
+// Host callback run in stream order after a round or a result copy: wake the worker.
+void CUDART_CB gpu_progress(void* p) { static_cast<osscir_server*>(p)->signal(); }
+
 bool osscir_server::begin(Slot* s) {
     Ticket* t = s->running;
     osscir_ctx* h = s->ctx;
@@ -216,7 +233,8 @@ bool osscir_server::enqueue_tail(Slot* s) {
     const bool ok =
         cudaMemcpyAsync(s->h_maps, h->x, sizeof(float4) * h->P, cudaMemcpyDeviceToHost, stream) == cudaSuccess &&
         cudaMemcpyAsync(s->h_dtpl, h->dtpl_out + 1, sizeof(double), cudaMemcpyDeviceToHost, stream) == cudaSuccess &&
-        cudaEventRecord(s->ev1, stream) == cudaSuccess;
+        cudaEventRecord(s->ev1, stream) == cudaSuccess &&
+        cudaLaunchHostFunc(stream, gpu_progress, this) == cudaSuccess;
     s->tail = true;
     return ok;
 }
@@ -250,7 +268,8 @@ bool osscir_server::enqueue_round(int g) {
     } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
         ev = nullptr;
     }
-    if (st == OSSCIR_OK && ev && cudaEventRecord(ev, G.stream) == cudaSuccess) {
+    if (st == OSSCIR_OK && ev && cudaEventRecord(ev, G.stream) == cudaSuccess &&
+        cudaLaunchHostFunc(G.stream, gpu_progress, this) == cudaSuccess) {
         G.rounds.push_back(ev);
     } else {
         if (ev) spare.push_back(ev);
@@ -283,6 +302,7 @@ void osscir_server::finish(Slot* s) {
     }
     s->ctx->iter = t->n_iters;
     t->maps.assign(s->h_maps, s->h_maps + (size_t)h->P * 4);
+    osscir::ctx_maps_out_host(h, t->maps.data());
     t->dtpl = *s->h_dtpl;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, s->ev0, s->ev1);
@@ -310,6 +330,11 @@ void osscir_server::run() {
     std::vector<Slot*> started;
     while (true) {
         started.clear();
+        uint64_t seen;
+        {
+            std::lock_guard<std::mutex> g(mu_sig);
+            seen = sig;   // any wake-up after this point ends the idle wait below at once
+        }
         {
             std::unique_lock<std::mutex> lock(mu);
             if (stop && running == 0) break;
@@ -374,8 +399,13 @@ void osscir_server::run() {
             acted = true;
         }
         if (!acted) {
-            if (running > 0) cv_work.wait_for(lock, std::chrono::microseconds(20));
-            else if (!stop && queue.empty()) cv_work.wait(lock);
+            // sleep until a submission, destroy, or a stream's callback; the 50 ms limit
+            // only bounds the cost of a callback that could not be enqueued
+            const bool busy = running > 0, idle = !stop && queue.empty();
+            lock.unlock();
+            std::unique_lock<std::mutex> ls(mu_sig);
+            if (busy) cv_sig.wait_for(ls, std::chrono::milliseconds(50), [&] { return sig != seen; });
+            else if (idle) cv_sig.wait(ls, [&] { return sig != seen; });
         }
     }
     for (Group& g : groups) {
@@ -426,7 +456,7 @@ osscir_status osscir_server_destroy(osscir_server_t s) {
         }
         s->queue.clear();
     }
-    s->cv_work.notify_all();
+    s->signal();
     if (s->worker.joinable()) s->worker.join();
     for (Slot* sl : s->slots) release_slot(sl);
     for (auto& kv : s->tickets) delete kv.second;
@@ -480,7 +510,7 @@ osscir_status osscir_submit(osscir_server_t s, const osscir_request* req, uint64
         s->queue.push_back(t);
         *ticket = t->id;
     }
-    s->cv_work.notify_all();
+    s->signal();
     return OSSCIR_OK;
 }
 

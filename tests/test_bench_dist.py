@@ -22,7 +22,7 @@ def _worker(rank, world, port, out):
 
 def test_whole_job_rate_uses_slowest_rank():
     port = 29500 + os.getpid() % 1000
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
         for rank in range(2):

@@ -39,3 +39,16 @@ def test_clock_summary_flags_throttling(tmp_path):
     s = c.summary()
     assert s["sm_max_mhz"] == 2070.0 and s["sm_mhz"] == 2070.0 and s["samples"] == 3
     assert set(s["reasons"]) == {"sw_power_cap", "hw_slowdown"}
+
+
+def test_roofs_come_from_the_device_and_the_sampled_clock(monkeypatch):
+    import types
+
+    import torch
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev: types.SimpleNamespace(multi_processor_count=76))
+    r = bench.device_roofs(0, 1500.0)
+    assert r["sms"] == 76 and r["sm_mhz"] == 1500.0
+    assert abs(r["fp32_tflops"] - 76 * 128 * 2 * 1.5e9 / 1e12) < 1e-9
+    assert abs(r["issue_per_s"] - 76 * 4 * 1.5e9) < 1.0
+    assert abs(r["l1_tbps"] - 76 * 128 * 1.5e9 / 1e12) < 1e-9
+    assert "76 SMs" in r["source"] and "1500 MHz" in r["source"]

@@ -115,3 +115,77 @@ def test_poisson_noise_rejects_invalid_arguments(lib):
     assert lib.osscir_poisson_noise(None, -1, 0, None, None) == _lib.OSSCIR_E_INVALID
     assert lib.osscir_poisson_noise(None, 4, 0, None, None) == _lib.OSSCIR_E_INVALID
     assert lib.osscir_poisson_noise(None, 0, 0, None, None) == _lib.OSSCIR_OK
+
+
+# --------------------------------------------------------------------------- boundary checks on a GPU
+
+def _small_context(lam):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g = inputs.make_geometry(16, 0.5, 24, 20)
+    sp = inputs.make_spectra(g.n_bins, 2e4)
+    return torch, g, sp, _lib.osscir_create(g, sp.s, sp.N, sp.mu, lam)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("bad", [-1.0, float("nan"), float("inf")])
+def test_reconstruct_rejects_invalid_host_counts(bad):
+    torch, g, sp, h = _small_context(1e-6)
+    try:
+        c = torch.full((g.n_rays, 4), 100.0, dtype=torch.float32)
+        c[g.n_rays // 2, 1] = bad
+        out = torch.zeros((g.n_pixels, 4), dtype=torch.float32)
+        with pytest.raises(_lib.OsscirError) as e:
+            _lib.osscir_reconstruct(h, c, 5, out)
+        assert e.value.status == _lib.OSSCIR_E_INVALID
+        assert torch.all(out == 0)                     # nothing was run or copied back
+    finally:
+        _lib.osscir_destroy(h)
+
+
+@pytest.mark.gpu
+def test_set_counts_check_is_reported_by_dtpl():
+    torch, g, sp, h = _small_context(1e-6)
+    try:
+        c = torch.full((g.n_rays, 4), 100.0, dtype=torch.float32, device="cuda")
+        c[3, 2] = -5.0
+        _lib.osscir_set_counts(h, c)
+        with pytest.raises(_lib.OsscirError) as e:
+            _lib.osscir_dtpl(h, 0)
+        assert e.value.status == _lib.OSSCIR_E_INVALID
+        c[3, 2] = 5.0                                   # valid counts clear the report
+        _lib.osscir_set_counts(h, c)
+        assert np.isfinite(_lib.osscir_dtpl(h, 0))
+    finally:
+        _lib.osscir_destroy(h)
+
+
+@pytest.mark.gpu
+def test_diverged_reconstruction_returns_diverged():
+    # a step ratio far above the stable range (the 64 x 64 sweep diverges from 3e-7 on)
+    torch, g, sp, h = _small_context(1.0)
+    try:
+        from paper_1801_06263_gb300 import Reconstructor  # noqa: F401  (loads the library)
+        f = np.tile([[1.0, 0.05, 0.005]], (g.n_pixels, 1))
+        f4 = torch.zeros((g.n_pixels, 4), dtype=torch.float32, device="cuda")
+        f4[:, :3] = torch.tensor(f, dtype=torch.float32, device="cuda")
+        chat = torch.zeros((g.n_rays, 4), dtype=torch.float32, device="cuda")
+        _lib.osscir_simulate(h, f4, chat)
+        c = chat.cpu().contiguous()
+        out = torch.zeros((g.n_pixels, 4), dtype=torch.float32)
+        with pytest.raises(_lib.OsscirError) as e:
+            _lib.osscir_reconstruct(h, c, 200, out)
+        assert e.value.status == _lib.OSSCIR_E_DIVERGED
+    finally:
+        _lib.osscir_destroy(h)
+
+
+def test_static_dtpl_wrapper_rejects_mismatched_tensors():
+    torch = pytest.importorskip("torch")
+    a = torch.zeros((8, 4), dtype=torch.float32)
+    out = torch.zeros(1, dtype=torch.float64)
+    with pytest.raises(ValueError):            # host tensors are not device buffers
+        _lib.osscir_dtpl_counts_static(a, a, out)
+    with pytest.raises(ValueError):            # [L, 3] is not the [L, 4] counts layout
+        _lib.osscir_dtpl_counts_static(a[:, :3], a[:, :3], out)

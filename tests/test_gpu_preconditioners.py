@@ -1,7 +1,8 @@
 """The comparison step-preconditioners of Sec. 2 and 3 on the GPU.
 
-  * the diagonal SPC of Pock and Chambolle and mu-PC (orthonormal material
-    basis + diagonal SPC) match the FP64 oracle's iterates;
+  * the diagonal SPC of Pock and Chambolle and mu-PC (the library's own change
+    to an orthonormal material basis, spc = 2, then the diagonal SPC) match the
+    FP64 oracle's iterates, mu-PC in the caller's basis;
   * with lambda tuned for each method on noiseless data (Sec. 3), the
     m-block-diagonal SPC reaches a lower D_TPL than the diagonal SPC in the
     original basis (the paper reports divergence for all tested lambda).  The
@@ -11,7 +12,7 @@
 import numpy as np
 import pytest
 
-from paper_1801_06263_gb300 import inputs, precond
+from paper_1801_06263_gb300 import inputs
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -32,9 +33,9 @@ def small(orc):
     return w, c
 
 
-def _run(w, c, lam, n_it, spc, mu=None, with_hist=False):
+def _run(w, c, lam, n_it, spc):
     from paper_1801_06263_gb300 import Reconstructor
-    R = Reconstructor(w.geom, w.spectra, lam, spc=spc, mu=mu)
+    R = Reconstructor(w.geom, w.spectra, lam, spc=spc)
     R.set_counts(torch.tensor(c, device="cuda"))
     R.step(n_it)
     x = R.maps().cpu().double().numpy()[:, :3]
@@ -50,31 +51,51 @@ def _run(w, c, lam, n_it, spc, mu=None, with_hist=False):
 @pytest.mark.parametrize("variant", ["diagonal", "mu_pc"])
 def test_comparison_preconditioners_match_oracle(orc, small, variant):
     w, c = small
-    mu = None
-    if variant == "mu_pc":
-        mu, M = precond.mu_pc(w.spectra.mu)
-        mu = mu.astype(np.float32).astype(np.float64)
     lam, n_it = (1e-7, 60) if variant == "diagonal" else (1e-4, 60)
-    x, _ = _run(w, c, lam, n_it, 1, mu)
-    st, _ = orc.mocca(w.geom, _sp32(w.spectra, mu), c.astype(np.float64), n_it, lam, spc="diagonal",
-                      mu=None if mu is None else mu)
+    x, _ = _run(w, c, lam, n_it, 1 if variant == "diagonal" else 2)
+    sp = _sp32(w.spectra)
+    if variant == "mu_pc":   # the oracle iterates in the basis of orthonormal curves, mapped back
+        mu_t, M = orc.mu_pc(sp.mu)
+        st, _ = orc.mocca(w.geom, sp, c.astype(np.float64), n_it, lam, spc="diagonal", mu=mu_t)
+        ref = orc.maps_from_basis(st.x, M)
+    else:
+        st, _ = orc.mocca(w.geom, sp, c.astype(np.float64), n_it, lam, spc="diagonal")
+        ref = st.x
     for m in range(3):
-        rel = np.linalg.norm(x[:, m] - st.x[:, m]) / np.linalg.norm(st.x[:, m])
+        rel = np.linalg.norm(x[:, m] - ref[:, m]) / np.linalg.norm(ref[:, m])
         assert rel < 1e-4, (variant, m, rel)
+
+
+def test_mu_pc_maps_leave_in_the_callers_basis(orc, small):
+    from paper_1801_06263_gb300 import Reconstructor, _lib
+    w, c = small
+    R = Reconstructor(w.geom, w.spectra, 1e-4, spc=2)
+    R.set_counts(torch.tensor(c, device="cuda"))
+    R.step(10)
+    x_state = R.get_state()[0].cpu().double().numpy()[:, :3]     # the iteration's basis
+    maps = R.maps().cpu().double().numpy()[:, :3]                # the caller's basis
+    _, M = orc.mu_pc(_sp32(w.spectra).mu)
+    np.testing.assert_allclose(maps, orc.maps_from_basis(x_state, M), rtol=1e-5,
+                               atol=1e-6 * np.abs(maps).max())
+    out = torch.zeros((w.geom.n_pixels, 4), dtype=torch.float32).pin_memory()
+    _lib.osscir_reconstruct(R.handle, torch.tensor(c).contiguous(), 10, out)
+    assert torch.equal(out, R.maps().cpu())                       # the same maps end to end
+    # simulate takes maps in the caller's basis: the truth gives the noiseless counts
+    f4 = torch.zeros((w.geom.n_pixels, 4), dtype=torch.float32, device="cuda")
+    f4[:, :3] = torch.tensor(w.f_true, dtype=torch.float32, device="cuda")
+    np.testing.assert_allclose(R.simulate(f4).cpu().double().numpy(), c, rtol=1e-5)
+    R.close()
 
 
 def test_block_spc_beats_diagonal_and_report_mu_pc(small):
     w, c = small
-    mu_t, M = precond.mu_pc(w.spectra.mu)
     n_it = 1000
     grid = 10.0 ** np.arange(-11.0, 1.01, 0.5)
     best = {}
-    for name, spc, mu in [("block", 0, None), ("mu_pc", 1, mu_t), ("diagonal", 1, None)]:
+    for name, spc in [("block", 0), ("mu_pc", 2), ("diagonal", 1)]:
         rows = []
         for lam in grid:
-            x, d = _run(w, c, float(lam), n_it, spc, mu)
-            if mu is not None:
-                x = precond.maps_from_basis(x, M)
+            x, d = _run(w, c, float(lam), n_it, spc)
             gd = np.linalg.norm(x[:, 2] - w.f_true[:, 2]) / np.linalg.norm(w.f_true[:, 2])
             rows.append((d if np.isfinite(d) else np.inf, float(lam), gd))
         best[name] = min(rows)
