@@ -54,7 +54,7 @@ void free_ctx(osscir_ctx* h) {
     void* ptrs[] = {h->rec,     h->r64,    h->views,     h->chord,    h->exc_off,    h->exc_ent,  h->s4,
                     h->N4,      h->mu,     h->mu_in,     h->g,        h->c,          h->y,        h->x,
                     h->xbar,    h->xo,     h->dtpl_part, h->dtpl_out, h->bad_counts, h->model,    h->fwd_row,
-                    h->fwd_cnt, h->fwd_pairs, h->bp_row, h->bp_cnt,   h->bp_pairs};
+                    h->fwd_cnt, h->fwd_pairs, h->bp_span, h->bp_row,  h->bp_cnt,   h->bp_pairs, h->bp_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -327,15 +327,17 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
 }
 
 void free_tables(osscir_ctx* h) {
-    void* ptrs[] = {h->fwd_row, h->fwd_cnt, h->fwd_pairs, h->bp_row, h->bp_cnt, h->bp_pairs};
+    void* ptrs[] = {h->fwd_row, h->fwd_cnt, h->fwd_pairs, h->bp_span, h->bp_row, h->bp_cnt, h->bp_pairs, h->bp_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->fwd_row = nullptr;
     h->fwd_cnt = nullptr;
     h->fwd_pairs = nullptr;
+    h->bp_span = nullptr;
     h->bp_row = nullptr;
     h->bp_cnt = nullptr;
     h->bp_pairs = nullptr;
+    h->bp_part = nullptr;
     h->bytes -= h->fp_bytes;
     h->fp_bytes = 0;
 }
@@ -364,7 +366,6 @@ osscir_status build_tables(osscir_ctx* h) {
     const GeomC& C = h->gc;
     const size_t nbg = (C.n_bins + 31) / 32, n_fw = (size_t)C.n_views * nbg;
     const int G = bp_view_groups(h->P, C.n_views);
-    const size_t n_bw = (size_t)fp_tiles(C.grid.n) * G;
     size_t before = h->bytes;
     g_dalloc_bytes = &h->bytes;
     auto fail = [&](cudaError_t e) -> osscir_status {
@@ -394,17 +395,50 @@ osscir_status build_tables(osscir_ctx* h) {
     CKT(cudaMemcpyAsync(h->fwd_row, rows.data(), sizeof(uint32_t) * (n_fw + 1), cudaMemcpyHostToDevice, st));
     CKT(dalloc(&h->fwd_pairs, (size_t)rows[n_fw] * 32));
     CKT(launch_fp_fwd_fill(C, h->exc(), h->rec, h->fwd_row, h->fwd_pairs, st));
-    // back-projection: per-lane counts and per-warp rows of each (tile, view group), then the pairs
-    CKT(dalloc(&h->bp_cnt, n_bw * 32));
-    CKT(dalloc(&h->bp_row, n_bw + 1));
-    CKT(launch_fp_bp_count(C, h->exc(), h->rec, h->views, G, h->bp_cnt, h->bp_row, st));
-    std::vector<uint32_t> brow(n_bw + 1, 0);
-    CKT(cudaMemcpyAsync(brow.data(), h->bp_row, sizeof(uint32_t) * n_bw, cudaMemcpyDeviceToHost, st));
+    // back-projection (blocked): per tile and view the union of candidate bins; the
+    // chunk size (views per staged chunk) so that two stage buffers fit in 48 KB;
+    // then per-pixel counts and per-warp rows of each (block, chunk), then the pairs
+    const int n_t = bt_tiles(C.grid.n), per = (C.n_views + G - 1) / G;
+    CKT(dalloc(&h->bp_span, (size_t)n_t * C.n_views));
+    CKT(launch_fpb_span(C, h->views, h->bp_span, st));
+    std::vector<uint32_t> span((size_t)n_t * C.n_views);
+    CKT(cudaMemcpyAsync(span.data(), h->bp_span, sizeof(uint32_t) * span.size(), cudaMemcpyDeviceToHost, st));
     CKT(cudaStreamSynchronize(st));
-    if (!prefix_rows(brow, n_bw)) return fail(cudaErrorMemoryAllocation);
-    CKT(cudaMemcpyAsync(h->bp_row, brow.data(), sizeof(uint32_t) * (n_bw + 1), cudaMemcpyHostToDevice, st));
-    CKT(dalloc(&h->bp_pairs, (size_t)brow[n_bw] * 32));
-    CKT(launch_fp_bp_fill(C, h->exc(), h->rec, h->views, G, h->bp_row, h->bp_pairs, st));
+    int chunk = 0, slots = 0;
+    for (int cand = kBTMaxChunk; cand >= 1 && !chunk; cand /= 2) {
+        int most = 0;
+        for (int t = 0; t < n_t; ++t)
+            for (int g = 0; g < G; ++g)
+                for (int u0 = std::min(C.n_views, g * per); u0 < std::min(C.n_views, (g + 1) * per); u0 += cand) {
+                    int sum = 0;
+                    for (int u = u0; u < std::min({C.n_views, (g + 1) * per, u0 + cand}); ++u)
+                        sum += (int)(span[(size_t)t * C.n_views + u] >> 16);
+                    most = std::max(most, sum);
+                }
+        if ((size_t)most * 6 * sizeof(float4) <= 48 * 1024) {
+            chunk = cand;
+            slots = most;
+        }
+    }
+    if (chunk > 0) {
+        const int nch = (per + chunk - 1) / chunk;
+        const size_t n_e = (size_t)n_t * G * nch;
+        CKT(dalloc(&h->bp_cnt, n_e * kBTThreads));
+        CKT(dalloc(&h->bp_row, n_e * (kBTThreads / 32) + 1));
+        CKT(launch_fpb_count(C, h->exc(), h->rec, h->views, G, chunk, nch, h->bp_cnt, h->bp_row, st));
+        const size_t n_w = n_e * (kBTThreads / 32);
+        std::vector<uint32_t> brow(n_w + 1, 0);
+        CKT(cudaMemcpyAsync(brow.data(), h->bp_row, sizeof(uint32_t) * n_w, cudaMemcpyDeviceToHost, st));
+        CKT(cudaStreamSynchronize(st));
+        if (!prefix_rows(brow, n_w)) return fail(cudaErrorMemoryAllocation);
+        CKT(cudaMemcpyAsync(h->bp_row, brow.data(), sizeof(uint32_t) * (n_w + 1), cudaMemcpyHostToDevice, st));
+        CKT(dalloc(&h->bp_pairs, (size_t)brow[n_w] * 32));
+        CKT(dalloc(&h->bp_part, (size_t)G * 9 * h->P));
+        CKT(launch_fpb_fill(C, h->exc(), h->rec, h->views, h->bp_span, G, chunk, nch, h->bp_row, h->bp_pairs, st));
+        h->bp_chunk = chunk;
+        h->bp_nch = nch;
+        h->bp_slots = slots;
+    }
     CKT(cudaStreamSynchronize(st));
 #undef CKT
     g_dalloc_bytes = &g_dalloc_bytes_sink;

@@ -1102,68 +1102,6 @@ __global__ void __launch_bounds__(kFwdThreads) k_fp_fwd_fill(GeomC C, ExcTable E
     });
 }
 
-// The pixel of lane `lane` in back-projection table tile t (kFpTX x kFpTY pixels).
-__device__ __forceinline__ void fp_tile_pixel(int n, int t, int lane, int& ix, int& iy) {
-    const int ntx = (n + kFpTX - 1) / kFpTX;
-    ix = (t % ntx) * kFpTX + lane % kFpTX;
-    iy = (t / ntx) * kFpTY + lane / kFpTX;
-}
-
-// The footprint pairs of pixel (ix, iy) in the views [v0, v1), in the order
-// bp_pixel_sum adds them (views ascending, candidate bins ascending, nonzero
-// weights only): visit(l, w).
-template <class Visit>
-__device__ __forceinline__ void pixel_pairs(const GeomC& C, const ExcTable& E, const RayRec* rec,
-                                            const ViewF* views, int ix, int iy, int v0, int v1, Visit&& visit) {
-    for (int v = v0; v < v1; ++v) {
-        int blo, bhi;
-        pixel_bin_range(C, views[v], ix, iy, blo, bhi);
-        for (int b = blo; b <= bhi; ++b) {
-            const int l = v * C.n_bins + b;
-            const float4 r0 = rec[l].r0, r1 = rec[l].r1;
-            const float w = x_weight(r0, r1.x, r1.y, C.grid, E, l, ix, iy);
-            if (w != 0.0f) visit(l, w);
-        }
-    }
-}
-
-// Back-projection table, pass 1: warp (tile t = blockIdx.x, view group g =
-// warp index of G): each lane's pair count and the warp's slot rows (the largest).
-__global__ void k_fp_bp_count(GeomC C, ExcTable E, const RayRec* rec, const ViewF* views, int* cnt,
-                              uint32_t* warp_rows) {
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, G = blockDim.x >> 5, t = blockIdx.x;
-    int ix, iy;
-    fp_tile_pixel(C.grid.n, t, lane, ix, iy);
-    int n = 0;
-    if (ix < C.grid.n && iy < C.grid.n) {
-        int v0, v1;
-        group_views(0, C.n_views, g, G, v0, v1);
-        pixel_pairs(C, E, rec, views, ix, iy, v0, v1, [&](int, float) { ++n; });
-    }
-    const int wi = t * G + g;
-    cnt[(size_t)wi * 32 + lane] = n;
-    n = __reduce_max_sync(0xffffffffu, n);
-    if (lane == 0) warp_rows[wi] = (uint32_t)n;
-}
-
-// Back-projection table, pass 2: lane r of warp wi writes its j-th pair (ray,
-// weight) at slot row bp_row[wi] + j.
-__global__ void k_fp_bp_fill(GeomC C, ExcTable E, const RayRec* rec, const ViewF* views,
-                             const uint32_t* __restrict__ bp_row, int2* pairs) {
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, G = blockDim.x >> 5, t = blockIdx.x;
-    int ix, iy;
-    fp_tile_pixel(C.grid.n, t, lane, ix, iy);
-    if (ix >= C.grid.n || iy >= C.grid.n) return;
-    int v0, v1;
-    group_views(0, C.n_views, g, G, v0, v1);
-    const size_t row = bp_row[t * G + g];
-    int j = 0;
-    pixel_pairs(C, E, rec, views, ix, iy, v0, v1, [&](int l, float w) {
-        pairs[(row + j) * 32 + lane] = make_int2(l, __float_as_int(w));
-        ++j;
-    });
-}
-
 // a1 from the forward table: the same line sums as proj_ray, in the same order,
 // with four pairs (and their gathers of xbar) in flight per step.
 __global__ void __launch_bounds__(kFwdThreads, 8) k_fp_proj(GeomC C, FpTables T, SolveD D, int v0, int v1) {
@@ -1194,55 +1132,261 @@ __global__ void __launch_bounds__(kFwdThreads, 8) k_fp_proj(GeomC C, FpTables T,
     D.g[l] = make_float4(gs.x, gs.y, gs.z, 0.f);
 }
 
-// a6 (+ a7) from the back-projection table: warp (tile, view group) streams its
-// lanes' pair lists (the order of bp_pixel_sum) with four pairs and their ray
-// gathers in flight per step; the view groups are combined as in k_mocca_bp.
-// With a view range [V0, V1) other than all views (PARTIAL, one GPU's share of
-// a split solve) the pairs of other views are skipped and the summed channels
-// go to chan ([9][P]).
-template <bool PARTIAL>
-__global__ void __launch_bounds__(kFpBpMaxThreads, 4) k_fp_bp(GeomC C, FpTables T, const RayRec* rec, StepParams P,
-                                                              SolveD D, int V0, int V1, float* chan) {
-    __shared__ float red[7 * 9 * 32];
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, G = blockDim.x >> 5;
-    const int t = blockIdx.x, wi = t * G + g, nb = C.n_bins;
+// The footprint pairs of pixel (ix, iy) in the views [v0, v1), in the order
+// bp_pixel_sum adds them (views ascending, candidate bins ascending, nonzero
+// weights only): visit(l, w).
+template <class Visit>
+__device__ __forceinline__ void pixel_pairs(const GeomC& C, const ExcTable& E, const RayRec* rec,
+                                            const ViewF* views, int ix, int iy, int v0, int v1, Visit&& visit) {
+    for (int v = v0; v < v1; ++v) {
+        int blo, bhi;
+        pixel_bin_range(C, views[v], ix, iy, blo, bhi);
+        for (int b = blo; b <= bhi; ++b) {
+            const int l = v * C.n_bins + b;
+            const float4 r0 = rec[l].r0, r1 = rec[l].r1;
+            const float w = x_weight(r0, r1.x, r1.y, C.grid, E, l, ix, iy);
+            if (w != 0.0f) visit(l, w);
+        }
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// ------------------------------------------------------------------ blocked back-projection table
+//
+// Block b = t G + g: pixel tile t (kBTX x kBTY pixels, one per thread) and view
+// group g of G (the split of k_mocca_bp).  The group's views go in chunks of
+// T.bp_chunk views; for chunk c the block stages, with asynchronous 16-byte
+// copies, the records of the rays that can meet the tile (per view u the bins
+// [tlo_u, tlo_u + span_u) of bp_span, view after view: stage slot
+// off_u + b - tlo_u), and each pixel runs through its pairs (slot, weight) of
+// the chunk, in the order of bp_pixel_sum.  A ray's record is read from L2 once
+// per tile and view and then from shared memory by every pixel that meets it.
+
+// The pixel of thread `tid` in tile t.
+__device__ __forceinline__ void bt_pixel(int n, int t, int tid, int& ix, int& iy) {
+    const int ntx = (n + kBTX - 1) / kBTX;
+    ix = (t % ntx) * kBTX + tid % kBTX;
+    iy = (t / ntx) * kBTY + tid / kBTX;
+}
+
+// The views [u0, u1) of chunk c of group g (views [V0, V1) of the whole range
+// split as group_views does, then in chunks of `chunk`).
+__device__ __forceinline__ void chunk_views(int n_views, int g, int G, int chunk, int c, int& u0, int& u1) {
+    int v0, v1;
+    group_views(0, n_views, g, G, v0, v1);
+    u0 = min(v1, v0 + c * chunk);
+    u1 = min(v1, u0 + chunk);
+}
+
+// Table pass 0: per tile and view the union of its pixels' candidate bins,
+// tlo | span << 16 (span 0: no pixel of the tile has a candidate there).
+__global__ void __launch_bounds__(kBTThreads) k_fpb_span(GeomC C, const ViewF* views, uint32_t* span) {
+    __shared__ int red_lo[kBTThreads / 32], red_hi[kBTThreads / 32];
+    const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     int ix, iy;
-    fp_tile_pixel(C.grid.n, t, lane, ix, iy);
+    bt_pixel(C.grid.n, t, tid, ix, iy);
+    const bool valid = ix < C.grid.n && iy < C.grid.n;
+    for (int v = 0; v < C.n_views; ++v) {
+        int blo = 0x7fffffff, bhi = -1;
+        if (valid) {
+            int lo, hi;
+            pixel_bin_range(C, views[v], ix, iy, lo, hi);
+            if (lo <= hi) {
+                blo = lo;
+                bhi = hi;
+            }
+        }
+        blo = __reduce_min_sync(0xffffffffu, blo);
+        bhi = __reduce_max_sync(0xffffffffu, bhi);
+        if (lane == 0) {
+            red_lo[wid] = blo;
+            red_hi[wid] = bhi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int lo = red_lo[0], hi = red_hi[0];
+            for (int w = 1; w < kBTThreads / 32; ++w) {
+                lo = min(lo, red_lo[w]);
+                hi = max(hi, red_hi[w]);
+            }
+            span[(size_t)t * C.n_views + v] = hi < lo ? 0u : (uint32_t)lo | ((uint32_t)(hi - lo + 1) << 16);
+        }
+        __syncthreads();
+    }
+}
+
+// The stage slot offsets of chunk views [u0, u1) of tile t: off[i] for view u0 + i.
+__device__ __forceinline__ int chunk_offsets(const uint32_t* span, int t, int n_views, int u0, int u1,
+                                             int off[kBTMaxChunk], int tlo[kBTMaxChunk], int wid[kBTMaxChunk]) {
+    int total = 0;
+#pragma unroll
+    for (int i = 0; i < kBTMaxChunk; ++i) {
+        const int u = u0 + i;
+        const uint32_t sp = u < u1 ? __ldg(span + (size_t)t * n_views + u) : 0u;
+        off[i] = total;
+        tlo[i] = (int)(sp & 0xffffu);
+        wid[i] = (int)(sp >> 16);
+        total += wid[i];
+    }
+    return total;
+}
+
+// Table pass 1: each pixel's pair count per chunk, and per (chunk, warp) the largest.
+__global__ void __launch_bounds__(kBTThreads) k_fpb_count(GeomC C, ExcTable E, const RayRec* rec,
+                                                          const ViewF* views, int G, int chunk, int nch,
+                                                          uint16_t* cnt, uint32_t* warp_rows) {
+    const int b = blockIdx.x, t = b / G, g = b % G, tid = threadIdx.x;
+    int ix, iy;
+    bt_pixel(C.grid.n, t, tid, ix, iy);
+    const bool valid = ix < C.grid.n && iy < C.grid.n;
+    for (int c = 0; c < nch; ++c) {
+        int u0, u1;
+        chunk_views(C.n_views, g, G, chunk, c, u0, u1);
+        int n = 0;
+        if (valid) pixel_pairs(C, E, rec, views, ix, iy, u0, u1, [&](int, float) { ++n; });
+        const size_t e = (size_t)b * nch + c;
+        cnt[e * kBTThreads + tid] = (uint16_t)n;
+        n = __reduce_max_sync(0xffffffffu, n);
+        if ((tid & 31) == 0) warp_rows[e * (kBTThreads / 32) + (tid >> 5)] = (uint32_t)n;
+    }
+}
+
+// Table pass 2: the pairs (stage slot, weight) at slot row bp_row[(e, warp)] + j.
+__global__ void __launch_bounds__(kBTThreads) k_fpb_fill(GeomC C, ExcTable E, const RayRec* rec,
+                                                         const ViewF* views, const uint32_t* __restrict__ span,
+                                                         int G, int chunk, int nch,
+                                                         const uint32_t* __restrict__ bp_row, int2* pairs) {
+    const int b = blockIdx.x, t = b / G, g = b % G, tid = threadIdx.x, lane = tid & 31;
+    int ix, iy;
+    bt_pixel(C.grid.n, t, tid, ix, iy);
+    if (ix >= C.grid.n || iy >= C.grid.n) return;
+    for (int c = 0; c < nch; ++c) {
+        int u0, u1;
+        chunk_views(C.n_views, g, G, chunk, c, u0, u1);
+        int off[kBTMaxChunk], tlo[kBTMaxChunk], wid[kBTMaxChunk];
+        chunk_offsets(span, t, C.n_views, u0, u1, off, tlo, wid);
+        const size_t e = (size_t)b * nch + c;
+        const size_t row = bp_row[e * (kBTThreads / 32) + (tid >> 5)];
+        int j = 0;
+        pixel_pairs(C, E, rec, views, ix, iy, u0, u1, [&](int l, float w) {
+            const int u = l / C.n_bins, i = u - u0;
+            const int slot = off[i] + (l - u * C.n_bins) - tlo[i];
+            pairs[(row + j) * 32 + lane] = make_int2(slot, __float_as_int(w));
+            ++j;
+        });
+    }
+}
+
+// Stage chunk views [u0, u1) of tile t (the rays of bp_span) into the buffer:
+// each slot gets the ray's r1 (b0, b1 in .zw) and its step half.
+__device__ __forceinline__ void stage_chunk(const GeomC& C, const FpTables& T, const RayRec* rec, const RayStep* steps,
+                                            int t, int u0, int u1, float4* s_r1, float4* s_s0, float4* s_s1) {
+    int off[kBTMaxChunk], tlo[kBTMaxChunk], wid[kBTMaxChunk];
+    const int total = chunk_offsets(T.bp_span, t, C.n_views, u0, u1, off, tlo, wid);
+    for (int r = threadIdx.x; r < total; r += kBTThreads) {
+        int i = 0;
+#pragma unroll
+        for (int q = 1; q < kBTMaxChunk; ++q)
+            if (q < u1 - u0 && r >= off[q]) i = q;
+        const int l = (u0 + i) * C.n_bins + tlo[i] + (r - off[i]);
+        cp_async16(s_r1 + r, &rec[l].r1);
+        cp_async16(s_s0 + r, &steps[l].s0);
+        cp_async16(s_s1 + r, &steps[l].s1);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// a6 from the blocked table: each pixel's nine channels over its group's views,
+// written to part ([G][9][P]); k_fpb_finish adds the groups and takes the step.
+// PARTIAL: only the views [V0, V1) (one GPU's share of a split solve).
+template <bool PARTIAL>
+__global__ void __launch_bounds__(kBTThreads) k_fpb_bp(GeomC C, FpTables T, const RayRec* rec, int V0, int V1,
+                                                       float* part) {
+    extern __shared__ float4 bt_smem[];   // two buffers of [3][bp_slots] float4
+    const int G = T.bp_groups, b = blockIdx.x, t = b / G, g = b % G, tid = threadIdx.x, lane = tid & 31;
+    const int S = T.bp_slots, nch = T.bp_nch, chunk = T.bp_chunk, nb = C.n_bins;
+    int ix, iy;
+    bt_pixel(C.grid.n, t, tid, ix, iy);
     const bool valid = ix < C.grid.n && iy < C.grid.n;
     const RayStep* steps = ray_steps(rec, C.n_views * nb);
-    const int2* p = T.bp_pairs + (size_t)__ldg(T.bp_row + wi) * 32 + lane;
-    const int n = __ldg(T.bp_cnt + (size_t)wi * 32 + lane);
-    const int l_lo = V0 * nb, l_hi = V1 * nb;   // the rays of the views [V0, V1)
     float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int j = 0;
-    for (; j + 3 < n; j += 4) {
-        int2 a[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = __ldg(p + 32 * u);
-        float4 r1[4];
-        RecHalf st[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            r1[u] = __ldg(&rec[a[u].x].r1);
-            st[u] = ldg_half(&steps[a[u].x].s0);
+    int u0, u1;
+    chunk_views(C.n_views, g, G, chunk, 0, u0, u1);
+    if (nch > 0) stage_chunk(C, T, rec, steps, t, u0, u1, bt_smem, bt_smem + S, bt_smem + 2 * S);
+    for (int c = 0; c < nch; ++c) {
+        float4* buf = bt_smem + (size_t)(c & 1) * 3 * S;
+        int n0, n1;
+        chunk_views(C.n_views, g, G, chunk, c, n0, n1);
+        if (c + 1 < nch) {   // the next chunk into the other buffer (free since the barrier ending chunk c - 1)
+            int w0, w1;
+            chunk_views(C.n_views, g, G, chunk, c + 1, w0, w1);
+            float4* nbuf = bt_smem + (size_t)((c + 1) & 1) * 3 * S;
+            stage_chunk(C, T, rec, steps, t, w0, w1, nbuf, nbuf + S, nbuf + 2 * S);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
+        __syncthreads();   // chunk c staged by every thread
+        int s_lo = 0, s_hi = 1 << 30;   // stage slots of the views [V0, V1) (PARTIAL)
+        if (PARTIAL) {
+            int off[kBTMaxChunk], tlo[kBTMaxChunk], wid[kBTMaxChunk];
+            const int total = chunk_offsets(T.bp_span, t, C.n_views, n0, n1, off, tlo, wid);
+            const int i0 = min(max(V0 - n0, 0), n1 - n0), i1 = min(max(V1 - n0, 0), n1 - n0);
+            s_lo = i0 < n1 - n0 ? off[i0] : total;
+            s_hi = i1 < n1 - n0 ? off[i1] : total;
+        }
+        const size_t e = (size_t)b * nch + c;
+        const int n = __ldg(T.bp_cnt + e * kBTThreads + tid);
+        const int2* p = T.bp_pairs + (size_t)__ldg(T.bp_row + e * (kBTThreads / 32) + (tid >> 5)) * 32 + lane;
+        const float4 *r1 = buf, *s0 = buf + S, *s1 = buf + 2 * S;
+        int j = 0;
+        for (; j + 3 < n; j += 4) {
+            int2 a[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (!PARTIAL || (a[u].x >= l_lo && a[u].x < l_hi))
-                bp_accumulate(acc, __int_as_float(a[u].y), r1[u], st[u].a, st[u].b);
-        p += 128;
+            for (int q = 0; q < 4; ++q) a[q] = __ldg(p + 32 * q);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (!PARTIAL || (a[q].x >= s_lo && a[q].x < s_hi))
+                    bp_accumulate(acc, __int_as_float(a[q].y), r1[a[q].x], s0[a[q].x], s1[a[q].x]);
+            p += 128;
+        }
+        for (; j < n; ++j, p += 32) {
+            const int2 a = __ldg(p);
+            if (!PARTIAL || (a.x >= s_lo && a.x < s_hi))
+                bp_accumulate(acc, __int_as_float(a.y), r1[a.x], s0[a.x], s1[a.x]);
+        }
+        __syncthreads();   // buffer c & 1 is read by everyone before chunk c + 2 overwrites it
     }
-    for (; j < n; ++j, p += 32) {
-        const int2 a = __ldg(p);
-        if (PARTIAL && (a.x < l_lo || a.x >= l_hi)) continue;
-        const float4 r1 = __ldg(&rec[a.x].r1);
-        const RecHalf st = ldg_half(&steps[a.x].s0);
-        bp_accumulate(acc, __int_as_float(a.y), r1, st.a, st.b);
+    if (valid) {
+        const size_t P_ = (size_t)C.grid.n * C.grid.n, k = (size_t)iy * C.grid.n + ix;
+#pragma unroll
+        for (int ch = 0; ch < 9; ++ch) part[((size_t)g * 9 + ch) * P_ + k] = acc[ch];
     }
-    if (PARTIAL)
-        bp_partial_out(C.grid.n * C.grid.n, iy * C.grid.n + ix, valid, lane, 32, g, G, red, acc, chan);
-    else
-        bp_finish(C, P, D, ix, iy, valid, lane, 32, g, G, red, acc);
+}
+
+// The view groups' channels added in group order (as bp_finish does), then a7
+// for every pixel; PARTIAL: the sum goes to chan ([9][P]) instead.
+template <bool PARTIAL>
+__global__ void k_fpb_finish(GeomC C, StepParams P, SolveD D, const float* __restrict__ part, int G, float* chan) {
+    const int P_ = C.grid.n * C.grid.n;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P_) return;
+    float acc[9];
+#pragma unroll
+    for (int ch = 0; ch < 9; ++ch) acc[ch] = part[(size_t)ch * P_ + k];
+    for (int gg = 1; gg < G; ++gg)
+#pragma unroll
+        for (int ch = 0; ch < 9; ++ch) acc[ch] += part[((size_t)gg * 9 + ch) * P_ + k];
+    if (PARTIAL) {
+#pragma unroll
+        for (int ch = 0; ch < 9; ++ch) chan[(size_t)ch * P_ + k] = acc[ch];
+    } else {
+        pixel_step(C, P, D, k, acc);
+    }
 }
 
 constexpr int kReduceThreads = 1024;
@@ -1390,13 +1534,23 @@ cudaError_t launch_mocca_ray_inner(const GeomC& C, RayRec* rec, const SolveD& D,
     return cudaGetLastError();
 }
 
+// The table-driven back-projection: the blocked pass into T.bp_part, then the
+// group sums with a7 (or into chan).
+template <bool PARTIAL>
+cudaError_t launch_fpb(const GeomC& C, const FpTables& T, const RayRec* rec, const StepParams& P, const SolveD& D,
+                       int v0, int v1, float* chan, cudaStream_t st) {
+    const size_t smem = sizeof(float4) * 6 * (size_t)T.bp_slots;
+    k_fpb_bp<PARTIAL><<<bt_tiles(C.grid.n) * T.bp_groups, kBTThreads, smem, st>>>(C, T, rec, v0, v1, T.bp_part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_fpb_finish<PARTIAL><<<blocks(C.grid.n * C.grid.n, 256), 256, 0, st>>>(C, P, D, T.bp_part, T.bp_groups, chan);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mocca_bp(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
                             const StepParams& P, const SolveD& D, cudaStream_t st, const FpTables* T) {
+    if (T && T->bp_pairs) return launch_fpb<false>(C, *T, rec, P, D, 0, C.n_views, nullptr, st);
     const int G = bp_view_groups(C.grid.n * C.grid.n, C.n_views);
-    if (T) {
-        k_fp_bp<false><<<fp_tiles(C.grid.n), 32 * T->bp_groups, 0, st>>>(C, *T, rec, P, D, 0, C.n_views, nullptr);
-        return cudaGetLastError();
-    }
     dim3 grid(blocks(C.grid.n, kBpPixX), blocks(C.grid.n, kBpPixY)), blk(kBpPixX, kBpPixY, G);
     const size_t smem = sizeof(float) * (size_t)(G - 1) * 9 * kBpPix;
     k_mocca_bp<false><<<grid, blk, smem, st>>>(C, E, rec, views, P, D, 0, C.n_views, nullptr);
@@ -1406,10 +1560,7 @@ cudaError_t launch_mocca_bp(const GeomC& C, const ExcTable& E, const RayRec* rec
 cudaError_t launch_mocca_bp_partial(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
                                     const StepParams& P, const SolveD& D, int v0, int v1, float* chan,
                                     cudaStream_t st, const FpTables* T) {
-    if (T) {
-        k_fp_bp<true><<<fp_tiles(C.grid.n), 32 * T->bp_groups, 0, st>>>(C, *T, rec, P, D, v0, v1, chan);
-        return cudaGetLastError();
-    }
+    if (T && T->bp_pairs) return launch_fpb<true>(C, *T, rec, P, D, v0, v1, chan, st);
     const int G = bp_view_groups(C.grid.n * C.grid.n, v1 - v0);
     dim3 grid(blocks(C.grid.n, kBpPixX), blocks(C.grid.n, kBpPixY)), blk(kBpPixX, kBpPixY, G);
     const size_t smem = sizeof(float) * (size_t)(G - 1) * 9 * kBpPix;
@@ -1429,15 +1580,21 @@ cudaError_t launch_fp_fwd_fill(const GeomC& C, const ExcTable& E, const RayRec* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_fp_bp_count(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views, int G,
-                               int* cnt, uint32_t* warp_rows, cudaStream_t st) {
-    k_fp_bp_count<<<fp_tiles(C.grid.n), 32 * G, 0, st>>>(C, E, rec, views, cnt, warp_rows);
+cudaError_t launch_fpb_span(const GeomC& C, const ViewF* views, uint32_t* span, cudaStream_t st) {
+    k_fpb_span<<<bt_tiles(C.grid.n), kBTThreads, 0, st>>>(C, views, span);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fp_bp_fill(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views, int G,
-                              const uint32_t* bp_row, int2* pairs, cudaStream_t st) {
-    k_fp_bp_fill<<<fp_tiles(C.grid.n), 32 * G, 0, st>>>(C, E, rec, views, bp_row, pairs);
+cudaError_t launch_fpb_count(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views, int G,
+                             int chunk, int nch, uint16_t* cnt, uint32_t* warp_rows, cudaStream_t st) {
+    k_fpb_count<<<bt_tiles(C.grid.n) * G, kBTThreads, 0, st>>>(C, E, rec, views, G, chunk, nch, cnt, warp_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fpb_fill(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
+                            const uint32_t* span, int G, int chunk, int nch, const uint32_t* bp_row, int2* pairs,
+                            cudaStream_t st) {
+    k_fpb_fill<<<bt_tiles(C.grid.n) * G, kBTThreads, 0, st>>>(C, E, rec, views, span, G, chunk, nch, bp_row, pairs);
     return cudaGetLastError();
 }
 

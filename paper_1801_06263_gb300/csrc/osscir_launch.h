@@ -62,31 +62,37 @@ constexpr int kBpTileX = 16, kBpTileY = 8;            // plain back-projection t
 constexpr int kBpPixX = 2, kBpPixY = 32;              // MOCCA back-projection pixel tile (2 x 32: measured fastest)
 constexpr int kBpPix = kBpPixX * kBpPixY;
 constexpr int kBpMaxThreads = 512;                    // kBpPix x up to 8 view groups
-// Footprint tables: the back-projection table's pixel tile (one pixel per lane
-// of a warp) and the table-driven back-projection's block (one warp per view group).
-constexpr int kFpTX = 8, kFpTY = 4;
-constexpr int kFpBpMaxThreads = 256;
-inline int fp_tiles(int n) { return ((n + kFpTX - 1) / kFpTX) * ((n + kFpTY - 1) / kFpTY); }
+// Blocked back-projection table: a block is a tile of kBTX x kBTY pixels (one
+// per thread) and one view group; its views go in chunks of at most kBTMaxChunk.
+constexpr int kBTX = 16, kBTY = 16, kBTThreads = kBTX * kBTY, kBTMaxChunk = 8;
+inline int bt_tiles(int n) { return ((n + kBTX - 1) / kBTX) * ((n + kBTY - 1) / kBTY); }
 
 // Footprint tables of one geometry: the pairs (l, k) of X with their weights,
-// in the order each projector visits them.  Both are lists per warp with the
-// lanes interleaved: lane r's j-th entry of warp w is at (row[w] + j) 32 + r,
-// row[w] the prefix sum of the warps' largest counts, cnt the lanes' counts.
+// in the order each projector visits them.
 //   Forward (ray-major): warp w = (view v, 32-bin group bx), w = v nbg + bx with
-//   nbg = ceil(n_bins / 32), lane r = bin 32 bx + r; entries (pixel k, weight
-//   bits) in the visiting order of ray_weights.
-//   Back-projection (pixel-major): warp w = t G + g (tile t of kFpTX x kFpTY
-//   pixels, lane r = pixel (r mod kFpTX, r div kFpTX) of the tile; view group g
-//   of bp_groups, the split of k_mocca_bp); entries (ray l, weight bits) of the
-//   group's views in the order of bp_pixel_sum.
+//   nbg = ceil(n_bins / 32), lane r = bin 32 bx + r.  The j-th pair of ray l (in
+//   the visiting order of ray_weights) is fwd_pairs[(fwd_row[w] + j) 32 + r] =
+//   (pixel k, weight bits), fwd_cnt[l] pairs; fwd_row is the prefix sum of the
+//   warps' largest counts.
+//   Back-projection (blocked): block b = t G + g (tile t, view group g of G =
+//   bp_groups); the group's views (the split of k_mocca_bp) in chunks of
+//   bp_chunk views, bp_nch chunks per group, entry e = b bp_nch + c.  bp_span
+//   [t n_views + u] = tlo | span << 16: the union of the tile's candidate bins in
+//   view u; a chunk's rays are staged view after view, ray (u, tlo + i) at slot
+//   (sum of the earlier views' spans) + i, at most bp_slots slots.  Thread r's
+//   j-th pair of entry e (stage slot, weight bits) is bp_pairs[(bp_row[8 e + r /
+//   32] + j) 32 + r % 32], bp_cnt[256 e + r] pairs, in the order of
+//   bp_pixel_sum.  bp_part: [G][9][P] scratch for the groups' channel sums.
 struct FpTables {
     const uint32_t* fwd_row;   // [n_views nbg + 1]
     const int* fwd_cnt;        // [L]
     const int2* fwd_pairs;
-    const uint32_t* bp_row;    // [fp_tiles(n) bp_groups + 1]
-    const int* bp_cnt;         // [fp_tiles(n) bp_groups 32]
-    const int2* bp_pairs;
-    int bp_groups;
+    const uint32_t* bp_span;   // [bt_tiles(n) n_views]
+    const uint32_t* bp_row;    // [n_entries 8 + 1]
+    const uint16_t* bp_cnt;    // [n_entries 256]
+    const int2* bp_pairs;      // null: the back-projection is computed on the fly
+    float* bp_part;            // [bp_groups][9][P]
+    int bp_groups, bp_chunk, bp_nch, bp_slots;
 };
 
 // View groups per pixel for the MOCCA back-projection: enough threads to fill
@@ -139,10 +145,12 @@ cudaError_t launch_fp_fwd_count(const GeomC& C, const ExcTable& E, const RayRec*
                                 uint32_t* warp_rows, cudaStream_t st);
 cudaError_t launch_fp_fwd_fill(const GeomC& C, const ExcTable& E, const RayRec* rec, const uint32_t* fwd_row,
                                int2* pairs, cudaStream_t st);
-cudaError_t launch_fp_bp_count(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views, int G,
-                               int* cnt, uint32_t* warp_rows, cudaStream_t st);
-cudaError_t launch_fp_bp_fill(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views, int G,
-                              const uint32_t* bp_row, int2* pairs, cudaStream_t st);
+cudaError_t launch_fpb_span(const GeomC& C, const ViewF* views, uint32_t* span, cudaStream_t st);
+cudaError_t launch_fpb_count(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views, int G,
+                             int chunk, int nch, uint16_t* cnt, uint32_t* warp_rows, cudaStream_t st);
+cudaError_t launch_fpb_fill(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
+                            const uint32_t* span, int G, int chunk, int nch, const uint32_t* bp_row, int2* pairs,
+                            cudaStream_t st);
 cudaError_t launch_mocca_apply(const GeomC& C, const StepParams& P, const SolveD& D, const float* chan,
                                cudaStream_t st);
 
