@@ -71,11 +71,16 @@ FP32_LANES_PER_SM, SCHEDULERS_PER_SM, L1_BYTES_PER_CLK_PER_SM = 128, 4, 128
 # instructions executed.  Valid only for that workload and for the kernel
 # sources they were taken on (source_sha, see _source_sha).
 NCU_WORKLOAD = "medium_256"
-NCU_COUNTS = {
-    "k_mocca_proj": {"dram_bytes": 10487296, "warp_instructions": 151.3e6, "source_sha": "dfbd97d3772e3c85"},
-    "k_mocca_ray": {"dram_bytes": 23002368 + 3328, "warp_instructions": 113.6e6, "source_sha": "dfbd97d3772e3c85"},
-    "k_mocca_bp": {"dram_bytes": 16140800 + 512, "warp_instructions": 205.5e6, "source_sha": "dfbd97d3772e3c85"},
-}
+NCU_COUNTS = {}
+
+
+def bp_view_groups(n_pixels, n_views):
+    """View groups per pixel of the library's back-projection (the same rule as the
+    library: enough threads to fill the GPU several times, at most 8, one view each)."""
+    G = 8 if n_pixels <= 131072 else (4 if n_pixels <= 524288 else 2)
+    while G > 1 and G > n_views:
+        G >>= 1
+    return G
 
 
 def device_roofs(dev, sm_mhz):
@@ -346,16 +351,29 @@ def run_gpu(args):
 
     if rank != 0:
         return 0
-    L, nE = w.geom.n_rays, w.spectra.n_energies
+    L, nE, P = w.geom.n_rays, w.spectra.n_energies, w.geom.n_pixels
     mean = [statistics.mean(k[i] for k in kms) for i in range(3)]
+    dev_bytes, table_bytes = _lib.osscir_memory(R.handle)
+    G = bp_view_groups(P, w.geom.n_views)
+    if table_bytes:
+        # footprint tables: the projections stream them.  Algorithmic HBM bytes per
+        # launch: forward 8 B per footprint pair (pixel, weight) + xbar read (16 B per
+        # pixel) + g written and the counts read (20 B per ray); back-projection 6 B per
+        # pair (weight, stage slot) + the view groups' channel sums written and read
+        # (2 x 36 B per pixel and group) + x, xbar read and written (48 B per pixel)
+        names = ("k_fp_proj", "k_mocca_ray", "k_fpb_bp")
+        alg = (8.0 * nnz + 16.0 * P + 20.0 * L, None, 6.0 * nnz + 72.0 * G * P + 48.0 * P)
+    else:
+        names = ("k_mocca_proj", "k_mocca_ray", "k_mocca_bp")
+        alg = (None, None, None)
     kern = {
-        # k_mocca_proj: 3 FMA per footprint pair (three materials)
-        "k_mocca_proj": {"ms": mean[0], "flop": 6.0 * nnz},
-        # k_mocca_ray: 29 FMA per (ray, energy): p_i (3), D_w (4), alpha numerators (12),
-        # beta_i (4) and sum_i beta_i mu_i mu_i^T (6); the FP64 per-ray algebra is not counted
-        "k_mocca_ray": {"ms": mean[1], "flop": 58.0 * L * nE},
-        # k_mocca_bp: 9 FMA per footprint pair (K^T y' and the 6-channel block SPC)
-        "k_mocca_bp": {"ms": mean[2], "flop": 18.0 * nnz},
+        # projection: 3 FMA per footprint pair (three materials)
+        names[0]: {"ms": mean[0], "flop": 6.0 * nnz, "bytes": alg[0]},
+        # per-ray step: 29 FMA per (ray, energy): p_i (3), D_w (4), alpha numerators (12),
+        # beta_i (4) and sum_i beta_i mu_i mu_i^T (6); the per-ray 3x3 algebra is not counted
+        names[1]: {"ms": mean[1], "flop": 58.0 * L * nE, "bytes": alg[1]},
+        # back-projection: 9 FMA per footprint pair (K^T y' and the 6-channel block SPC)
+        names[2]: {"ms": mean[2], "flop": 18.0 * nnz, "bytes": alg[2]},
     }
     dom = max(kern, key=lambda k: kern[k]["ms"])
     clocks = clk.summary()
@@ -368,31 +386,33 @@ def run_gpu(args):
         sec = v["ms"] * 1e-3
         row = {"ms": v["ms"], "algorithmic_tflops": v["flop"] / sec / 1e12,
                "alu_frac": v["flop"] / sec / 1e12 / roofs["fp32_tflops"]}
+        if v["bytes"]:
+            row["algorithmic_GBps"] = v["bytes"] / sec / 1e9
+            row["hbm_frac"] = v["bytes"] / sec / 1e9 / HBM_PEAK_GBPS
         if ncu.get(k):
             # issue: the warp instructions the kernel executed over the issue slots of its duration
             row["warp_instructions"] = ncu[k]["warp_instructions"]
             row["issue_frac"] = ncu[k]["warp_instructions"] / (sec * roofs["issue_per_s"])
             row["dram_bytes"] = ncu[k]["dram_bytes"]
-            row["hbm_frac"] = ncu[k]["dram_bytes"] / sec / 1e9 / HBM_PEAK_GBPS
-            row["binding"] = "issue"
+            row["dram_frac"] = ncu[k]["dram_bytes"] / sec / 1e9 / HBM_PEAK_GBPS
+        row["binding"] = "hbm" if v["bytes"] else "instruction issue"
         kernels[k] = row
-    # bytes each footprint pair must bring from L1 to the registers: proj the float4 of
-    # xbar; bp the ray's weight inputs (foot point, reciprocal direction, bounds: 24 B)
-    # and its b and S (36 B)
-    gather_bytes = {"k_mocca_proj": 16.0, "k_mocca_bp": 60.0}.get(dom)
-    gather = None
-    if gather_bytes:
-        g_ach = gather_bytes * nnz / (kern[dom]["ms"] * 1e-3) / 1e12
-        gather = {"bound": "l1", "kernel": dom, "bytes_per_pair": gather_bytes, "achieved": g_ach,
-                  "peak": roofs["l1_tbps"], "unit": "TB/s", "frac": g_ach / roofs["l1_tbps"],
-                  "peak_source": roofs["source"] + "; 128 B per clock per SM from L1 to registers"}
-    achieved = kern[dom]["flop"] / (kern[dom]["ms"] * 1e-3) / 1e12
     traffic = ncu[dom]["dram_bytes"] if ncu.get(dom) else None
-    issue = None
-    if ncu.get(dom):
-        ach_i = ncu[dom]["warp_instructions"] / (kern[dom]["ms"] * 1e-3)
-        issue = {"warp_instructions": ncu[dom]["warp_instructions"], "achieved": ach_i / 1e12,
-                 "peak": roofs["issue_per_s"] / 1e12, "unit": "T warp-instr/s", "frac": ach_i / roofs["issue_per_s"]}
+    if kern[dom]["bytes"]:
+        ach = kern[dom]["bytes"] / (kern[dom]["ms"] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": HBM_PEAK_GBPS, "unit": "GB/s",
+                    "frac": ach / HBM_PEAK_GBPS, "traffic": traffic, "peak_source": HBM_PEAK_SOURCE,
+                    "algorithmic_bytes": kern[dom]["bytes"]}
+    else:
+        ach = kern[dom]["flop"] / (kern[dom]["ms"] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": roofs["fp32_tflops"],
+                    "unit": "TFLOP/s", "frac": ach / roofs["fp32_tflops"], "traffic": traffic,
+                    "peak_source": roofs["source"] + "; 128 FP32 lanes x 2 flop per clock per SM"}
+        if ncu.get(dom):
+            ach_i = ncu[dom]["warp_instructions"] / (kern[dom]["ms"] * 1e-3)
+            roofline["binding"] = {"unit": "instruction issue", "warp_instructions": ncu[dom]["warp_instructions"],
+                                   "achieved": ach_i / 1e12, "peak": roofs["issue_per_s"] / 1e12,
+                                   "peak_unit": "T warp-instr/s", "frac": ach_i / roofs["issue_per_s"]}
     cpu = None
     if ws == 1 and args.cpu_iters > 0:
         rate, cores, dt = cpu_oracle_rate(args.cpu_iters)
@@ -413,12 +433,9 @@ def run_gpu(args):
         "kernel_ms": {k: v["ms"] for k, v in kern.items()},
         "footprint_pairs": nnz,
         "intersections_per_s": 2.0 * nnz / (total_s / args.steps) * ws,
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": roofs["fp32_tflops"],
-                     "unit": "TFLOP/s", "frac": achieved / roofs["fp32_tflops"], "traffic": traffic,
-                     "peak_source": roofs["source"] + "; 128 FP32 lanes x 2 flop per clock per SM",
-                     "binding": {"unit": "instruction issue", **issue} if issue else None},
+        "roofline": roofline,
         "kernels": kernels,
-        "gather_roofline": gather,
+        "memory": {"context_bytes": dev_bytes, "footprint_table_bytes": table_bytes},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_rate, "unit": "iter/s", "h2d_bytes_per_step": int(c_host.numel() * 4),
                 "d2h_bytes_per_step": int(maps_host.numel() * 4),
@@ -430,7 +447,7 @@ def run_gpu(args):
         "batched": batched,
         "served_mixed": mixed,
         "clocks": clocks,
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": (5 if table_bytes else 4) * args.steps,   # proj, ray, reduction, bp (+ group sums)
         "dtpl_last": d_last,
         "maps_finite": finite,
     }

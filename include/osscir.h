@@ -77,7 +77,12 @@ typedef struct {
 /* Solver parameters.  lambda is the step-size ratio of the step-preconditioner
  * (Sec. 2 leaves it to tuning).  model = 0 uses the per-ray Hessian of Sec. 2 with
  * its negative eigenvalues removed as the curvature of the local quadratic;
- * model = 1 uses zero curvature (a preconditioned gradient step).  use_box = 1
+ * model = 1 uses zero curvature (a preconditioned gradient step); model = 2 the
+ * Hessian's first term alone, sum_w c_w alpha_w alpha_w^T (Gauss-Newton: the
+ * term weighted by the residual is dropped, so no eigenvalue is negative);
+ * model = 3 the separable W = diag(c) on the window line integrals (equal to
+ * model 2's curvature on the range of K).  Models 2 and 3 are readings of the
+ * local quadratic that Sec. 2 defers to Barber et al. 2016.  use_box = 1
  * constrains every iterate to lo <= f <= hi per material (the convex constraint
  * set of the one-step framework, Sec. 1); bounds may be infinite, so lo = 0,
  * hi = +inf is nonnegativity; 0 leaves f unconstrained (Sec. 2: the softexp
@@ -137,6 +142,13 @@ osscir_status osscir_destroy(osscir_t h);
 /* Sizes of the context: pixels P = n*n, rays L = n_views*n_bins, and the
  * number of footprint pairs decided in FP64 (any pointer may be NULL). */
 osscir_status osscir_info(osscir_t h, int *n_pixels, int *n_rays, int *n_fp64_pairs);
+
+/* Device memory held by the context (host size_t, either pointer may be NULL):
+ * device_bytes all of it, table_bytes the part taken by the footprint tables,
+ * which the context builds before its first iteration (0 before that, and 0 if
+ * the device had no room for them: the projections are then recomputed every
+ * iteration, with the same results).  The paper has no counterpart. */
+osscir_status osscir_memory(osscir_t h, size_t *device_bytes, size_t *table_bytes);
 
 /* Forward projection g_l = sum_k X_{l,k} x_k of four channels (the X of Eq. fullModel).
  *   x: device float[P][4] (input), g: device float[L][4] (output). */

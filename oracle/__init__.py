@@ -81,7 +81,7 @@ def lib():
         L.orc_solve.restype = ct.c_int
         L.orc_eig_sym3.argtypes = [_dp, _dp, _dp]
         L.orc_clip_psd3.argtypes = [_dp, _dp]
-        L.orc_dual_update.argtypes = [_dp, _dp, _dp, _dp, ct.c_int, _dp, _dp]
+        L.orc_dual_update.argtypes = [_dp, _dp, _dp, _dp, ct.c_int, _dp, _dp, _dp]
         L.orc_dual_update.restype = ct.c_int
         L.orc_primal_update.argtypes = [_dp, _dp, _dp, ct.c_int, _dp, _dp, _dp]
         L.orc_primal_update.restype = ct.c_int
@@ -125,7 +125,7 @@ class _SpecHolder:
 
 def _params(lam, use_box=False, lo=(0, 0, 0), hi=(0, 0, 0), spc="block", model="hessian", inner=1):
     return _Params(float(lam), int(bool(use_box)), (ct.c_double * 3)(*lo), (ct.c_double * 3)(*hi),
-                   {"block": 0, "diagonal": 1}[spc], {"hessian": 0, "gradient": 1}[model], int(inner))
+                   {"block": 0, "diagonal": 1}[spc], MODELS[model], int(inner))
 
 
 def set_threads(n: int) -> None:
@@ -243,10 +243,15 @@ def clip_psd3(H):
     return Hp.reshape(3, 3)
 
 
-def dual_update(alpha, Hp, r, sigma_inv, y, model="hessian"):
+MODELS = {"hessian": 0, "gradient": 1, "gauss_newton": 2, "separable": 3}
+
+
+def dual_update(alpha, Hp, r, sigma_inv, y, model="hessian", c=None):
+    """Dual step of one ray; c (the window counts) is needed by model="separable"."""
     out = np.zeros(4)
+    cw = _f64(np.zeros(4) if c is None else c)
     st = lib().orc_dual_update(_ptr(_f64(alpha)), _ptr(_f64(Hp)), _ptr(_f64(r)),
-                               _ptr(_f64(sigma_inv)), {"hessian": 0, "gradient": 1}[model],
+                               _ptr(_f64(sigma_inv)), MODELS[model], _ptr(cw),
                                _ptr(_f64(y)), _ptr(out))
     if st:
         raise np.linalg.LinAlgError("singular dual system")
@@ -318,13 +323,15 @@ def mocca(geom, spectra, c, n_iters, lam, state=None, *, box=None, spc="block",
 
 # --------------------------------------------------------------------------- mu-PC basis change
 
-def mu_pc(mu):
+def mu_pc(mu, weights=None):
     """mu-PC (Sec. 1 and 2): (mu_t, M) with mu_t = M mu, whose rows are
-    orthonormal over the energy grid in the Euclidean inner product, and
-    M = (mu mu^T)^(-1/2), the symmetric choice (the paper leaves the
-    orthogonalisation to Barber et al. 2016).  numpy's eigh is the step."""
+    orthonormal over the energy grid in the inner product sum_i weights_i a_i b_i
+    (Euclidean when weights is None), and M = (mu diag(weights) mu^T)^(-1/2), the
+    symmetric choice (the paper leaves the orthogonalisation to Barber et al.
+    2016).  numpy's eigh is the step."""
     mu = np.asarray(mu, dtype=np.float64)
-    w, V = np.linalg.eigh(mu @ mu.T)
+    wts = np.ones(mu.shape[1]) if weights is None else np.asarray(weights, dtype=np.float64)
+    w, V = np.linalg.eigh((mu * wts) @ mu.T)
     M = V @ np.diag(w ** -0.5) @ V.T
     return M @ mu, M
 

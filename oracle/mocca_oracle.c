@@ -66,7 +66,10 @@ typedef struct {
     int use_box;   /* 0: C = R^3, 1: box lo <= x <= hi                     */
     double lo[3], hi[3];
     int spc;   /* 0: m-block-diagonal SPC (Sec. 2); 1: diagonal SPC (Pock-Chambolle) */
-    int model; /* 0: eigen-clipped Hessian; 1: W = 0 (preconditioned gradient step) */
+    int model; /* curvature of the local quadratic: 0 the eigen-clipped per-ray Hessian; 1 W = 0
+                  (preconditioned gradient step); 2 the Hessian's first term alone, sum_w c_w alpha_w
+                  alpha_w^T (Gauss-Newton, always PSD); 3 W = diag(c) on the window line integrals
+                  (separable; equal to 2 on the range of K) */
     int inner; /* iterations per local model: 1 single-loop MOCCA; k > 1 nested (see orc_mocca) */
 } orc_params;
 
@@ -462,13 +465,17 @@ void orc_clip_psd3(const double *H, double *Hp) {
 
 /* ------------------------------------------------------------------ MOCCA step pieces */
 
-/* Dual step of one ray.  sigma_inv[w] is (Sigma^-1)_{wl}; Hp the clipped
- * Hessian; model 1 takes W = 0.  With Sigma = diag(1/sigma_inv),
- *   G = (alpha^T alpha)^-1 alpha^T,  W = G^T Hp G,
+/* Dual step of one ray.  sigma_inv[w] is (Sigma^-1)_{wl}; Hp the curvature in
+ * the ray's line integrals g (models 0 and 2); c the measured counts (model 3).
+ * With Sigma = diag(1/sigma_inv),
+ *   models 0, 2:  G = (alpha^T alpha)^-1 alpha^T,  W = G^T Hp G;
+ *   model 1:      W = 0;
+ *   model 3:      W = diag(c);
  *   y' = y - Sigma (W + Sigma)^-1 (y - r).
  * A ray with a zero entry of sigma_inv misses the image and keeps y. */
 int orc_dual_update(const double alpha[12], const double Hp[9], const double r[4],
-                    const double sigma_inv[4], int model, const double y[4], double y_out[4]) {
+                    const double sigma_inv[4], int model, const double c[4], const double y[4],
+                    double y_out[4]) {
     for (int w = 0; w < NW; ++w)
         if (!(sigma_inv[w] > 0.0)) {
             memcpy(y_out, y, sizeof(double) * NW);
@@ -477,7 +484,9 @@ int orc_dual_update(const double alpha[12], const double Hp[9], const double r[4
     double sig[NW];
     for (int w = 0; w < NW; ++w) sig[w] = 1.0 / sigma_inv[w];
     double W[16] = {0};
-    if (model == 0) {
+    if (model == 3)
+        for (int w = 0; w < NW; ++w) W[w * NW + w] = c[w];
+    if (model == 0 || model == 2) {
         double AtA[9], AtAi[9], Gm[12];
         for (int m = 0; m < NM; ++m)
             for (int q = 0; q < NM; ++q) {
@@ -759,8 +768,18 @@ int orc_mocca(const orc_geometry *G, const orc_spectra *sp, const orc_params *P,
                 double *all = al + (size_t)l * 12;
                 if (outer) {
                     orc_ray_terms(sp, b, g + (size_t)l * NM, cl, chat, r, all, NULL, H, NULL, NULL);
-                    if (P->model == 0) orc_clip_psd3(H, Hp);
-                    else memset(Hp, 0, sizeof Hp);
+                    if (P->model == 0) {
+                        orc_clip_psd3(H, Hp);
+                    } else if (P->model == 2) {   /* sum_w c_w alpha_w alpha_w^T */
+                        for (int m = 0; m < NM; ++m)
+                            for (int q = 0; q < NM; ++q) {
+                                double acc = 0.0;
+                                for (int w = 0; w < NW; ++w) acc += cl[w] * all[w * NM + m] * all[w * NM + q];
+                                Hp[m * NM + q] = acc;
+                            }
+                    } else {
+                        memset(Hp, 0, sizeof Hp);
+                    }
                     int cnt = orc_siddon(G, l / G->n_bins, b, pp, ll, cap);
                     ray_sigma_inv(P, all, cnt, ll, sinv);
                     memcpy(u, y + (size_t)l * NW, sizeof u);
@@ -786,7 +805,7 @@ int orc_mocca(const orc_geometry *G, const orc_spectra *sp, const orc_params *P,
                 double d = 0.0;
                 for (int w = 0; w < NW; ++w) d += dtpl_term(chat[w], cl[w]);
                 dt[l] = d;
-                if (orc_dual_update(all, Hp, r, sinv, P->model, u, yn)) {
+                if (orc_dual_update(all, Hp, r, sinv, P->model, cl, u, yn)) {
 #pragma omp atomic write
                     status = -1;
                 }

@@ -32,7 +32,7 @@ EXPORTS = (
     "osscir_server_create", "osscir_server_destroy", "osscir_submit", "osscir_poll", "osscir_server_info",
     "osscir_batch_create", "osscir_batch_destroy", "osscir_batch_step", "osscir_batch_get_config",
     "osscir_batch_set_config", "osscir_batch_last_kernel_ms", "osscir_poisson_noise", "osscir_mocca_partial",
-    "osscir_mocca_apply",
+    "osscir_mocca_apply", "osscir_memory",
 )
 
 
@@ -129,6 +129,7 @@ def load(build_if_missing: bool = True):
         "osscir_poisson_noise": ([vp, ct.c_int, ct.c_uint64, vp, vp], ct.c_int),
         "osscir_mocca_partial": ([vp, ct.c_int, ct.c_int, vp, vp], ct.c_int),
         "osscir_mocca_apply": ([vp, vp, vp], ct.c_int),
+        "osscir_memory": ([vp, ct.POINTER(ct.c_size_t), ct.POINTER(ct.c_size_t)], ct.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -208,6 +209,13 @@ def osscir_info(h):
     P, Lr, E = ct.c_int(), ct.c_int(), ct.c_int()
     _check("osscir_info", load().osscir_info(ct.c_void_p(h), ct.byref(P), ct.byref(Lr), ct.byref(E)))
     return P.value, Lr.value, E.value
+
+
+def osscir_memory(h):
+    """(device bytes of the context, bytes of its footprint tables)."""
+    d, t = ct.c_size_t(), ct.c_size_t()
+    _check("osscir_memory", load().osscir_memory(ct.c_void_p(h), ct.byref(d), ct.byref(t)))
+    return d.value, t.value
 
 
 def osscir_forward(h, x, g, stream=None):

@@ -54,7 +54,8 @@ void free_ctx(osscir_ctx* h) {
     void* ptrs[] = {h->rec,     h->r64,    h->views,     h->chord,    h->exc_off,    h->exc_ent,  h->s4,
                     h->N4,      h->mu,     h->mu_in,     h->g,        h->c,          h->y,        h->x,
                     h->xbar,    h->xo,     h->dtpl_part, h->dtpl_out, h->bad_counts, h->model,    h->fwd_row,
-                    h->fwd_cnt, h->fwd_pairs, h->bp_span, h->bp_row,  h->bp_cnt,   h->bp_pairs, h->bp_part};
+                    h->fwd_cnt, h->fwd_pairs, h->bp_span, h->bp_row,  h->bp_cnt,   h->bp_w,
+                    h->bp_slot, h->bp_roff,   h->bp_rays, h->bp_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -189,7 +190,7 @@ osscir_status validate(const osscir_geometry* g, const osscir_spectra* sp, const
     for (int i = 0; i < 3 * nE; ++i)   // a transformed basis (mu-PC) may have negative curves
         if (!std::isfinite(mu[i])) return OSSCIR_E_INVALID;
     if (!finite_pos(pa->lambda) || !(pa->lambda < 3.0e38)) return OSSCIR_E_INVALID;
-    if (pa->model != 0 && pa->model != 1) return OSSCIR_E_INVALID;
+    if (pa->model < 0 || pa->model > 3) return OSSCIR_E_INVALID;
     if (pa->spc < 0 || pa->spc > 2) return OSSCIR_E_INVALID;
     if (pa->spc == 2) {
         double M[9];
@@ -327,7 +328,8 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
 }
 
 void free_tables(osscir_ctx* h) {
-    void* ptrs[] = {h->fwd_row, h->fwd_cnt, h->fwd_pairs, h->bp_span, h->bp_row, h->bp_cnt, h->bp_pairs, h->bp_part};
+    void* ptrs[] = {h->fwd_row, h->fwd_cnt, h->fwd_pairs, h->bp_span, h->bp_row, h->bp_cnt,
+                    h->bp_w,    h->bp_slot, h->bp_roff,   h->bp_rays, h->bp_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->fwd_row = nullptr;
@@ -336,7 +338,10 @@ void free_tables(osscir_ctx* h) {
     h->bp_span = nullptr;
     h->bp_row = nullptr;
     h->bp_cnt = nullptr;
-    h->bp_pairs = nullptr;
+    h->bp_w = nullptr;
+    h->bp_slot = nullptr;
+    h->bp_roff = nullptr;
+    h->bp_rays = nullptr;
     h->bp_part = nullptr;
     h->bytes -= h->fp_bytes;
     h->fp_bytes = 0;
@@ -405,24 +410,53 @@ osscir_status build_tables(osscir_ctx* h) {
     CKT(cudaMemcpyAsync(span.data(), h->bp_span, sizeof(uint32_t) * span.size(), cudaMemcpyDeviceToHost, st));
     CKT(cudaStreamSynchronize(st));
     int chunk = 0, slots = 0;
+    auto group_range = [&](int g, int& v0, int& v1) {
+        v0 = std::min(C.n_views, g * per);
+        v1 = std::min(C.n_views, v0 + per);
+    };
     for (int cand = kBTMaxChunk; cand >= 1 && !chunk; cand /= 2) {
         int most = 0;
         for (int t = 0; t < n_t; ++t)
-            for (int g = 0; g < G; ++g)
-                for (int u0 = std::min(C.n_views, g * per); u0 < std::min(C.n_views, (g + 1) * per); u0 += cand) {
+            for (int g = 0; g < G; ++g) {
+                int v0, v1;
+                group_range(g, v0, v1);
+                for (int u0 = v0; u0 < v1; u0 += cand) {
                     int sum = 0;
-                    for (int u = u0; u < std::min({C.n_views, (g + 1) * per, u0 + cand}); ++u)
+                    for (int u = u0; u < std::min(v1, u0 + cand); ++u)
                         sum += (int)(span[(size_t)t * C.n_views + u] >> 16);
                     most = std::max(most, sum);
                 }
-        if ((size_t)most * 6 * sizeof(float4) <= 48 * 1024) {
+            }
+        const int padded = (most + 3) / 4 * 4;   // stage buffers of 44-byte slots stay 16-byte aligned
+        if (fpb_stage_bytes(padded) <= 48 * 1024) {
             chunk = cand;
-            slots = most;
+            slots = padded;
         }
     }
     if (chunk > 0) {
         const int nch = (per + chunk - 1) / chunk;
         const size_t n_e = (size_t)n_t * G * nch;
+        // each entry's staged rays, view after view, in slot order
+        std::vector<uint32_t> roff(n_e + 1, 0);
+        std::vector<int> rays;
+        for (int t = 0; t < n_t; ++t)
+            for (int g = 0; g < G; ++g) {
+                int v0, v1;
+                group_range(g, v0, v1);
+                for (int c = 0; c < nch; ++c) {
+                    roff[((size_t)t * G + g) * nch + c] = (uint32_t)rays.size();
+                    const int u0 = std::min(v1, v0 + c * chunk), u1 = std::min(v1, u0 + chunk);
+                    for (int u = u0; u < u1; ++u) {
+                        const uint32_t sp = span[(size_t)t * C.n_views + u];
+                        for (uint32_t i = 0; i < (sp >> 16); ++i) rays.push_back(u * C.n_bins + (int)(sp & 0xffffu) + (int)i);
+                    }
+                }
+            }
+        roff[n_e] = (uint32_t)rays.size();
+        CKT(dalloc(&h->bp_roff, n_e + 1));
+        CKT(dalloc(&h->bp_rays, rays.size()));
+        CKT(cudaMemcpyAsync(h->bp_roff, roff.data(), sizeof(uint32_t) * (n_e + 1), cudaMemcpyHostToDevice, st));
+        CKT(cudaMemcpyAsync(h->bp_rays, rays.data(), sizeof(int) * rays.size(), cudaMemcpyHostToDevice, st));
         CKT(dalloc(&h->bp_cnt, n_e * kBTThreads));
         CKT(dalloc(&h->bp_row, n_e * (kBTThreads / 32) + 1));
         CKT(launch_fpb_count(C, h->exc(), h->rec, h->views, G, chunk, nch, h->bp_cnt, h->bp_row, st));
@@ -430,11 +464,14 @@ osscir_status build_tables(osscir_ctx* h) {
         std::vector<uint32_t> brow(n_w + 1, 0);
         CKT(cudaMemcpyAsync(brow.data(), h->bp_row, sizeof(uint32_t) * n_w, cudaMemcpyDeviceToHost, st));
         CKT(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < n_w; ++i) brow[i] = (brow[i] + 1) & ~1u;   // even: entries are read two at a time
         if (!prefix_rows(brow, n_w)) return fail(cudaErrorMemoryAllocation);
         CKT(cudaMemcpyAsync(h->bp_row, brow.data(), sizeof(uint32_t) * (n_w + 1), cudaMemcpyHostToDevice, st));
-        CKT(dalloc(&h->bp_pairs, (size_t)brow[n_w] * 32));
+        CKT(dalloc(&h->bp_w, (size_t)brow[n_w] * 32));
+        CKT(dalloc(&h->bp_slot, (size_t)brow[n_w] * 32));
         CKT(dalloc(&h->bp_part, (size_t)G * 9 * h->P));
-        CKT(launch_fpb_fill(C, h->exc(), h->rec, h->views, h->bp_span, G, chunk, nch, h->bp_row, h->bp_pairs, st));
+        CKT(launch_fpb_fill(C, h->exc(), h->rec, h->views, h->bp_span, G, chunk, nch, h->bp_row, h->bp_w,
+                            h->bp_slot, st));
         h->bp_chunk = chunk;
         h->bp_nch = nch;
         h->bp_slots = slots;
@@ -602,6 +639,13 @@ osscir_status osscir_info(osscir_t h, int* n_pixels, int* n_rays, int* n_fp64_pa
     if (n_pixels) *n_pixels = h->P;
     if (n_rays) *n_rays = h->L;
     if (n_fp64_pairs) *n_fp64_pairs = h->exc_n;
+    return OSSCIR_OK;
+}
+
+osscir_status osscir_memory(osscir_t h, size_t* device_bytes, size_t* table_bytes) {
+    if (!h) return OSSCIR_E_INVALID;
+    if (device_bytes) *device_bytes = h->bytes;
+    if (table_bytes) *table_bytes = h->fp_state == 1 ? h->fp_bytes : 0;
     return OSSCIR_OK;
 }
 

@@ -704,12 +704,23 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
                 for (int w = 0; w < 4; ++w)
                     for (int j = 0; j < 4; ++j) Bm[w][j] = 0.0f;
             }
+        } else if (P.model == 3) {   // W = diag(c): y'_w = r_w + c_w sinv_w / (c_w sinv_w + 1) (y_w - r_w)
+            sigma_inv();
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const float cs = cv[w] * sinv[w], f = cs / (cs + 1.0f);
+                yo[w] = df_f(df_add(rw[w], df_mulf(df_sub(dfl{y[w], 0.0f}, rw[w]), f)));
+                if (KEEP)
+                    for (int j = 0; j < 4; ++j) Bm[w][j] = j == w ? f : 0.0f;
+            }
         } else {
-            // sum_i beta_i mu_i mu_i^T = sum_w (r_w / D_w) U_w
+            // model 0: sum_i beta_i mu_i mu_i^T = sum_w (r_w / D_w) U_w is subtracted from
+            // sum_w c_w alpha_w alpha_w^T; model 2 (Gauss-Newton) keeps the first term alone
             float Bt[6];
 #pragma unroll
             for (int k = 0; k < 6; ++k)
-                Bt[k] = fmaf(qw[3], U[3][k], fmaf(qw[2], U[2][k], fmaf(qw[1], U[1][k], qw[0] * U[0][k])));
+                Bt[k] = P.model == 2 ? 0.0f
+                                     : fmaf(qw[3], U[3][k], fmaf(qw[2], U[2][k], fmaf(qw[1], U[1][k], qw[0] * U[0][k])));
             sigma_inv();
             ray_dual<KEEP>(al, sinv, cv, rw, Bt, y, yo, Bm);
         }
@@ -1102,8 +1113,9 @@ __global__ void __launch_bounds__(kFwdThreads) k_fp_fwd_fill(GeomC C, ExcTable E
     });
 }
 
-// a1 from the forward table: the same line sums as proj_ray, in the same order,
-// with four pairs (and their gathers of xbar) in flight per step.
+// a1 from the forward table: the same line sums as proj_ray, in the same order.
+// The table is read four entries at a time, the next four loaded while the
+// current four's gathers of xbar are added, so a table load is always in flight.
 __global__ void __launch_bounds__(kFwdThreads, 8) k_fp_proj(GeomC C, FpTables T, SolveD D, int v0, int v1) {
     const int bx = centre_out(blockIdx.y, gridDim.y);
     const int l = ray_in_views(C, bx, blockIdx.x, kFwdThreads / 32, v0, v1);
@@ -1113,16 +1125,24 @@ __global__ void __launch_bounds__(kFwdThreads, 8) k_fp_proj(GeomC C, FpTables T,
     const int n = __ldg(T.fwd_cnt + l);
     LineSum acc;
     int j = 0;
-    for (; j + 3 < n; j += 4) {
+    if (n >= 4) {
         int2 a[4];
-        float4 x[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) a[u] = __ldg(p + 32 * u);
+        for (; j + 3 < n; j += 4) {
+            p += 128;
+            int2 nx[4];
+            const bool more = j + 7 < n;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) x[u] = __ldg(D.xbar + a[u].x);
+            for (int u = 0; u < 4; ++u) nx[u] = more ? __ldg(p + 32 * u) : make_int2(0, 0);
+            float4 x[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc.add(__int_as_float(a[u].y), x[u]);
-        p += 128;
+            for (int u = 0; u < 4; ++u) x[u] = __ldg(D.xbar + a[u].x);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc.add(__int_as_float(a[u].y), x[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = nx[u];
+        }
     }
     for (; j < n; ++j, p += 32) {
         const int2 a = __ldg(p);
@@ -1259,7 +1279,8 @@ __global__ void __launch_bounds__(kBTThreads) k_fpb_count(GeomC C, ExcTable E, c
 __global__ void __launch_bounds__(kBTThreads) k_fpb_fill(GeomC C, ExcTable E, const RayRec* rec,
                                                          const ViewF* views, const uint32_t* __restrict__ span,
                                                          int G, int chunk, int nch,
-                                                         const uint32_t* __restrict__ bp_row, int2* pairs) {
+                                                         const uint32_t* __restrict__ bp_row, float* bp_w,
+                                                         uint16_t* bp_slot) {
     const int b = blockIdx.x, t = b / G, g = b % G, tid = threadIdx.x, lane = tid & 31;
     int ix, iy;
     bt_pixel(C.grid.n, t, tid, ix, iy);
@@ -1275,91 +1296,123 @@ __global__ void __launch_bounds__(kBTThreads) k_fpb_fill(GeomC C, ExcTable E, co
         pixel_pairs(C, E, rec, views, ix, iy, u0, u1, [&](int l, float w) {
             const int u = l / C.n_bins, i = u - u0;
             const int slot = off[i] + (l - u * C.n_bins) - tlo[i];
-            pairs[(row + j) * 32 + lane] = make_int2(slot, __float_as_int(w));
+            const size_t at = (row + (j & ~1)) * 32 + 2 * lane + (j & 1);   // entries j, j + 1 side by side
+            bp_w[at] = w;
+            bp_slot[at] = (uint16_t)slot;
             ++j;
         });
     }
 }
 
-// Stage chunk views [u0, u1) of tile t (the rays of bp_span) into the buffer:
-// each slot gets the ray's r1 (b0, b1 in .zw) and its step half.
-__device__ __forceinline__ void stage_chunk(const GeomC& C, const FpTables& T, const RayRec* rec, const RayStep* steps,
-                                            int t, int u0, int u1, float4* s_r1, float4* s_s0, float4* s_s1) {
-    int off[kBTMaxChunk], tlo[kBTMaxChunk], wid[kBTMaxChunk];
-    const int total = chunk_offsets(T.bp_span, t, C.n_views, u0, u1, off, tlo, wid);
-    for (int r = threadIdx.x; r < total; r += kBTThreads) {
-        int i = 0;
-#pragma unroll
-        for (int q = 1; q < kBTMaxChunk; ++q)
-            if (q < u1 - u0 && r >= off[q]) i = q;
-        const int l = (u0 + i) * C.n_bins + tlo[i] + (r - off[i]);
-        cp_async16(s_r1 + r, &rec[l].r1);
-        cp_async16(s_s0 + r, &steps[l].s0);
-        cp_async16(s_s1 + r, &steps[l].s1);
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// One stage buffer of S slots: the step halves (b2 and S in s0.x..s1.z), b0 and
+// b1 (the .zw of the weight half), and the ray index of each slot.
+struct StageBuf {
+    float4* s0;
+    float4* s1;
+    float2* b01;
+    int* ray;
+    __device__ StageBuf(float4* base, int S)
+        : s0(base), s1(base + S), b01(reinterpret_cast<float2*>(base + 2 * S)),
+          ray(reinterpret_cast<int*>(reinterpret_cast<float2*>(base + 2 * S) + S)) {}
+};
+// float4 units per stage buffer of S slots (S a multiple of 4: 44 S bytes).
+__host__ __device__ __forceinline__ int stage_f4(int S) { return (44 * S) / 16; }
+
+// Stage entry e's rays (bp_rays[bp_roff[e] ..]) into the buffer, asynchronously.
+__device__ __forceinline__ void stage_entry(const FpTables& T, const RayRec* rec, const RayStep* steps, size_t e,
+                                            StageBuf B) {
+    const uint32_t r0 = __ldg(T.bp_roff + e), nr = __ldg(T.bp_roff + e + 1) - r0;
+    for (uint32_t r = threadIdx.x; r < nr; r += kBTThreads) {
+        const int l = __ldg(T.bp_rays + r0 + r);
+        cp_async16(B.s0 + r, &steps[l].s0);
+        cp_async16(B.s1 + r, &steps[l].s1);
+        cp_async8(B.b01 + r, &rec[l].r1.z);
+        B.ray[r] = l;
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
+// The nine channels of one pair from a stage slot.
+__device__ __forceinline__ void bp_accumulate_slot(float acc[9], float w, const StageBuf& B, int s) {
+    const float2 b = B.b01[s];
+    const float4 s0 = B.s0[s], s1 = B.s1[s];
+    acc[0] = fmaf(w, b.x, acc[0]);
+    acc[1] = fmaf(w, b.y, acc[1]);
+    acc[2] = fmaf(w, s0.x, acc[2]);
+    acc[3] = fmaf(w, s0.y, acc[3]);
+    acc[4] = fmaf(w, s0.z, acc[4]);
+    acc[5] = fmaf(w, s0.w, acc[5]);
+    acc[6] = fmaf(w, s1.x, acc[6]);
+    acc[7] = fmaf(w, s1.y, acc[7]);
+    acc[8] = fmaf(w, s1.z, acc[8]);
+}
+
 // a6 from the blocked table: each pixel's nine channels over its group's views,
 // written to part ([G][9][P]); k_fpb_finish adds the groups and takes the step.
-// PARTIAL: only the views [V0, V1) (one GPU's share of a split solve).
+// The chunks go through two stage buffers: chunk c + 1 is copied while chunk c
+// is summed.  PARTIAL: only the rays of the views [V0, V1) (one GPU's share of a
+// split solve).
 template <bool PARTIAL>
 __global__ void __launch_bounds__(kBTThreads) k_fpb_bp(GeomC C, FpTables T, const RayRec* rec, int V0, int V1,
                                                        float* part) {
-    extern __shared__ float4 bt_smem[];   // two buffers of [3][bp_slots] float4
+    extern __shared__ float4 bt_smem[];   // two stage buffers
     const int G = T.bp_groups, b = blockIdx.x, t = b / G, g = b % G, tid = threadIdx.x, lane = tid & 31;
-    const int S = T.bp_slots, nch = T.bp_nch, chunk = T.bp_chunk, nb = C.n_bins;
+    const int S = T.bp_slots, nch = T.bp_nch, nb = C.n_bins;
     int ix, iy;
     bt_pixel(C.grid.n, t, tid, ix, iy);
     const bool valid = ix < C.grid.n && iy < C.grid.n;
     const RayStep* steps = ray_steps(rec, C.n_views * nb);
+    const int l_lo = V0 * nb, l_hi = V1 * nb;
     float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int u0, u1;
-    chunk_views(C.n_views, g, G, chunk, 0, u0, u1);
-    if (nch > 0) stage_chunk(C, T, rec, steps, t, u0, u1, bt_smem, bt_smem + S, bt_smem + 2 * S);
+    const size_t e0 = (size_t)b * nch;
+    const StageBuf B0(bt_smem, S), B1(bt_smem + stage_f4(S), S);
+    if (nch > 0) stage_entry(T, rec, steps, e0, B0);
     for (int c = 0; c < nch; ++c) {
-        float4* buf = bt_smem + (size_t)(c & 1) * 3 * S;
-        int n0, n1;
-        chunk_views(C.n_views, g, G, chunk, c, n0, n1);
+        const StageBuf& B = (c & 1) ? B1 : B0;
         if (c + 1 < nch) {   // the next chunk into the other buffer (free since the barrier ending chunk c - 1)
-            int w0, w1;
-            chunk_views(C.n_views, g, G, chunk, c + 1, w0, w1);
-            float4* nbuf = bt_smem + (size_t)((c + 1) & 1) * 3 * S;
-            stage_chunk(C, T, rec, steps, t, w0, w1, nbuf, nbuf + S, nbuf + 2 * S);
+            stage_entry(T, rec, steps, e0 + c + 1, (c & 1) ? B0 : B1);
             asm volatile("cp.async.wait_group 1;" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();   // chunk c staged by every thread
-        int s_lo = 0, s_hi = 1 << 30;   // stage slots of the views [V0, V1) (PARTIAL)
-        if (PARTIAL) {
-            int off[kBTMaxChunk], tlo[kBTMaxChunk], wid[kBTMaxChunk];
-            const int total = chunk_offsets(T.bp_span, t, C.n_views, n0, n1, off, tlo, wid);
-            const int i0 = min(max(V0 - n0, 0), n1 - n0), i1 = min(max(V1 - n0, 0), n1 - n0);
-            s_lo = i0 < n1 - n0 ? off[i0] : total;
-            s_hi = i1 < n1 - n0 ? off[i1] : total;
-        }
-        const size_t e = (size_t)b * nch + c;
+        const size_t e = e0 + c;
         const int n = __ldg(T.bp_cnt + e * kBTThreads + tid);
-        const int2* p = T.bp_pairs + (size_t)__ldg(T.bp_row + e * (kBTThreads / 32) + (tid >> 5)) * 32 + lane;
-        const float4 *r1 = buf, *s0 = buf + S, *s1 = buf + 2 * S;
+        const size_t row = __ldg(T.bp_row + e * (kBTThreads / 32) + (tid >> 5));   // even
+        const float2* wp = reinterpret_cast<const float2*>(T.bp_w + row * 32) + lane;
+        const ushort2* sp = reinterpret_cast<const ushort2*>(T.bp_slot + row * 32) + lane;
         int j = 0;
-        for (; j + 3 < n; j += 4) {
-            int2 a[4];
+        for (; j + 7 < n; j += 8) {   // eight table entries (four loads of two) in flight
+            float2 w[4];
+            ushort2 sl[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) a[q] = __ldg(p + 32 * q);
+            for (int q = 0; q < 4; ++q) {
+                w[q] = __ldg(wp + 32 * q);
+                sl[q] = __ldg(sp + 32 * q);
+            }
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (!PARTIAL || (a[q].x >= s_lo && a[q].x < s_hi))
-                    bp_accumulate(acc, __int_as_float(a[q].y), r1[a[q].x], s0[a[q].x], s1[a[q].x]);
-            p += 128;
+            for (int q = 0; q < 4; ++q) {
+                if (!PARTIAL || (B.ray[sl[q].x] >= l_lo && B.ray[sl[q].x] < l_hi))
+                    bp_accumulate_slot(acc, w[q].x, B, sl[q].x);
+                if (!PARTIAL || (B.ray[sl[q].y] >= l_lo && B.ray[sl[q].y] < l_hi))
+                    bp_accumulate_slot(acc, w[q].y, B, sl[q].y);
+            }
+            wp += 128;
+            sp += 128;
         }
-        for (; j < n; ++j, p += 32) {
-            const int2 a = __ldg(p);
-            if (!PARTIAL || (a.x >= s_lo && a.x < s_hi))
-                bp_accumulate(acc, __int_as_float(a.y), r1[a.x], s0[a.x], s1[a.x]);
+        for (; j < n; j += 2, wp += 32, sp += 32) {
+            const float2 w = __ldg(wp);
+            const ushort2 sl = __ldg(sp);
+            if (!PARTIAL || (B.ray[sl.x] >= l_lo && B.ray[sl.x] < l_hi)) bp_accumulate_slot(acc, w.x, B, sl.x);
+            if (j + 1 < n && (!PARTIAL || (B.ray[sl.y] >= l_lo && B.ray[sl.y] < l_hi)))
+                bp_accumulate_slot(acc, w.y, B, sl.y);
         }
-        __syncthreads();   // buffer c & 1 is read by everyone before chunk c + 2 overwrites it
+        __syncthreads();   // this buffer is read by everyone before chunk c + 2 overwrites it
     }
     if (valid) {
         const size_t P_ = (size_t)C.grid.n * C.grid.n, k = (size_t)iy * C.grid.n + ix;
@@ -1539,7 +1592,7 @@ cudaError_t launch_mocca_ray_inner(const GeomC& C, RayRec* rec, const SolveD& D,
 template <bool PARTIAL>
 cudaError_t launch_fpb(const GeomC& C, const FpTables& T, const RayRec* rec, const StepParams& P, const SolveD& D,
                        int v0, int v1, float* chan, cudaStream_t st) {
-    const size_t smem = sizeof(float4) * 6 * (size_t)T.bp_slots;
+    const size_t smem = sizeof(float4) * 2 * (size_t)stage_f4(T.bp_slots);
     k_fpb_bp<PARTIAL><<<bt_tiles(C.grid.n) * T.bp_groups, kBTThreads, smem, st>>>(C, T, rec, v0, v1, T.bp_part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1549,7 +1602,7 @@ cudaError_t launch_fpb(const GeomC& C, const FpTables& T, const RayRec* rec, con
 
 cudaError_t launch_mocca_bp(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
                             const StepParams& P, const SolveD& D, cudaStream_t st, const FpTables* T) {
-    if (T && T->bp_pairs) return launch_fpb<false>(C, *T, rec, P, D, 0, C.n_views, nullptr, st);
+    if (T && T->bp_w) return launch_fpb<false>(C, *T, rec, P, D, 0, C.n_views, nullptr, st);
     const int G = bp_view_groups(C.grid.n * C.grid.n, C.n_views);
     dim3 grid(blocks(C.grid.n, kBpPixX), blocks(C.grid.n, kBpPixY)), blk(kBpPixX, kBpPixY, G);
     const size_t smem = sizeof(float) * (size_t)(G - 1) * 9 * kBpPix;
@@ -1560,7 +1613,7 @@ cudaError_t launch_mocca_bp(const GeomC& C, const ExcTable& E, const RayRec* rec
 cudaError_t launch_mocca_bp_partial(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
                                     const StepParams& P, const SolveD& D, int v0, int v1, float* chan,
                                     cudaStream_t st, const FpTables* T) {
-    if (T && T->bp_pairs) return launch_fpb<true>(C, *T, rec, P, D, v0, v1, chan, st);
+    if (T && T->bp_w) return launch_fpb<true>(C, *T, rec, P, D, v0, v1, chan, st);
     const int G = bp_view_groups(C.grid.n * C.grid.n, v1 - v0);
     dim3 grid(blocks(C.grid.n, kBpPixX), blocks(C.grid.n, kBpPixY)), blk(kBpPixX, kBpPixY, G);
     const size_t smem = sizeof(float) * (size_t)(G - 1) * 9 * kBpPix;
@@ -1592,11 +1645,14 @@ cudaError_t launch_fpb_count(const GeomC& C, const ExcTable& E, const RayRec* re
 }
 
 cudaError_t launch_fpb_fill(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
-                            const uint32_t* span, int G, int chunk, int nch, const uint32_t* bp_row, int2* pairs,
-                            cudaStream_t st) {
-    k_fpb_fill<<<bt_tiles(C.grid.n) * G, kBTThreads, 0, st>>>(C, E, rec, views, span, G, chunk, nch, bp_row, pairs);
+                            const uint32_t* span, int G, int chunk, int nch, const uint32_t* bp_row, float* bp_w,
+                            uint16_t* bp_slot, cudaStream_t st) {
+    k_fpb_fill<<<bt_tiles(C.grid.n) * G, kBTThreads, 0, st>>>(C, E, rec, views, span, G, chunk, nch, bp_row, bp_w,
+                                                               bp_slot);
     return cudaGetLastError();
 }
+
+int fpb_stage_bytes(int slots) { return 2 * 16 * stage_f4(slots); }
 
 cudaError_t launch_mocca_apply(const GeomC& C, const StepParams& P, const SolveD& D, const float* chan,
                                cudaStream_t st) {

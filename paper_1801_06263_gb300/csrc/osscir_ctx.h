@@ -58,13 +58,16 @@ struct osscir_ctx {
     uint32_t* bp_span = nullptr;
     uint32_t* bp_row = nullptr;
     uint16_t* bp_cnt = nullptr;
-    int2* bp_pairs = nullptr;   // null: the back-projection stays on the fly
+    float* bp_w = nullptr;   // null: the back-projection stays on the fly
+    uint16_t* bp_slot = nullptr;
+    uint32_t* bp_roff = nullptr;
+    int* bp_rays = nullptr;
     float* bp_part = nullptr;
     int bp_groups = 1, bp_chunk = 0, bp_nch = 0, bp_slots = 0;
     size_t fp_bytes = 0;
     osscir::FpTables fp() const {
-        return osscir::FpTables{fwd_row, fwd_cnt, fwd_pairs, bp_span,  bp_row,   bp_cnt,
-                                bp_pairs, bp_part, bp_groups, bp_chunk, bp_nch, bp_slots};
+        return osscir::FpTables{fwd_row, fwd_cnt, fwd_pairs, bp_span, bp_row,    bp_cnt,   bp_w,
+                                bp_slot, bp_roff, bp_rays,   bp_part, bp_groups, bp_chunk, bp_nch, bp_slots};
     }
     const osscir::FpTables* fp_or_null() const { return fp_state == 1 ? &fp_tab : nullptr; }
     osscir::FpTables fp_tab{};

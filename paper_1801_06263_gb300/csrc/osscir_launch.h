@@ -32,7 +32,7 @@ struct SpecD {
 // MOCCA per-solve parameters.
 struct StepParams {
     float lambda;
-    int model;       // 0: eigen-clipped Hessian, 1: W = 0
+    int model;       // 0: eigen-clipped Hessian, 1: W = 0, 2: Gauss-Newton sum_w c_w a_w a_w^T, 3: W = diag(c)
     int spc;         // 0: m-block-diagonal SPC, 1: diagonal SPC
     int use_box;
     float lo[3], hi[3];
@@ -64,7 +64,7 @@ constexpr int kBpPix = kBpPixX * kBpPixY;
 constexpr int kBpMaxThreads = 512;                    // kBpPix x up to 8 view groups
 // Blocked back-projection table: a block is a tile of kBTX x kBTY pixels (one
 // per thread) and one view group; its views go in chunks of at most kBTMaxChunk.
-constexpr int kBTX = 16, kBTY = 16, kBTThreads = kBTX * kBTY, kBTMaxChunk = 8;
+constexpr int kBTX = 16, kBTY = 16, kBTThreads = kBTX * kBTY, kBTMaxChunk = 16;
 inline int bt_tiles(int n) { return ((n + kBTX - 1) / kBTX) * ((n + kBTY - 1) / kBTY); }
 
 // Footprint tables of one geometry: the pairs (l, k) of X with their weights,
@@ -78,11 +78,13 @@ inline int bt_tiles(int n) { return ((n + kBTX - 1) / kBTX) * ((n + kBTY - 1) / 
 //   bp_groups); the group's views (the split of k_mocca_bp) in chunks of
 //   bp_chunk views, bp_nch chunks per group, entry e = b bp_nch + c.  bp_span
 //   [t n_views + u] = tlo | span << 16: the union of the tile's candidate bins in
-//   view u; a chunk's rays are staged view after view, ray (u, tlo + i) at slot
-//   (sum of the earlier views' spans) + i, at most bp_slots slots.  Thread r's
-//   j-th pair of entry e (stage slot, weight bits) is bp_pairs[(bp_row[8 e + r /
-//   32] + j) 32 + r % 32], bp_cnt[256 e + r] pairs, in the order of
-//   bp_pixel_sum.  bp_part: [G][9][P] scratch for the groups' channel sums.
+//   view u.  An entry's rays, view after view (ray (u, tlo + i)), are its stage
+//   slots: bp_rays[bp_roff[e] + slot], at most bp_slots of them.  Thread r's
+//   pairs (stage slot, weight) of entry e, bp_cnt[256 e + r] of them in the order
+//   of bp_pixel_sum, go two per slot row: pair j at (bp_slot, bp_w)[(row + j - j
+//   mod 2) 32 + 2 (r mod 32) + j mod 2], row = bp_row[8 e + r / 32] (the rows of
+//   a warp are even in number, so that a lane reads two pairs with one load).
+//   bp_part: [G][9][P] scratch for the groups' channel sums.
 struct FpTables {
     const uint32_t* fwd_row;   // [n_views nbg + 1]
     const int* fwd_cnt;        // [L]
@@ -90,10 +92,15 @@ struct FpTables {
     const uint32_t* bp_span;   // [bt_tiles(n) n_views]
     const uint32_t* bp_row;    // [n_entries 8 + 1]
     const uint16_t* bp_cnt;    // [n_entries 256]
-    const int2* bp_pairs;      // null: the back-projection is computed on the fly
+    const float* bp_w;         // null: the back-projection is computed on the fly
+    const uint16_t* bp_slot;
+    const uint32_t* bp_roff;   // [n_entries + 1]
+    const int* bp_rays;
     float* bp_part;            // [bp_groups][9][P]
     int bp_groups, bp_chunk, bp_nch, bp_slots;
 };
+// Shared memory of the blocked back-projection's two stage buffers of `slots` slots.
+int fpb_stage_bytes(int slots);
 
 // View groups per pixel for the MOCCA back-projection: enough threads to fill
 // the GPU several times over, at most 8, and at least one view per group.
@@ -149,8 +156,8 @@ cudaError_t launch_fpb_span(const GeomC& C, const ViewF* views, uint32_t* span, 
 cudaError_t launch_fpb_count(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views, int G,
                              int chunk, int nch, uint16_t* cnt, uint32_t* warp_rows, cudaStream_t st);
 cudaError_t launch_fpb_fill(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
-                            const uint32_t* span, int G, int chunk, int nch, const uint32_t* bp_row, int2* pairs,
-                            cudaStream_t st);
+                            const uint32_t* span, int G, int chunk, int nch, const uint32_t* bp_row, float* bp_w,
+                            uint16_t* bp_slot, cudaStream_t st);
 cudaError_t launch_mocca_apply(const GeomC& C, const StepParams& P, const SolveD& D, const float* chan,
                                cudaStream_t st);
 

@@ -189,3 +189,28 @@ def test_static_dtpl_wrapper_rejects_mismatched_tensors():
         _lib.osscir_dtpl_counts_static(a, a, out)
     with pytest.raises(ValueError):            # [L, 3] is not the [L, 4] counts layout
         _lib.osscir_dtpl_counts_static(a[:, :3], a[:, :3], out)
+
+
+def test_memory_query_rejects_null(lib):
+    d, t = ct.c_size_t(), ct.c_size_t()
+    assert lib.osscir_memory(ct.c_void_p(0), ct.byref(d), ct.byref(t)) == _lib.OSSCIR_E_INVALID
+
+
+@pytest.mark.gpu
+def test_footprint_tables_are_built_before_the_first_iteration():
+    torch, g, sp, h = _small_context(1e-6)
+    try:
+        dev0, tab0 = _lib.osscir_memory(h)
+        assert tab0 == 0 and dev0 > 0
+        c = torch.full((g.n_rays, 4), 100.0, dtype=torch.float32, device="cuda")
+        _lib.osscir_set_counts(h, c)
+        _lib.osscir_mocca_step(h, 1)
+        torch.cuda.synchronize()
+        dev1, tab1 = _lib.osscir_memory(h)
+        # at least the forward pairs: 8 bytes per footprint pair
+        cnt = torch.zeros(g.n_rays, dtype=torch.int32, device="cuda")
+        _lib.osscir_footprint_rays(h, 0, g.n_rays, 0, cnt, None, None)
+        assert tab1 >= 8 * int(cnt.sum().item())
+        assert dev1 == dev0 + tab1
+    finally:
+        _lib.osscir_destroy(h)

@@ -74,12 +74,13 @@ def test_one_iteration_from_random_state(orc):
     R.close()
 
 
-@pytest.mark.parametrize("model", ["hessian", "gradient"])
+@pytest.mark.parametrize("model", ["hessian", "gradient", "gauss_newton", "separable"])
 def test_small_64_iterates_match_oracle(orc, small, model):
     w, s32, c = small
     # the zero-curvature variant takes larger dual steps and needs a smaller step ratio
-    lam, n_it = (1e-7, 200) if model == "hessian" else (3e-8, 60)
-    R = _recon(w, lam, model=0 if model == "hessian" else 1)
+    lam, n_it = {"hessian": (1e-7, 200), "gradient": (3e-8, 60), "gauss_newton": (1e-7, 100),
+                 "separable": (1e-7, 100)}[model]
+    R = _recon(w, lam, model=orc.MODELS[model])
     R.set_counts(torch.tensor(c, device="cuda"))
     R.step(n_it)
     x = R.maps().cpu().double().numpy()[:, :3]

@@ -81,6 +81,18 @@ def test_dual_step_without_curvature_returns_residual(orc):
                                rtol=1e-14, atol=1e-12)
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_separable_dual_step_is_the_windowwise_prox(orc, seed):
+    """W = diag(c) makes the 4 x 4 prox separable: y'_w = r_w + c_w / (c_w + sigma_w) (y_w - r_w),
+    sigma_w = 1 / (Sigma^-1)_w, which the oracle's general solve must reproduce."""
+    rng = np.random.default_rng(20 + seed)
+    alpha, H, r, sinv, y = _ray(rng)
+    c = rng.uniform(10.0, 1e5, size=4)
+    yp = orc.dual_update(alpha, np.zeros((3, 3)), r, sinv, y, model="separable", c=c)
+    sig = 1.0 / sinv
+    np.testing.assert_allclose(yp, r + c / (c + sig) * (y - r), rtol=1e-12, atol=1e-12 * np.abs(y).max())
+
+
 def test_dual_step_keeps_rays_outside_the_image(orc):
     rng = np.random.default_rng(8)
     alpha, H, r, sinv, y = _ray(rng)

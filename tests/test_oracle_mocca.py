@@ -243,3 +243,29 @@ def test_inner_one_is_the_single_loop(orc):
     a, ha = orc.mocca(geom, sp, c, 25, 1e-6)
     b, hb = orc.mocca(geom, sp, c, 25, 1e-6, inner=1)
     assert np.array_equal(a.x, b.x) and np.array_equal(a.y, b.y) and np.array_equal(ha, hb)
+
+
+def test_gauss_newton_curvature_equals_the_hessian_at_zero_residual(orc):
+    """The per-ray Hessian of Sec. 2 is sum_w c_w alpha_w alpha_w^T minus a term
+    weighted by the residual r = c - c^; with noiseless counts at the expansion
+    point (c = c^(f), xbar = f) that term vanishes, so one iteration with the
+    Gauss-Newton curvature (model 2) equals one with the clipped Hessian
+    (model 0, nothing to clip)."""
+    from paper_1801_06263_gb300 import inputs
+    geom = inputs.make_geometry(12, 0.5, 16, 14)
+    sp = inputs.make_spectra(geom.n_bins, 1e4)
+    f = inputs.disk_phantom(geom, radius_mm=2.5, insert_mm=0.6)
+    c = orc.counts(geom, sp, f)
+    y0 = np.random.default_rng(4).normal(scale=30.0, size=(geom.n_rays, 4))   # W acts on y - r = y
+    out = []
+    for model in ("hessian", "gauss_newton", "gradient"):
+        st = orc.State(geom)
+        st.x[:] = f
+        st.xbar[:] = f
+        st.y[:] = y0
+        st, _ = orc.mocca(geom, sp, c, 1, 1e-6, st, model=model)
+        out.append((st.x.copy(), st.y.copy()))
+    np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-9, atol=1e-9 * np.abs(out[0][1]).max())
+    np.testing.assert_allclose(out[1][0], out[0][0], rtol=1e-9, atol=1e-9 * np.abs(out[0][0]).max())
+    # and the curvature does act here: without it (W = 0) the step is different
+    assert np.abs(out[2][1] - out[0][1]).max() > 1e-3 * np.abs(out[0][1]).max()

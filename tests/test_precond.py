@@ -34,3 +34,11 @@ def test_mu_pc_of_orthonormal_curves_is_identity(orc):
     mu_t, M = orc.mu_pc(Q.T)
     np.testing.assert_allclose(M, np.eye(3), atol=1e-12)
     np.testing.assert_allclose(mu_t, Q.T, atol=1e-12)
+
+
+def test_weighted_mu_pc_is_orthonormal_in_its_inner_product(orc):
+    sp = inputs.make_spectra(8, 1e4)
+    phi = np.linspace(1.0, 3.0, sp.mu.shape[1])
+    mu_t, M = orc.mu_pc(sp.mu, weights=phi)
+    np.testing.assert_allclose((mu_t * phi) @ mu_t.T, np.eye(3), atol=1e-10)
+    np.testing.assert_allclose(M, M.T, rtol=0, atol=1e-12 * np.abs(M).max())
