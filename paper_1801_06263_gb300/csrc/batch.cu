@@ -60,7 +60,22 @@ SolveDesc make_desc(const osscir_ctx* h) {
     d.dtpl_out = h->dtpl_out + 1;
     d.n_part = h->n_part;
     d.bp_groups = bp_view_groups(h->P, h->g64.n_views);
+    d.T = h->fp_state == 1 ? h->fp() : FpTables{};
     return d;
+}
+
+// Whether every solve has its footprint tables (then the batch streams them;
+// otherwise all solves take the on-the-fly kernels).
+bool all_tables(const std::vector<osscir_ctx*>& ctx) {
+    for (const osscir_ctx* h : ctx)
+        if (h->fp_state != 1 || !h->bp_w) return false;
+    return !ctx.empty();
+}
+
+// Build the footprint tables of every solve that has none yet.
+osscir_status build_all_tables(const std::vector<osscir_ctx*>& ctx) {
+    for (osscir_ctx* h : ctx) CKS(ctx_build_tables(h));
+    return OSSCIR_OK;
 }
 
 // Relative device time of one iteration of a solve: footprint pairs (~ rays x
@@ -72,28 +87,35 @@ double solve_cost(const osscir_ctx* h) {
 }
 
 // Items per solve and the relative cost of one item, for kernel k (0 projection,
-// 1 ray, 2 back-projection) under configuration c.
-void item_counts(const osscir_ctx* h, int k, const osscir_batch_config& c, int* count, double* cost) {
+// 1 ray, 2 back-projection, 3 the group sums after a table back-projection)
+// under configuration c; `tables`: the back-projection streams footprint tables.
+void item_counts(const osscir_ctx* h, int k, const osscir_batch_config& c, bool tables, int* count, double* cost) {
     const int nb = h->g64.n_bins, nv = h->g64.n_views, N = h->g64.n;
+    const int G = bp_view_groups(h->P, nv);
     if (k == 0) {
         *count = batch_proj_tiles(nb, nv, c.proj_views);
         *cost = (double)N;                       // pixels per ray ~ image side
     } else if (k == 1) {
         *count = batch_proj_tiles(nb, nv, kFwdThreads / 32);
         *cost = (double)h->nE;                   // energies per ray
-    } else {
-        const int G = bp_view_groups(h->P, nv);
+    } else if (k == 2 && tables) {
+        *count = bt_tiles(N) * G;                // (16 x 16 pixel tile, view group) blocks
+        *cost = (double)nv / G;
+    } else if (k == 2) {
         *count = batch_bp_items(N, c.bp_tile_x, G);
         *cost = (double)nv / G;                  // views per thread group
+    } else {
+        *count = tables ? (h->P + 255) / 256 : 0;
+        *cost = (double)G;
     }
 }
 
 // Work list of kernel k over solves [first, first + n) of the descriptor array.
 void build_items(const std::vector<osscir_ctx*>& ctx, int first, int n, int k, const osscir_batch_config& c,
-                 std::vector<int2>& out) {
+                 bool tables, std::vector<int2>& out) {
     std::vector<int> count(n);
     std::vector<double> cost(n);
-    for (int s = 0; s < n; ++s) item_counts(ctx[first + s], k, c, &count[s], &cost[s]);
+    for (int s = 0; s < n; ++s) item_counts(ctx[first + s], k, c, tables, &count[s], &cost[s]);
     const int order = k == 0 ? c.proj_order : (k == 1 ? c.ray_order : c.bp_order);
     out.clear();
     if (n == 0) return;
@@ -117,10 +139,12 @@ void build_items(const std::vector<osscir_ctx*>& ctx, int first, int n, int k, c
 // branch's three work lists, as one byte image.
 struct Plan {
     int branches = 1;
+    bool tables = false;              // the back-projection streams every solve's tables
+    size_t fpb_smem = 0;              // its dynamic shared memory: the largest solve's stages
     std::vector<osscir_ctx*> order;   // descriptor order
     int first[kMaxBranches] = {0, 0, 0, 0}, count[kMaxBranches] = {0, 0, 0, 0};
-    size_t off[kMaxBranches][3] = {};
-    int n_items[kMaxBranches][3] = {};
+    size_t off[kMaxBranches][4] = {};
+    int n_items[kMaxBranches][4] = {};
     std::vector<char> image;
 };
 
@@ -145,11 +169,15 @@ void make_plan(const std::vector<osscir_ctx*>& ctx, const osscir_batch_config& c
             if (owner[i] == b) p.order.push_back(ctx[i]);
         p.count[b] = (int)p.order.size() - p.first[b];
     }
+    p.tables = all_tables(ctx);
+    p.fpb_smem = 0;
+    if (p.tables)
+        for (const osscir_ctx* h : ctx) p.fpb_smem = std::max(p.fpb_smem, (size_t)fpb_stage_bytes(h->bp_slots));
     size_t bytes = sizeof(SolveDesc) * n;
-    std::vector<int2> lists[kMaxBranches][3];
+    std::vector<int2> lists[kMaxBranches][4];
     for (int b = 0; b < p.branches; ++b)
-        for (int k = 0; k < 3; ++k) {
-            build_items(p.order, p.first[b], p.count[b], k, c, lists[b][k]);
+        for (int k = 0; k < 4; ++k) {
+            build_items(p.order, p.first[b], p.count[b], k, c, p.tables, lists[b][k]);
             bytes = (bytes + 255) & ~size_t(255);
             p.off[b][k] = bytes;
             p.n_items[b][k] = (int)lists[b][k].size();
@@ -161,7 +189,7 @@ void make_plan(const std::vector<osscir_ctx*>& ctx, const osscir_batch_config& c
         std::memcpy(p.image.data() + sizeof(SolveDesc) * i, &d, sizeof d);
     }
     for (int b = 0; b < p.branches; ++b)
-        for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < 4; ++k)
             if (!lists[b][k].empty())
                 std::memcpy(p.image.data() + p.off[b][k], lists[b][k].data(), sizeof(int2) * lists[b][k].size());
 }
@@ -178,6 +206,8 @@ cudaError_t launch_branch_kernel(const Plan& p, const char* dev, int b, int k, c
     const int n = p.n_items[b][k];
     if (k == 0) return launch_batch_proj(d, it, n, c.proj_views, c.proj_grid, st);
     if (k == 1) return launch_batch_ray(d, it, n, c.ray_grid, st);
+    if (p.tables)
+        return launch_batch_fpb(d, it, n, plan_items(p, dev, b, 3), p.n_items[b][3], c.bp_grid, p.fpb_smem, st);
     return launch_batch_bp(d, it, n, c.bp_tile_x, c.bp_grid, st);
 }
 
@@ -363,7 +393,7 @@ osscir_status tune_kernel(osscir_batch* b, int k, int persistent_grid, cudaEvent
                 best = c;
             }
         }
-    if (k != 1) {
+    if (k == 0 || (k == 2 && !b->plan.tables)) {
         c = best;
         const int views[4] = {1, 2, 4, 8};
         const int txs[5] = {2, 4, 8, 16, 32};
@@ -436,10 +466,13 @@ osscir_status autotune(osscir_batch* b) {
     if (e == cudaSuccess) e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
     if (e != cudaSuccess) s = from_cuda(e);
-    const int threads[3] = {32 * kDefault.proj_views, kFwdThreads, kBpMaxThreads};
+    make_plan(b->ctx, b->cfg, b->plan);   // whether the back-projection streams tables
+    const bool tables = b->plan.tables;
+    const int threads[3] = {32 * kDefault.proj_views, kFwdThreads, tables ? kBTThreads : kBpMaxThreads};
     for (int k = 0; k < 3 && s == OSSCIR_OK; ++k) {
         int per_sm = 0;
-        e = batch_resident_ctas(k, threads[k], &per_sm);
+        e = (k == 2 && tables) ? batch_resident_ctas(3, threads[k], &per_sm, b->plan.fpb_smem)
+                               : batch_resident_ctas(k, threads[k], &per_sm);
         if (e != cudaSuccess) {
             s = from_cuda(e);
             break;
@@ -500,6 +533,7 @@ double batch_solve_cost(const osscir_ctx* h) { return solve_cost(h); }
 osscir_status batchrun_set(BatchRun* r, const std::vector<osscir_ctx*>& ctx, int branches, cudaStream_t st) {
     r->ctx = ctx;
     if (ctx.empty()) return OSSCIR_OK;
+    CKS(build_all_tables(ctx));   // new solves only (each built once, on its own stream)
     if (branches < 1 || branches > kMaxBranches || (branches & (branches - 1))) return OSSCIR_E_INVALID;
     if (!r->lanes_ok) {
         CK(r->lanes.create());
@@ -573,6 +607,7 @@ osscir_status osscir_batch_create(const osscir_t* solves, int n, int autotune_fl
     // work already queued on the solves (on any stream) must be done before the
     // autotuner saves their state
     CK(cudaDeviceSynchronize());
+    CKS(build_all_tables(v));
 
     osscir_batch* b = new (std::nothrow) osscir_batch();
     if (!b) return OSSCIR_E_NOMEM;

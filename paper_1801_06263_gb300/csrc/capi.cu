@@ -584,6 +584,8 @@ osscir_status ctx_validate(const osscir_geometry* geom, const osscir_spectra* sp
 
 osscir_status ctx_ensure_graph(osscir_ctx* h) { return ensure_graph(h); }
 
+osscir_status ctx_build_tables(osscir_ctx* h) { return build_tables(h); }
+
 cudaError_t ctx_maps_out(const osscir_ctx* h, const float4* x, float4* out, cudaStream_t st) {
     if (!h->basis) return cudaMemcpyAsync(out, x, sizeof(float4) * h->P, cudaMemcpyDeviceToDevice, st);
     Basis3 B;

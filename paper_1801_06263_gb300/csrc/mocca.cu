@@ -1113,15 +1113,13 @@ __global__ void __launch_bounds__(kFwdThreads) k_fp_fwd_fill(GeomC C, ExcTable E
     });
 }
 
-// a1 from the forward table: the same line sums as proj_ray, in the same order.
-// The table is read four entries at a time, the next four loaded while the
-// current four's gathers of xbar are added, so a table load is always in flight.
-__global__ void __launch_bounds__(kFwdThreads, 8) k_fp_proj(GeomC C, FpTables T, SolveD D, int v0, int v1) {
-    const int bx = centre_out(blockIdx.y, gridDim.y);
-    const int l = ray_in_views(C, bx, blockIdx.x, kFwdThreads / 32, v0, v1);
-    if (l < 0) return;
-    const int v = l / C.n_bins, lane = threadIdx.x & 31;
-    const int2* p = T.fwd_pairs + (size_t)T.fwd_row[v * ((C.n_bins + 31) >> 5) + bx] * 32 + lane;
+// a1 from the forward table for ray l of warp wi = v nbg + bx: the same line sums
+// as proj_ray, in the same order.  The table is read four entries at a time, the
+// next four loaded while the current four's gathers of xbar are added, so a
+// table load is always in flight.
+__device__ __forceinline__ void fp_proj_ray(const FpTables& T, const SolveD& D, int l, int wi) {
+    const int lane = threadIdx.x & 31;
+    const int2* p = T.fwd_pairs + (size_t)T.fwd_row[wi] * 32 + lane;
     const int n = __ldg(T.fwd_cnt + l);
     LineSum acc;
     int j = 0;
@@ -1150,6 +1148,12 @@ __global__ void __launch_bounds__(kFwdThreads, 8) k_fp_proj(GeomC C, FpTables T,
     }
     const float4 gs = acc.sum();
     D.g[l] = make_float4(gs.x, gs.y, gs.z, 0.f);
+}
+
+__global__ void __launch_bounds__(kFwdThreads, 8) k_fp_proj(GeomC C, FpTables T, SolveD D, int v0, int v1) {
+    const int bx = centre_out(blockIdx.y, gridDim.y);
+    const int l = ray_in_views(C, bx, blockIdx.x, kFwdThreads / 32, v0, v1);
+    if (l >= 0) fp_proj_ray(T, D, l, (l / C.n_bins) * ((C.n_bins + 31) >> 5) + bx);
 }
 
 // The footprint pairs of pixel (ix, iy) in the views [v0, v1), in the order
@@ -1352,16 +1356,16 @@ __device__ __forceinline__ void bp_accumulate_slot(float acc[9], float w, const 
     acc[8] = fmaf(w, s1.z, acc[8]);
 }
 
-// a6 from the blocked table: each pixel's nine channels over its group's views,
-// written to part ([G][9][P]); k_fpb_finish adds the groups and takes the step.
-// The chunks go through two stage buffers: chunk c + 1 is copied while chunk c
-// is summed.  PARTIAL: only the rays of the views [V0, V1) (one GPU's share of a
-// split solve).
+// a6 from the blocked table for block b = t G + g: each pixel's nine channels
+// over its group's views, written to part ([G][9][P]); the group sums and the
+// step follow in a second pass.  The chunks go through two stage buffers (smem):
+// chunk c + 1 is copied while chunk c is summed.  PARTIAL: only the rays of the
+// views [V0, V1) (one GPU's share of a split solve).  Every thread of the block
+// must call this (it contains block barriers).
 template <bool PARTIAL>
-__global__ void __launch_bounds__(kBTThreads) k_fpb_bp(GeomC C, FpTables T, const RayRec* rec, int V0, int V1,
-                                                       float* part) {
-    extern __shared__ float4 bt_smem[];   // two stage buffers
-    const int G = T.bp_groups, b = blockIdx.x, t = b / G, g = b % G, tid = threadIdx.x, lane = tid & 31;
+__device__ __forceinline__ void fpb_block(const GeomC& C, const FpTables& T, const RayRec* rec, int V0, int V1,
+                                          float* part, int b, float4* smem) {
+    const int G = T.bp_groups, t = b / G, g = b % G, tid = threadIdx.x, lane = tid & 31;
     const int S = T.bp_slots, nch = T.bp_nch, nb = C.n_bins;
     int ix, iy;
     bt_pixel(C.grid.n, t, tid, ix, iy);
@@ -1370,7 +1374,7 @@ __global__ void __launch_bounds__(kBTThreads) k_fpb_bp(GeomC C, FpTables T, cons
     const int l_lo = V0 * nb, l_hi = V1 * nb;
     float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const size_t e0 = (size_t)b * nch;
-    const StageBuf B0(bt_smem, S), B1(bt_smem + stage_f4(S), S);
+    const StageBuf B0(smem, S), B1(smem + stage_f4(S), S);
     if (nch > 0) stage_entry(T, rec, steps, e0, B0);
     for (int c = 0; c < nch; ++c) {
         const StageBuf& B = (c & 1) ? B1 : B0;
@@ -1421,6 +1425,22 @@ __global__ void __launch_bounds__(kBTThreads) k_fpb_bp(GeomC C, FpTables T, cons
     }
 }
 
+template <bool PARTIAL>
+__global__ void __launch_bounds__(kBTThreads) k_fpb_bp(GeomC C, FpTables T, const RayRec* rec, int V0, int V1,
+                                                       float* part) {
+    extern __shared__ float4 bt_smem[];   // two stage buffers
+    fpb_block<PARTIAL>(C, T, rec, V0, V1, part, blockIdx.x, bt_smem);
+}
+
+// The view groups of pixel k added in group order (as bp_finish does).
+__device__ __forceinline__ void fpb_sum(const float* __restrict__ part, int G, size_t P_, size_t k, float acc[9]) {
+#pragma unroll
+    for (int ch = 0; ch < 9; ++ch) acc[ch] = part[(size_t)ch * P_ + k];
+    for (int gg = 1; gg < G; ++gg)
+#pragma unroll
+        for (int ch = 0; ch < 9; ++ch) acc[ch] += part[((size_t)gg * 9 + ch) * P_ + k];
+}
+
 // The view groups' channels added in group order (as bp_finish does), then a7
 // for every pixel; PARTIAL: the sum goes to chan ([9][P]) instead.
 template <bool PARTIAL>
@@ -1429,11 +1449,7 @@ __global__ void k_fpb_finish(GeomC C, StepParams P, SolveD D, const float* __res
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= P_) return;
     float acc[9];
-#pragma unroll
-    for (int ch = 0; ch < 9; ++ch) acc[ch] = part[(size_t)ch * P_ + k];
-    for (int gg = 1; gg < G; ++gg)
-#pragma unroll
-        for (int ch = 0; ch < 9; ++ch) acc[ch] += part[((size_t)gg * 9 + ch) * P_ + k];
+    fpb_sum(part, G, P_, k, acc);
     if (PARTIAL) {
 #pragma unroll
         for (int ch = 0; ch < 9; ++ch) chan[(size_t)ch * P_ + k] = acc[ch];
@@ -1483,8 +1499,39 @@ __global__ void __launch_bounds__(kBatchProjMaxThreads) k_batch_proj(const Solve
         const GeomC C = d.C;
         const int nbx = (C.n_bins + 31) >> 5, nby = (C.n_views + vb - 1) / vb;
         // views fastest, bin groups centre-out (long central rays first), as in k_mocca_proj
-        const int l = ray_at(C, centre_out(w.y / nby, nbx), w.y % nby, vb);
-        if (l >= 0) proj_ray(C, d.E, d.rec, d.D, l);
+        const int bx = centre_out(w.y / nby, nbx);
+        const int l = ray_at(C, bx, w.y % nby, vb);
+        if (l >= 0) {
+            if (d.T.fwd_pairs) fp_proj_ray(d.T, d.D, l, (l / C.n_bins) * nbx + bx);   // the solve's table
+            else proj_ray(C, d.E, d.rec, d.D, l);
+        }
+    }
+}
+
+// Batched back-projection from the solves' blocked tables: item (solve, block b)
+// runs fpb_block; the dynamic shared memory holds the largest solve's stages.
+__global__ void __launch_bounds__(kBTThreads) k_batch_fpb_bp(const SolveDesc* __restrict__ sd,
+                                                             const int2* __restrict__ items, int n_items) {
+    extern __shared__ float4 bt_smem[];
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int2 w = __ldg(items + it);
+        const SolveDesc& d = sd[w.x];
+        fpb_block<false>(d.C, d.T, d.rec, 0, d.C.n_views, d.T.bp_part, w.y, bt_smem);
+    }
+}
+
+// The view groups added and a7, item (solve, block of 256 pixels).
+__global__ void __launch_bounds__(256) k_batch_fpb_finish(const SolveDesc* __restrict__ sd,
+                                                          const int2* __restrict__ items, int n_items) {
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int2 w = __ldg(items + it);
+        const SolveDesc& d = sd[w.x];
+        const size_t P_ = (size_t)d.C.grid.n * d.C.grid.n, k = (size_t)w.y * 256 + threadIdx.x;
+        if (k < P_) {
+            float acc[9];
+            fpb_sum(d.T.bp_part, d.T.bp_groups, P_, k, acc);
+            pixel_step(d.C, d.P, d.D, (int)k, acc);
+        }
     }
 }
 
@@ -1691,10 +1738,23 @@ cudaError_t launch_batch_dtpl(const SolveDesc* sd, int n_solves, cudaStream_t st
     return cudaGetLastError();
 }
 
-cudaError_t batch_resident_ctas(int kernel, int threads, int* per_sm) {
+cudaError_t launch_batch_fpb(const SolveDesc* sd, const int2* items, int n_items, const int2* fin_items,
+                             int n_fin, int grid, size_t smem, cudaStream_t st) {
+    if (n_items > 0) {
+        k_batch_fpb_bp<<<grid > 0 ? grid : n_items, kBTThreads, smem, st>>>(sd, items, n_items);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (n_fin <= 0) return cudaSuccess;
+    k_batch_fpb_finish<<<n_fin, 256, 0, st>>>(sd, fin_items, n_fin);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_resident_ctas(int kernel, int threads, int* per_sm, size_t smem) {
     switch (kernel) {
         case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch_proj, threads, 0);
         case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch_ray, threads, 0);
+        case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch_fpb_bp, threads, smem);
         default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch_bp, threads, 0);
     }
 }

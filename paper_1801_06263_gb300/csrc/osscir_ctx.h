@@ -106,6 +106,9 @@ cudaError_t ctx_maps_out(const osscir_ctx* h, const float4* x, float4* out, cuda
 void ctx_maps_out_host(const osscir_ctx* h, float* maps);
 // Capture the per-iteration graph(s) once.
 osscir_status ctx_ensure_graph(osscir_ctx* h);
+// Build the footprint tables if they are not built yet (synchronises the
+// context's own stream); a device without room leaves the on-the-fly kernels.
+osscir_status ctx_build_tables(osscir_ctx* h);
 
 // Batch runner for the served form: the batched kernels over a set of contexts
 // that changes over time, with all updates in stream order on one stream.

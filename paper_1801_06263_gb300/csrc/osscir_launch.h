@@ -182,6 +182,7 @@ struct SolveDesc {
     double* dtpl_out;   // D_TPL at the last expansion point
     int n_part;         // dtpl_partials(n_bins, n_views)
     int bp_groups;      // bp_view_groups(P, n_views), a divisor of 8
+    FpTables T;         // the solve's footprint tables (null pointers: the projections run on the fly)
 };
 
 constexpr int kBatchProjMaxThreads = 256;   // up to 8 views x 32 bins per projection block
@@ -204,7 +205,13 @@ cudaError_t launch_batch_ray(const SolveDesc* sd, const int2* items, int n_items
 cudaError_t launch_batch_bp(const SolveDesc* sd, const int2* items, int n_items, int tx, int grid,
                             cudaStream_t st);
 cudaError_t launch_batch_dtpl(const SolveDesc* sd, int n_solves, cudaStream_t st);
-// Resident CTAs per SM of a batched kernel (0 projection, 1 ray, 2 back-projection).
-cudaError_t batch_resident_ctas(int kernel, int threads, int* per_sm);
+// Back-projection of solves with footprint tables: items (solve, table block),
+// then fin_items (solve, block of 256 pixels) for the group sums and a7; smem:
+// the largest solve's two stage buffers (fpb_stage_bytes).
+cudaError_t launch_batch_fpb(const SolveDesc* sd, const int2* items, int n_items, const int2* fin_items,
+                             int n_fin, int grid, size_t smem, cudaStream_t st);
+// Resident CTAs per SM of a batched kernel (0 projection, 1 ray, 2 back-projection
+// on the fly, 3 back-projection from tables with smem bytes of dynamic shared memory).
+cudaError_t batch_resident_ctas(int kernel, int threads, int* per_sm, size_t smem = 0);
 
 }  // namespace osscir

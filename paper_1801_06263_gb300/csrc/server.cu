@@ -105,8 +105,12 @@ size_t estimate_bytes(const Config& c) {
     const size_t L = (size_t)c.geom.n_views * c.geom.n_bins, P = (size_t)c.geom.n * c.geom.n;
     const size_t per_ray = 64 + 32 + 4 + 4 + 16 + 16 + 8 * 4 / 128 + 2;   // records, FP64 rays, chord, offsets, c, y, partials
     const size_t mu_pc = c.params.spc == 2 ? P * 16 + 12 * c.nE : 0;   // the caller's curves and a maps buffer
+    // footprint tables: about 0.9 n footprint pairs per ray (0.82 n measured at 256 x 256), 8.8 bytes each
+    // in the forward table and 7.5 in the back-projection's (with the rows' padding), and the view
+    // groups' channel sums (at most 8 groups of 36 bytes per pixel)
+    const size_t tables = (size_t)(0.9 * c.geom.n * (double)L * 16.3) + P * 288 + L * 8;
     return L * per_ray + P * 32 + (size_t)c.nE * c.geom.n_bins * 16 + c.geom.n_bins * 16 + 12 * c.nE +
-           c.geom.n_views * 8 + (L / 8) * 8 + mu_pc + (1 << 16);
+           c.geom.n_views * 8 + (L / 8) * 8 + mu_pc + tables + (1 << 16);
 }
 
 void release_slot(Slot* s) {
@@ -188,6 +192,7 @@ Slot* osscir_server::acquire(Ticket* t) {
     s->key = t->key;
     osscir_spectra sp{t->cfg.nE, t->cfg.s.data(), t->cfg.N.data()};
     osscir_status st = osscir::ctx_create(&t->cfg.geom, &sp, t->cfg.mu.data(), &t->cfg.params, &s->ctx);
+    if (st == OSSCIR_OK) st = osscir::ctx_build_tables(s->ctx);   // counted in the context's bytes below
     const size_t L = (size_t)t->cfg.geom.n_views * t->cfg.geom.n_bins, P = (size_t)t->cfg.geom.n * t->cfg.geom.n;
     if (st == OSSCIR_OK && (cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess ||
                             cudaHostAlloc(&s->h_counts, L * 16, cudaHostAllocDefault) != cudaSuccess ||
