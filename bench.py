@@ -71,7 +71,13 @@ FP32_LANES_PER_SM, SCHEDULERS_PER_SM, L1_BYTES_PER_CLK_PER_SM = 128, 4, 128
 # instructions executed.  Valid only for that workload and for the kernel
 # sources they were taken on (source_sha, see _source_sha).
 NCU_WORKLOAD = "medium_256"
-NCU_COUNTS = {}
+NCU_COUNTS = {
+    "k_fp_proj": {"dram_bytes": 471092736 + 4667648, "warp_instructions": 36490880, "source_sha": "5d35a0ffd9d037b6"},
+    "k_mocca_ray": {"dram_bytes": 23002624 + 2304, "warp_instructions": 113676145, "source_sha": "5d35a0ffd9d037b6"},
+    # the back-projection's two launches: k_fpb_bp and k_fpb_finish
+    "k_fpb_bp": {"dram_bytes": 428959488 + 16539648 + 19964928, "warp_instructions": 78614524 + 1333248,
+                 "source_sha": "5d35a0ffd9d037b6"},
+}
 
 
 def bp_view_groups(n_pixels, n_views):
@@ -539,7 +545,10 @@ def run_batched(args, rank):
     finite = sum(1 for R in recs if np.isfinite(R.dtpl(1)))
     P = sum(w.geom.n_pixels for w in ws)
     L = sum(w.geom.n_rays for w in ws)
-    alg_bytes = 48.0 * P + 124.0 * L        # per iteration: x_n, x_{n-1} read, x_{n+1} written; per-ray fields
+    # per iteration: x_n, x_{n-1} read, x_{n+1} written; the per-ray fields; and the footprint
+    # tables, which the batch streams once per iteration (about all of their bytes)
+    table_bytes = sum(_lib.osscir_memory(R.handle)[1] for R in recs)
+    alg_bytes = 48.0 * P + 124.0 * L + table_bytes
     best_ms = min(default_ms, tuned_ms)
     for R in recs:
         R.close()
@@ -555,7 +564,8 @@ def run_batched(args, rank):
         "solve_iterations_per_s": len(ws) * 1e3 / best_ms,
         "kernel_ms_default": list(kms_default), "kernel_ms_tuned": list(kms_tuned),
         "tuned_config": cfg, "autotune_s": tune_s, "finite_solves": finite,
-        "hbm": {"algorithmic_bytes_per_iteration": alg_bytes, "achieved_GBps": alg_bytes / (best_ms * 1e-3) / 1e9,
+        "hbm": {"algorithmic_bytes_per_iteration": alg_bytes, "footprint_table_bytes": table_bytes,
+                "achieved_GBps": alg_bytes / (best_ms * 1e-3) / 1e9,
                 "peak_GBps": HBM_PEAK_GBPS, "frac": alg_bytes / (best_ms * 1e-3) / 1e9 / HBM_PEAK_GBPS,
                 "peak_source": HBM_PEAK_SOURCE},
     }
