@@ -36,7 +36,8 @@ class _Geom(ct.Structure):
 
 
 class _Spectra(ct.Structure):
-    _fields_ = [("n_energies", ct.c_int), ("s", _dp), ("N", _dp), ("mu", _dp), ("exp_model", ct.c_int)]
+    _fields_ = [("n_energies", ct.c_int), ("s", _dp), ("N", _dp), ("mu", _dp), ("exp_model", ct.c_int),
+                ("n_windows", ct.c_int)]
 
 
 class _Params(ct.Structure):
@@ -81,7 +82,7 @@ def lib():
         L.orc_solve.restype = ct.c_int
         L.orc_eig_sym3.argtypes = [_dp, _dp, _dp]
         L.orc_clip_psd3.argtypes = [_dp, _dp]
-        L.orc_dual_update.argtypes = [_dp, _dp, _dp, _dp, ct.c_int, _dp, _dp, _dp]
+        L.orc_dual_update.argtypes = [ct.c_int, _dp, _dp, _dp, _dp, ct.c_int, _dp, _dp, _dp]
         L.orc_dual_update.restype = ct.c_int
         L.orc_primal_update.argtypes = [_dp, _dp, _dp, ct.c_int, _dp, _dp, _dp]
         L.orc_primal_update.restype = ct.c_int
@@ -119,8 +120,9 @@ class _SpecHolder:
         self.s = _f64(sp.s)
         self.N = _f64(sp.N)
         self.mu = _f64(sp.mu if mu is None else mu)
+        self.nw = self.s.shape[2]
         self.c = _Spectra(self.s.shape[1], _ptr(self.s), _ptr(self.N), _ptr(self.mu),
-                          {"softexp": 0, "exp": 1}[counts_model])
+                          {"softexp": 0, "exp": 1}[counts_model], self.nw)
 
 
 def _params(lam, use_box=False, lo=(0, 0, 0), hi=(0, 0, 0), spc="block", model="hessian", inner=1):
@@ -173,31 +175,31 @@ def backproject(geom, rf):
 # --------------------------------------------------------------------------- counts model
 
 def counts(geom, spectra, f, mu=None, counts_model="softexp"):
-    """Expected counts c^(f), [L, 4] (Eq. finalModel; counts_model="exp": Eq. fullModel)."""
+    """Expected counts c^(f), [L, W] (Eq. finalModel; counts_model="exp": Eq. fullModel)."""
     sh = _SpecHolder(spectra, mu, counts_model)
     f = _f64(f)
-    chat = np.zeros((geom.n_rays, 4))
+    chat = np.zeros((geom.n_rays, sh.nw))
     lib().orc_counts(ct.byref(_geom(geom)), ct.byref(sh.c), _ptr(f), _ptr(chat))
     return chat
 
 
 def ray_terms(spectra, b, g, c=None, with_AB=False, mu=None, counts_model="softexp"):
     sh = _SpecHolder(spectra, mu, counts_model)
-    nE = sh.s.shape[1]
+    nE, nw = sh.s.shape[1], sh.nw
     g = _f64(g)
     cw = None if c is None else _f64(c)
     out = {k: np.zeros(sz) for k, sz in
-           (("chat", 4), ("r", 4), ("alpha", 12), ("grad", 3), ("H", 9))}
-    A = np.zeros(4 * nE) if with_AB else None
-    B = np.zeros(4 * nE) if with_AB else None
+           (("chat", nw), ("r", nw), ("alpha", 3 * nw), ("grad", 3), ("H", 9))}
+    A = np.zeros(nw * nE) if with_AB else None
+    B = np.zeros(nw * nE) if with_AB else None
     lib().orc_ray_terms(ct.byref(sh.c), int(b), _ptr(g), _ptr(cw), _ptr(out["chat"]),
                         _ptr(out["r"]), _ptr(out["alpha"]), _ptr(out["grad"]), _ptr(out["H"]),
                         _ptr(A), _ptr(B))
-    out["alpha"] = out["alpha"].reshape(4, 3)
+    out["alpha"] = out["alpha"].reshape(nw, 3)
     out["H"] = out["H"].reshape(3, 3)
     if with_AB:
-        out["A"] = A.reshape(4, nE)
-        out["B"] = B.reshape(4, nE)
+        out["A"] = A.reshape(nw, nE)
+        out["B"] = B.reshape(nw, nE)
     return out
 
 
@@ -248,9 +250,11 @@ MODELS = {"hessian": 0, "gradient": 1, "gauss_newton": 2, "separable": 3}
 
 def dual_update(alpha, Hp, r, sigma_inv, y, model="hessian", c=None):
     """Dual step of one ray; c (the window counts) is needed by model="separable"."""
-    out = np.zeros(4)
-    cw = _f64(np.zeros(4) if c is None else c)
-    st = lib().orc_dual_update(_ptr(_f64(alpha)), _ptr(_f64(Hp)), _ptr(_f64(r)),
+    alpha = _f64(alpha).reshape(-1, 3)
+    nw = alpha.shape[0]
+    out = np.zeros(nw)
+    cw = _f64(np.zeros(nw) if c is None else c)
+    st = lib().orc_dual_update(nw, _ptr(alpha), _ptr(_f64(Hp)), _ptr(_f64(r)),
                                _ptr(_f64(sigma_inv)), MODELS[model], _ptr(cw),
                                _ptr(_f64(y)), _ptr(out))
     if st:
@@ -275,21 +279,21 @@ def step_matrices(geom, spectra, xbar, lam, spc="block", mu=None, counts_model="
     sh = _SpecHolder(spectra, mu, counts_model)
     P = _params(lam, spc=spc)
     xbar = _f64(xbar)
-    sinv = np.zeros((geom.n_rays, 4))
+    sinv = np.zeros((geom.n_rays, sh.nw))
     Tinv = np.zeros((geom.n_pixels, 9))
-    alpha = np.zeros((geom.n_rays, 12))
+    alpha = np.zeros((geom.n_rays, 3 * sh.nw))
     lib().orc_step_matrices(ct.byref(_geom(geom)), ct.byref(sh.c), ct.byref(P), _ptr(xbar),
                             _ptr(sinv), _ptr(Tinv), _ptr(alpha))
-    return sinv, Tinv.reshape(-1, 3, 3), alpha.reshape(-1, 4, 3)
+    return sinv, Tinv.reshape(-1, 3, 3), alpha.reshape(-1, sh.nw, 3)
 
 
 class State:
-    """MOCCA state: x = x_n [P,3], xbar = 2 x_n - x_{n-1} [P,3], y = y_n [L,4]."""
+    """MOCCA state: x = x_n [P,3], xbar = 2 x_n - x_{n-1} [P,3], y = y_n [L,W]."""
 
-    def __init__(self, geom):
+    def __init__(self, geom, n_windows=4):
         self.x = np.zeros((geom.n_pixels, 3))
         self.xbar = np.zeros((geom.n_pixels, 3))
-        self.y = np.zeros((geom.n_rays, 4))
+        self.y = np.zeros((geom.n_rays, n_windows))
         self.n = 0
 
     def copy(self):
@@ -306,7 +310,8 @@ def mocca(geom, spectra, c, n_iters, lam, state=None, *, box=None, spc="block",
     inner=k > 1: nested MOCCA, a new local model every k iterations of this call
     (the first iteration of a call is always an outer one; see orc_mocca)."""
     sh = _SpecHolder(spectra, mu, counts_model)
-    st = State(geom) if state is None else state
+    st = State(geom, sh.nw) if state is None else state
+    assert st.y.shape == (geom.n_rays, sh.nw)
     lo, hi = (box if box is not None else ((0, 0, 0), (0, 0, 0)))
     P = _params(lam, box is not None, tuple(lo), tuple(hi), spc, model, inner)
     c = _f64(c)

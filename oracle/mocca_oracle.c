@@ -41,7 +41,7 @@
 #include <omp.h>
 #endif
 
-#define NW 4 /* energy windows */
+#define NWMAX 8 /* energy windows: n_windows of the spectra, at most NWMAX */
 #define NM 3 /* basis materials */
 
 typedef struct {
@@ -55,10 +55,11 @@ typedef struct {
 
 typedef struct {
     int n_energies;
-    const double *s;  /* [n_bins][nE][4]  normalised spectral response s_{w,l,i} */
-    const double *N;  /* [n_bins][4]      incident photons N_{w,l}              */
+    const double *s;  /* [n_bins][nE][W]  normalised spectral response s_{w,l,i} */
+    const double *N;  /* [n_bins][W]      incident photons N_{w,l}              */
     const double *mu; /* [3][nE]          mu_{m,i} in 1/mm                       */
     int exp_model;    /* 0: softexp (Eq. finalModel); 1: exp (the standard model, Eq. fullModel) */
+    int n_windows;    /* W, the energy windows (1 .. NWMAX); every per-ray window array is [W] */
 } orc_spectra;
 
 typedef struct {
@@ -243,10 +244,10 @@ static double sexp2(double x, int expm) { return (x <= 0.0 || expm) ? exp(x) : 0
  *   H_mn = sum_w (chat_w + r_w) alpha_wm alpha_wn - sum_i (B^T r)_i mu_mi mu_ni
  *          (the ray's block of the Hessian of Sec. 2, in g)
  * Any output pointer may be NULL. */
-void orc_ray_terms(const orc_spectra *sp, int b, const double g[3], const double cw[4],
-                   double chat[4], double r[4], double alpha[12], double grad[3], double H[9],
-                   double A_out[] /* [4][nE] or NULL */, double B_out[] /* [4][nE] or NULL */) {
-    const int nE = sp->n_energies;
+void orc_ray_terms(const orc_spectra *sp, int b, const double g[3], const double cw[] /* [W] */,
+                   double chat[] /* [W] */, double r[] /* [W] */, double alpha[] /* [W][3] */, double grad[3],
+                   double H[9], double A_out[] /* [W][nE] or NULL */, double B_out[] /* [W][nE] or NULL */) {
+    const int nE = sp->n_energies, NW = sp->n_windows;
     const double *s = sp->s + (size_t)b * nE * NW;
     double *e0 = (double *)malloc(sizeof(double) * nE);
     double *e1 = (double *)malloc(sizeof(double) * nE);
@@ -258,7 +259,7 @@ void orc_ray_terms(const orc_spectra *sp, int b, const double g[3], const double
         e1[i] = sexp1(-p, sp->exp_model);
         e2[i] = sexp2(-p, sp->exp_model);
     }
-    double D[NW], ch[NW], rr[NW], al[NW][NM];
+    double D[NWMAX], ch[NWMAX], rr[NWMAX], al[NWMAX][NM];
     for (int w = 0; w < NW; ++w) {
         D[w] = 0.0;
         for (int i = 0; i < nE; ++i) D[w] += s[i * NW + w] * e0[i];
@@ -277,8 +278,8 @@ void orc_ray_terms(const orc_spectra *sp, int b, const double g[3], const double
     if (B_out)
         for (int w = 0; w < NW; ++w)
             for (int i = 0; i < nE; ++i) B_out[w * nE + i] = s[i * NW + w] * e2[i] / D[w];
-    if (chat) memcpy(chat, ch, sizeof ch);
-    if (r) memcpy(r, rr, sizeof rr);
+    if (chat) memcpy(chat, ch, sizeof(double) * NW);
+    if (r) memcpy(r, rr, sizeof(double) * NW);
     if (alpha)
         for (int w = 0; w < NW; ++w)
             for (int m = 0; m < NM; ++m) alpha[w * NM + m] = al[w][m];
@@ -313,7 +314,7 @@ void orc_counts(const orc_geometry *G, const orc_spectra *sp, const double *f, d
     orc_forward(G, f, NM, g);
 #pragma omp parallel for schedule(static)
     for (int l = 0; l < L; ++l)
-        orc_ray_terms(sp, l % G->n_bins, g + (size_t)l * NM, NULL, chat + (size_t)l * NW, NULL, NULL,
+        orc_ray_terms(sp, l % G->n_bins, g + (size_t)l * NM, NULL, chat + (size_t)l * sp->n_windows, NULL, NULL,
                       NULL, NULL, NULL, NULL);
     free(g);
 }
@@ -332,7 +333,7 @@ double orc_dtpl(int n, const double *c, const double *chat) {
 /* D_TPL(c, c^(f)) and its gradient Z^T A^T r per pixel (grad may be NULL). */
 double orc_objective(const orc_geometry *G, const orc_spectra *sp, const double *c, const double *f,
                      double *grad /* [P][3] */) {
-    const int L = G->n_views * G->n_bins;
+    const int L = G->n_views * G->n_bins, NW = sp->n_windows;
     double *g = (double *)malloc(sizeof(double) * (size_t)L * NM);
     double *chat = (double *)malloc(sizeof(double) * (size_t)L * NW);
     double *gr = (double *)malloc(sizeof(double) * (size_t)L * NM);
@@ -354,8 +355,8 @@ double orc_objective(const orc_geometry *G, const orc_spectra *sp, const double 
 /* Solve the n x n system M x = rhs by Gaussian elimination with partial
  * pivoting (M and rhs are copied).  Returns 0 on success, -1 if singular. */
 int orc_solve(int n, const double *M, const double *rhs, double *x) {
-    double a[16], bb[4];
-    if (n > 4) return -1;
+    double a[NWMAX * NWMAX], bb[NWMAX];
+    if (n > NWMAX) return -1;
     memcpy(a, M, sizeof(double) * n * n);
     memcpy(bb, rhs, sizeof(double) * n);
     for (int col = 0; col < n; ++col) {
@@ -473,21 +474,20 @@ void orc_clip_psd3(const double *H, double *Hp) {
  *   model 3:      W = diag(c);
  *   y' = y - Sigma (W + Sigma)^-1 (y - r).
  * A ray with a zero entry of sigma_inv misses the image and keeps y. */
-int orc_dual_update(const double alpha[12], const double Hp[9], const double r[4],
-                    const double sigma_inv[4], int model, const double c[4], const double y[4],
-                    double y_out[4]) {
+int orc_dual_update(int NW, const double alpha[] /* [W][3] */, const double Hp[9], const double r[],
+                    const double sigma_inv[], int model, const double c[], const double y[], double y_out[]) {
     for (int w = 0; w < NW; ++w)
         if (!(sigma_inv[w] > 0.0)) {
             memcpy(y_out, y, sizeof(double) * NW);
             return 0;
         }
-    double sig[NW];
+    double sig[NWMAX];
     for (int w = 0; w < NW; ++w) sig[w] = 1.0 / sigma_inv[w];
-    double W[16] = {0};
+    double W[NWMAX * NWMAX] = {0};
     if (model == 3)
         for (int w = 0; w < NW; ++w) W[w * NW + w] = c[w];
     if (model == 0 || model == 2) {
-        double AtA[9], AtAi[9], Gm[12];
+        double AtA[9], AtAi[9], Gm[NM * NWMAX];
         for (int m = 0; m < NM; ++m)
             for (int q = 0; q < NM; ++q) {
                 double acc = 0.0;
@@ -509,8 +509,8 @@ int orc_dual_update(const double alpha[12], const double Hp[9], const double r[4
                 W[w1 * NW + w2] = acc;
             }
     }
-    double M4[16], d[NW], u[NW];
-    for (int i = 0; i < 16; ++i) M4[i] = W[i];
+    double M4[NWMAX * NWMAX], d[NWMAX], u[NWMAX];
+    for (int i = 0; i < NW * NW; ++i) M4[i] = W[i];
     for (int w = 0; w < NW; ++w) {
         M4[w * NW + w] += sig[w];
         d[w] = y[w] - r[w];
@@ -597,8 +597,8 @@ int orc_primal_update(const double Tinv_in[9], const double v[3], const double x
  *   block SPC:    (Sigma^-1)_{wl} = lambda sum_k sqrt(sum_m K_{wl,mk}^2)
  *   diagonal SPC: (Sigma^-1)_{wl} = lambda sum_{m,k} |K_{wl,mk}|
  * both written out over the ray's footprint. */
-static void ray_sigma_inv(const orc_params *P, const double alpha[12], int cnt, const double *len,
-                          double sigma_inv[4]) {
+static void ray_sigma_inv(const orc_params *P, int NW, const double alpha[], int cnt, const double *len,
+                          double sigma_inv[]) {
     for (int w = 0; w < NW; ++w) {
         double acc = 0.0;
         for (int j = 0; j < cnt; ++j) {
@@ -622,7 +622,7 @@ static void ray_sigma_inv(const orc_params *P, const double alpha[12], int cnt, 
  *   v_k    += sum_w K_{wl,mk} y'_{wl}                       (K^T y')
  *   block SPC:    Tinv_k[m][m'] += (1/lambda) sum_w K_m K_m' / sqrt(sum_m'' K_m''^2)
  *   diagonal SPC: Tinv_k[m][m]  += (1/lambda) sum_w |K_m|                       */
-static void ray_scatter(const orc_params *P, const double alpha[12], const double yp[4], int cnt,
+static void ray_scatter(const orc_params *P, int NW, const double alpha[], const double yp[], int cnt,
                         const int *pix, const double *len, int k_lo, int k_hi, double *v, double *Tinv) {
     for (int j = 0; j < cnt; ++j) {
         if (pix[j] < k_lo || pix[j] >= k_hi) continue;   /* another thread's pixels */
@@ -656,7 +656,7 @@ static void ray_scatter(const orc_params *P, const double alpha[12], const doubl
  * the number of threads, and the result is bit-identical to it. */
 enum { kScatterChunk = 2048 };
 
-static void scatter_rays(const orc_geometry *G, const orc_params *P, const double *al, const double *y,
+static void scatter_rays(const orc_geometry *G, const orc_params *P, int NW, const double *al, const double *y,
                          double *v, double *Tinv, int *fp_cnt, int *fp_pix, double *fp_len) {
     const int L = G->n_views * G->n_bins, Pn = G->n * G->n, cap = 2 * G->n + 4;
     memset(v, 0, sizeof(double) * (size_t)Pn * 3);
@@ -678,7 +678,7 @@ static void scatter_rays(const orc_geometry *G, const orc_params *P, const doubl
                                             fp_len + (size_t)(l - l0) * cap, cap);
             /* (the implicit barrier: the chunk's footprints are complete) */
             for (int l = l0; l < l1; ++l)
-                ray_scatter(P, al + (size_t)l * 12, y + (size_t)l * NW, fp_cnt[l - l0],
+                ray_scatter(P, NW, al + (size_t)l * NM * NW, y + (size_t)l * NW, fp_cnt[l - l0],
                             fp_pix + (size_t)(l - l0) * cap, fp_len + (size_t)(l - l0) * cap, k_lo, k_hi, v,
                             Tinv);
 #pragma omp barrier
@@ -687,12 +687,12 @@ static void scatter_rays(const orc_geometry *G, const orc_params *P, const doubl
 }
 
 /* Step matrices at the expansion point xbar without updating anything:
- * sigma_inv [L][4], Tinv [P][9], alpha [L][12] (any may be NULL). */
+ * sigma_inv [L][W], Tinv [P][9], alpha [L][W][3] (any may be NULL). */
 void orc_step_matrices(const orc_geometry *G, const orc_spectra *sp, const orc_params *P,
                        const double *xbar, double *sigma_inv, double *Tinv, double *alpha_out) {
-    const int L = G->n_views * G->n_bins, Pn = G->n * G->n, cap = 2 * G->n + 4;
+    const int L = G->n_views * G->n_bins, Pn = G->n * G->n, cap = 2 * G->n + 4, NW = sp->n_windows;
     double *g = (double *)malloc(sizeof(double) * (size_t)L * NM);
-    double *al = (double *)malloc(sizeof(double) * (size_t)L * 12);
+    double *al = (double *)malloc(sizeof(double) * (size_t)L * NM * NW);
     double *zeros = (double *)calloc((size_t)L * NW, sizeof(double));
     orc_forward(G, xbar, NM, g);
     int *pix = (int *)malloc(sizeof(int) * cap);
@@ -700,13 +700,13 @@ void orc_step_matrices(const orc_geometry *G, const orc_spectra *sp, const orc_p
     double *v = (double *)calloc((size_t)Pn * 3, sizeof(double));
     if (Tinv) memset(Tinv, 0, sizeof(double) * (size_t)Pn * 9);
     for (int l = 0; l < L; ++l) {
-        orc_ray_terms(sp, l % G->n_bins, g + (size_t)l * NM, NULL, NULL, NULL, al + (size_t)l * 12,
+        orc_ray_terms(sp, l % G->n_bins, g + (size_t)l * NM, NULL, NULL, NULL, al + (size_t)l * NM * NW,
                       NULL, NULL, NULL, NULL);
         int cnt = orc_siddon(G, l / G->n_bins, l % G->n_bins, pix, len, cap);
-        if (sigma_inv) ray_sigma_inv(P, al + (size_t)l * 12, cnt, len, sigma_inv + (size_t)l * NW);
-        if (Tinv) ray_scatter(P, al + (size_t)l * 12, zeros, cnt, pix, len, 0, Pn, v, Tinv);
+        if (sigma_inv) ray_sigma_inv(P, NW, al + (size_t)l * NM * NW, cnt, len, sigma_inv + (size_t)l * NW);
+        if (Tinv) ray_scatter(P, NW, al + (size_t)l * NM * NW, zeros, cnt, pix, len, 0, Pn, v, Tinv);
     }
-    if (alpha_out) memcpy(alpha_out, al, sizeof(double) * (size_t)L * 12);
+    if (alpha_out) memcpy(alpha_out, al, sizeof(double) * (size_t)L * NM * NW);
     free(g);
     free(al);
     free(zeros);
@@ -733,9 +733,9 @@ void orc_step_matrices(const orc_geometry *G, const orc_spectra *sp, const orc_p
  * Returns 0, or -1 if a small system was singular. */
 int orc_mocca(const orc_geometry *G, const orc_spectra *sp, const orc_params *P, const double *c,
               double *x, double *xbar, double *y, int n_iters, double *dtpl_hist) {
-    const int L = G->n_views * G->n_bins, Pn = G->n * G->n, cap = 2 * G->n + 4;
+    const int L = G->n_views * G->n_bins, Pn = G->n * G->n, cap = 2 * G->n + 4, NW = sp->n_windows;
     double *g = (double *)malloc(sizeof(double) * (size_t)L * NM);
-    double *al = (double *)malloc(sizeof(double) * (size_t)L * 12);
+    double *al = (double *)malloc(sizeof(double) * (size_t)L * NM * NW);
     double *dt = (double *)malloc(sizeof(double) * (size_t)L);
     double *v = (double *)malloc(sizeof(double) * (size_t)Pn * 3);
     double *Tinv = (double *)malloc(sizeof(double) * (size_t)Pn * 9);
@@ -763,9 +763,9 @@ int orc_mocca(const orc_geometry *G, const orc_spectra *sp, const orc_params *P,
 #pragma omp for schedule(static)
             for (int l = 0; l < L; ++l) {
                 const int b = l % G->n_bins;
-                double chat[4], r[4], H[9], Hp[9], sinv[4], yn[4], u[4];
+                double chat[NWMAX], r[NWMAX], H[9], Hp[9], sinv[NWMAX], yn[NWMAX], u[NWMAX];
                 const double *cl = c + (size_t)l * NW;
-                double *all = al + (size_t)l * 12;
+                double *all = al + (size_t)l * NM * NW;
                 if (outer) {
                     orc_ray_terms(sp, b, g + (size_t)l * NM, cl, chat, r, all, NULL, H, NULL, NULL);
                     if (P->model == 0) {
@@ -781,20 +781,20 @@ int orc_mocca(const orc_geometry *G, const orc_spectra *sp, const orc_params *P,
                         memset(Hp, 0, sizeof Hp);
                     }
                     int cnt = orc_siddon(G, l / G->n_bins, b, pp, ll, cap);
-                    ray_sigma_inv(P, all, cnt, ll, sinv);
-                    memcpy(u, y + (size_t)l * NW, sizeof u);
+                    ray_sigma_inv(P, NW, all, cnt, ll, sinv);
+                    memcpy(u, y + (size_t)l * NW, sizeof(double) * NW);
                     if (inner > 1) {
                         memcpy(mHp + (size_t)l * 9, Hp, sizeof Hp);
-                        memcpy(mr + (size_t)l * NW, r, sizeof r);
-                        memcpy(msinv + (size_t)l * NW, sinv, sizeof sinv);
+                        memcpy(mr + (size_t)l * NW, r, sizeof(double) * NW);
+                        memcpy(msinv + (size_t)l * NW, sinv, sizeof(double) * NW);
                         memcpy(mg0 + (size_t)l * NM, g + (size_t)l * NM, sizeof(double) * NM);
                     }
                 } else {
-                    double dummy[12];   /* D_TPL at xbar as a diagnostic; the model stays fixed */
+                    double dummy[NM * NWMAX];   /* D_TPL at xbar as a diagnostic; the model stays fixed */
                     orc_ray_terms(sp, b, g + (size_t)l * NM, cl, chat, NULL, dummy, NULL, NULL, NULL, NULL);
                     memcpy(Hp, mHp + (size_t)l * 9, sizeof Hp);
-                    memcpy(r, mr + (size_t)l * NW, sizeof r);
-                    memcpy(sinv, msinv + (size_t)l * NW, sizeof sinv);
+                    memcpy(r, mr + (size_t)l * NW, sizeof(double) * NW);
+                    memcpy(sinv, msinv + (size_t)l * NW, sizeof(double) * NW);
                     const double *gl = g + (size_t)l * NM, *g0 = mg0 + (size_t)l * NM;
                     for (int w = 0; w < NW; ++w) {
                         double kz = 0.0;   /* (K (xbar - f0))_w = alpha_w . (g - g0) */
@@ -805,11 +805,11 @@ int orc_mocca(const orc_geometry *G, const orc_spectra *sp, const orc_params *P,
                 double d = 0.0;
                 for (int w = 0; w < NW; ++w) d += dtpl_term(chat[w], cl[w]);
                 dt[l] = d;
-                if (orc_dual_update(all, Hp, r, sinv, P->model, cl, u, yn)) {
+                if (orc_dual_update(NW, all, Hp, r, sinv, P->model, cl, u, yn)) {
 #pragma omp atomic write
                     status = -1;
                 }
-                memcpy(y + (size_t)l * NW, yn, sizeof yn);
+                memcpy(y + (size_t)l * NW, yn, sizeof(double) * NW);
             }
             free(pp);
             free(ll);
@@ -820,7 +820,7 @@ int orc_mocca(const orc_geometry *G, const orc_spectra *sp, const orc_params *P,
             dtpl_hist[it] = acc;
         }
         /* back-projection of K^T y' and of the block step matrix */
-        scatter_rays(G, P, al, y, v, Tinv, fp_cnt, fp_pix, fp_len);
+        scatter_rays(G, P, NW, al, y, v, Tinv, fp_cnt, fp_pix, fp_len);
         /* per-pixel primal step and extrapolation */
 #pragma omp parallel for schedule(static)
         for (int k = 0; k < Pn; ++k) {
