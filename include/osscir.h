@@ -7,7 +7,9 @@
  * step-preconditioning" (arXiv:1801.06263), Sec. 2.  Notation:
  *   f_{k,m}   material maps, pixel k = iy * n + ix, material m = 0 (PMMA), 1 (Al), 2 (Gd)
  *   l         ray (view v, detector bin b), l = v * n_bins + b
- *   w         energy window, 4 windows
+ *   w         energy window: W = 4 windows (the paper's overlapping realistic
+ *             responses, Sec. 3) or W = 5 (the ideal non-overlapping responses
+ *             of the earlier one-step work that Sec. 1 contrasts them with)
  *   X_{l,k}   length (mm) of ray l inside pixel k
  *   c^_{w,l}  counts model N_{w,l} sum_i s_{w,l,i} softexp(-sum_{m,k} mu_{m,i} X_{l,k} f_{k,m})  (Eq. finalModel)
  *   D_TPL     transmission-Poisson Kullback-Leibler data discrepancy                        (Eq. DTPL)
@@ -24,6 +26,10 @@
  *     used from one host thread at a time.
  *   - Every float4-shaped array is `float[count][4]`, 16-byte aligned, with the
  *     three materials (or four windows) in the first components.
+ *   - Per-ray window arrays (counts c and c^, the dual y) are `float[L][WS]`,
+ *     16-byte aligned, with WS = 4 for four windows and WS = 8 for five: the
+ *     windows in the first W components, the rest padding (ignored on input,
+ *     written as zero on output).  Written "float[L][WS]" below.
  */
 #ifndef OSSCIR_H_
 #define OSSCIR_H_
@@ -64,14 +70,18 @@ typedef struct {
     double bin_mm, sid_mm, sdd_mm;
 } osscir_geometry;
 
-/* Normalised spectral response and incident photons of Eq. (fullModel):
- *   s  host float[n_bins][n_energies][4]: s_{w,b,i} >= 0 with sum_i s_{w,b,i} = 1 (within 1e-4)
- *   N  host float[n_bins][4]:             N_{w,b} > 0 (photons per ray and window)
- * The response depends on the detector bin, not on the view. */
+/* Normalised spectral response and incident photons of Eq. (fullModel) over W
+ * windows (W = n_windows; 0 means 4):
+ *   s  host float[n_bins][n_energies][W]: s_{w,b,i} >= 0 with sum_i s_{w,b,i} = 1 (within 1e-4)
+ *   N  host float[n_bins][W]:             N_{w,b} > 0 (photons per ray and window)
+ * The response depends on the detector bin, not on the view.  W = 5 is taken by
+ * the single-solve entry points; the batched and served forms and nested
+ * solves (inner > 1) take four windows only (OSSCIR_E_INVALID otherwise). */
 typedef struct {
     int n_energies; /* 1 .. 256 */
     const float *s;
     const float *N;
+    int n_windows;  /* 0 or 4: four windows; 5: five */
 } osscir_spectra;
 
 /* Solver parameters.  lambda is the step-size ratio of the step-preconditioner
@@ -159,12 +169,12 @@ osscir_status osscir_forward(osscir_t h, const float *x, float *g, void *stream)
 osscir_status osscir_backproject(osscir_t h, const float *rf, float *img, void *stream);
 
 /* Expected counts c^(f) of Eq. (finalModel) for material maps f.
- *   f: device float[P][4] (first three components used), chat: device float[L][4] (output). */
+ *   f: device float[P][4] (first three components used), chat: device float[L][WS] (output). */
 osscir_status osscir_simulate(osscir_t h, const float *f, float *chat, void *stream);
 
 /* Load measured counts c_{w,l} (Eq. DTPL) and reset the solver state to
  * x_0 = xbar_0 = 0, y_0 = 0, iteration 0.
- *   c: device float[L][4], c >= 0 and finite (copied on the stream).
+ *   c: device float[L][WS], c >= 0 and finite (copied on the stream).
  * The counts are checked on the device, on the stream, after the copy; the
  * call itself does not wait for the check.  The next osscir_dtpl returns
  * OSSCIR_E_INVALID if any count was negative or not finite (the iterations in
@@ -206,7 +216,7 @@ osscir_status osscir_mocca_partial(osscir_t h, int v0, int v1, float *chan, void
 osscir_status osscir_mocca_apply(osscir_t h, const float *chan, void *stream);
 
 /* End-to-end reconstruction with host buffers: copies the counts c (host
- * float[L][4], c >= 0; pinned memory makes the copy asynchronous DMA) to the
+ * float[L][WS], c >= 0; pinned memory makes the copy asynchronous DMA) to the
  * device, resets the state as osscir_set_counts does, runs n_iters MOCCA
  * iterations and copies the maps x_n to maps_out (host float[P][4]).
  * Synchronises the stream before returning.  Errors: OSSCIR_E_INVALID (NULL
@@ -230,7 +240,7 @@ osscir_status osscir_last_kernel_ms(osscir_t h, float *ms, void *stream);
 osscir_status osscir_get_maps(osscir_t h, float *x_out, void *stream);
 
 /* Checkpoint / resume of the solver state (x_n, xbar_n, y_n, n).  All arrays
- * are device pointers: x, xbar float[P][4], y float[L][4].  get copies out,
+ * are device pointers: x, xbar float[P][4], y float[L][WS].  get copies out,
  * set copies in; resuming from a saved state reproduces the uninterrupted
  * iterates bit for bit.  iter: host int.  The kept local models of a nested
  * solve are not part of the state: the first iteration after set is an outer one. */
@@ -406,6 +416,8 @@ osscir_status osscir_server_info(osscir_server_t s, int *running, int *queued, s
  * allocation may cause; osscir_dtpl needs a context, and creating one allocates.
  *   chat, c: device float[n_rays][4];  out: device double (written on the stream).
  *   n_rays: 1 .. 4,194,304 (larger values return OSSCIR_E_INVALID).
+ *   Five-window arrays float[L][8] pass as n_rays = 2 L when their padding is
+ *   zero (a term with c = c^ = 0 is zero).
  * Scratch: a fixed 128 KiB array of per-block partial sums inside the library's
  * device memory, held by every GPU that loads the library until the process
  * exits.  The first call on a device looks up that array's device address (with

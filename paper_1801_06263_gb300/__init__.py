@@ -11,7 +11,7 @@ from . import inputs
 from ._lib import (OsscirError, load, osscir_backproject, osscir_create, osscir_destroy, osscir_dtpl,
                    osscir_footprint_pixels, osscir_footprint_rays, osscir_forward, osscir_get_maps,
                    osscir_get_state, osscir_info, osscir_mocca_step, osscir_set_counts, osscir_set_state,
-                   osscir_simulate)
+                   osscir_simulate, window_stride)
 
 __all__ = ["inputs", "Reconstructor", "Batch", "OsscirError", "load"]
 
@@ -20,7 +20,8 @@ class Reconstructor:
     """One reconstruction context on the current CUDA device.
 
     Device arrays are torch float32 tensors: maps [P, 4] (PMMA, Al, Gd, unused),
-    ray fields [L, 4] (four windows or four channels).
+    projections [L, 4] (four channels), per-ray window arrays (counts, dual)
+    [L, WS] with WS = 4 for four windows and 8 for five (windows first, zero padding).
     """
 
     def __init__(self, geom, spectra, lam: float, *, model: int = 0, box=None, mu=None, spc: int = 0,
@@ -33,6 +34,8 @@ class Reconstructor:
                                     model=model, box=box, spc=spc, counts_model=counts_model,
                                     inner=inner)
         self.n_pixels, self.n_rays, self.n_fp64_pairs = osscir_info(self.handle)
+        self.n_windows = int(spectra.s.shape[2])
+        self.window_stride = window_stride(self.n_windows)
 
     # -- tensors
     def _new(self, rows):
@@ -44,6 +47,19 @@ class Reconstructor:
 
     def rays(self):
         return self._new(self.n_rays)
+
+    def window_rays(self):
+        import torch
+        return torch.zeros((self.n_rays, self.window_stride), dtype=torch.float32, device="cuda")
+
+    def _windows(self, c):
+        """Counts [L, W] or [L, WS] as the library's [L, WS] layout (zero padding added)."""
+        import torch
+        if c.dim() == 2 and c.shape[1] == self.n_windows and self.n_windows != self.window_stride:
+            out = torch.zeros((c.shape[0], self.window_stride), dtype=c.dtype, device=c.device)
+            out[:, :self.n_windows] = c
+            return out
+        return c
 
     # -- operators
     def forward(self, x, out=None, stream=None):
@@ -57,13 +73,15 @@ class Reconstructor:
         return out
 
     def simulate(self, f, out=None, stream=None):
-        out = self.rays() if out is None else out
+        out = self.window_rays() if out is None else out
         osscir_simulate(self.handle, f, out, stream)
         return out
 
     # -- solver
     def set_counts(self, c, stream=None):
+        c = self._windows(c)
         osscir_set_counts(self.handle, c, stream)
+        self._counts = c   # the copy runs on the stream: keep a padded temporary alive until it has
 
     def step(self, n_iters: int, stream=None):
         osscir_mocca_step(self.handle, n_iters, stream)
@@ -77,7 +95,7 @@ class Reconstructor:
         return osscir_dtpl(self.handle, which, stream)
 
     def get_state(self, stream=None):
-        x, xbar, y = self.image(), self.image(), self.rays()
+        x, xbar, y = self.image(), self.image(), self.window_rays()
         it = osscir_get_state(self.handle, x, xbar, y, stream)
         return x, xbar, y, it
 

@@ -49,7 +49,8 @@ class Geometry(ct.Structure):
 
 
 class Spectra(ct.Structure):
-    _fields_ = [("n_energies", ct.c_int), ("s", ct.POINTER(ct.c_float)), ("N", ct.POINTER(ct.c_float))]
+    _fields_ = [("n_energies", ct.c_int), ("s", ct.POINTER(ct.c_float)), ("N", ct.POINTER(ct.c_float)),
+                ("n_windows", ct.c_int)]
 
 
 class Params(ct.Structure):
@@ -183,16 +184,23 @@ def _params(lam, model=0, box=None, spc=0, counts_model=0, inner=1):
                   int(spc), int(counts_model), int(inner))
 
 
+def window_stride(n_windows: int) -> int:
+    """Floats per ray of the per-ray window arrays (counts, dual): 4 for four windows, 8 for five."""
+    return 4 * ((int(n_windows) + 3) // 4)
+
+
 def osscir_create(geom, s, N, mu, lam, model=0, box=None, spc=0, counts_model=0, inner=1):
-    """geom: object with the osscir_geometry fields; s [n_bins, nE, 4], N [n_bins, 4],
-    mu [3, nE] host arrays (copied).  Returns the handle (int)."""
+    """geom: object with the osscir_geometry fields; s [n_bins, nE, W], N [n_bins, W]
+    (W = 4 or 5 windows), mu [3, nE] host arrays (copied).  Returns the handle (int)."""
     L = load()
     s32 = np.ascontiguousarray(s, dtype=np.float32)
     N32 = np.ascontiguousarray(N, dtype=np.float32)
     mu32 = np.ascontiguousarray(mu, dtype=np.float32)
+    if s32.ndim != 3 or N32.shape != (s32.shape[0], s32.shape[2]):
+        raise ValueError("s must be [n_bins, nE, W] and N [n_bins, W]")
     g = _geometry(geom)
     sp = Spectra(int(s32.shape[1]), s32.ctypes.data_as(ct.POINTER(ct.c_float)),
-                 N32.ctypes.data_as(ct.POINTER(ct.c_float)))
+                 N32.ctypes.data_as(ct.POINTER(ct.c_float)), int(s32.shape[2]))
     p = _params(lam, model, box, spc, counts_model, inner)
     h = ct.c_void_p()
     _check("osscir_create", L.osscir_create(ct.byref(g), ct.byref(sp),
@@ -283,7 +291,7 @@ def osscir_mocca_apply(h, chan, stream=None):
 
 
 def osscir_reconstruct(h, c_host, n_iters, maps_out_host, stream=None):
-    """c_host [L, 4] and maps_out_host [P, 4]: contiguous float32 CPU tensors (pinned for DMA)."""
+    """c_host [L, WS] and maps_out_host [P, 4]: contiguous float32 CPU tensors (pinned for DMA)."""
     if c_host.is_cuda or maps_out_host.is_cuda:
         raise ValueError("osscir_reconstruct takes host buffers")
     _check("osscir_reconstruct", load().osscir_reconstruct(ct.c_void_p(h), _ptr(c_host), int(n_iters),
@@ -333,7 +341,7 @@ def osscir_submit(server, geom, s, N, mu, lam, counts, n_iters, model=0, box=Non
     mu32 = np.ascontiguousarray(mu, dtype=np.float32)
     c32 = np.ascontiguousarray(counts, dtype=np.float32)
     fptr = lambda a: a.ctypes.data_as(ct.POINTER(ct.c_float))
-    req = Request(_geometry(geom), Spectra(int(s32.shape[1]), fptr(s32), fptr(N32)), fptr(mu32),
+    req = Request(_geometry(geom), Spectra(int(s32.shape[1]), fptr(s32), fptr(N32), int(s32.shape[2])), fptr(mu32),
                   _params(lam, model, box, spc, counts_model, inner), fptr(c32), int(n_iters))
     t = ct.c_uint64()
     _check("osscir_submit", load().osscir_submit(ct.c_void_p(server), ct.byref(req), ct.byref(t)))

@@ -602,8 +602,8 @@ osscir_status osscir_batch_create(const osscir_t* solves, int n, int autotune_fl
     if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return OSSCIR_E_INVALID;
     int dev = 0;
     CK(cudaGetDevice(&dev));
-    for (osscir_ctx* h : v)   // nested solves (inner > 1) step on their own
-        if (h->device != dev || h->inner > 1) return OSSCIR_E_INVALID;
+    for (osscir_ctx* h : v)   // nested solves (inner > 1) step on their own; the batched kernels take four windows
+        if (h->device != dev || h->inner > 1 || h->nw != 4) return OSSCIR_E_INVALID;
     // work already queued on the solves (on any stream) must be done before the
     // autotuner saves their state
     CK(cudaDeviceSynchronize());

@@ -63,19 +63,25 @@ void free_ctx(osscir_ctx* h) {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
-// Measured counts must be finite and >= 0 (Eq. DTPL takes c log c).
-bool counts_valid(const float* c, size_t n) {
-    for (size_t i = 0; i < n; ++i)
-        if (!(c[i] >= 0.0f) || !std::isfinite(c[i])) return false;
+// Measured counts must be finite and >= 0 (Eq. DTPL takes c log c).  c holds L
+// rays of `stride` floats, of which the first W are the windows (the rest is padding).
+bool counts_valid(const float* c, size_t L, int stride, int W) {
+    for (size_t l = 0; l < L; ++l)
+        for (int w = 0; w < W; ++w) {
+            const float v = c[l * stride + w];
+            if (!(v >= 0.0f) || !std::isfinite(v)) return false;
+        }
     return true;
 }
 
 // The same check on device counts: any invalid value sets *bad (never cleared here).
-__global__ void k_check_counts(const float4* __restrict__ c, int L, int* bad) {
+__global__ void k_check_counts(const float* __restrict__ c, int L, int stride, int W, int* bad) {
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < L; l += gridDim.x * blockDim.x) {
-        const float4 v = c[l];
-        const bool ok = v.x >= 0.0f && v.y >= 0.0f && v.z >= 0.0f && v.w >= 0.0f && isfinite(v.x) &&
-                        isfinite(v.y) && isfinite(v.z) && isfinite(v.w);
+        bool ok = true;
+        for (int w = 0; w < W; ++w) {
+            const float v = c[(size_t)l * stride + w];
+            ok = ok && v >= 0.0f && isfinite(v);
+        }
         if (!ok) *bad = 1;
     }
 }
@@ -163,6 +169,9 @@ __global__ void k_maps_out(const float4* __restrict__ x, Basis3 B, float4* __res
                          (float)(B.m[6] * a + B.m[7] * b + B.m[8] * c), 0.f);
 }
 
+// Energy windows of a spectra struct (0 means the default four).
+int n_windows(const osscir_spectra* sp) { return sp->n_windows == 0 ? 4 : sp->n_windows; }
+
 osscir_status validate(const osscir_geometry* g, const osscir_spectra* sp, const float* mu,
                        const osscir_params* pa) {
     if (!g || !sp || !mu || !pa || !sp->s || !sp->N) return OSSCIR_E_INVALID;
@@ -174,17 +183,19 @@ osscir_status validate(const osscir_geometry* g, const osscir_spectra* sp, const
     const double rc = g->n * g->pixel_mm * std::sqrt(2.0) / 2.0;
     if (!(g->sid_mm > rc) || !(g->sdd_mm > g->sid_mm)) return OSSCIR_E_INVALID;
     if (sp->n_energies < 1 || sp->n_energies > 256) return OSSCIR_E_INVALID;
-    const int nE = sp->n_energies;
+    const int nE = sp->n_energies, W = n_windows(sp);
+    if (W != 4 && W != 5) return OSSCIR_E_INVALID;
+    if (W != 4 && pa->inner > 1) return OSSCIR_E_INVALID;   // nested MOCCA keeps four-window models
     for (int b = 0; b < g->n_bins; ++b) {
-        for (int w = 0; w < 4; ++w) {
+        for (int w = 0; w < W; ++w) {
             double sum = 0.0;
             for (int i = 0; i < nE; ++i) {
-                const float v = sp->s[((size_t)b * nE + i) * 4 + w];
+                const float v = sp->s[((size_t)b * nE + i) * W + w];
                 if (!std::isfinite(v) || v < 0.f) return OSSCIR_E_INVALID;
                 sum += v;
             }
             if (std::fabs(sum - 1.0) > 1e-4) return OSSCIR_E_INVALID;
-            if (!finite_pos(sp->N[(size_t)b * 4 + w])) return OSSCIR_E_INVALID;
+            if (!finite_pos(sp->N[(size_t)b * W + w])) return OSSCIR_E_INVALID;
         }
     }
     for (int i = 0; i < 3 * nE; ++i)   // a transformed basis (mu-PC) may have negative curves
@@ -215,6 +226,7 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     h->P = n * n;
     h->L = g->n_views * g->n_bins;
     h->nE = sp->n_energies;
+    h->nw = n_windows(sp);
     GeomD& G = h->g64;
     G.n = n;
     G.h = g->pixel_mm;
@@ -256,16 +268,17 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     CK(dalloc(&h->views, g->n_views));
     CK(dalloc(&h->chord, L));
     CK(dalloc(&h->exc_off, L + 1));
-    CK(dalloc(&h->s4, (size_t)nE * g->n_bins));
-    CK(dalloc(&h->N4, g->n_bins));
+    const int W = h->nw, F4 = h->wf4();
+    CK(dalloc(&h->s4, (size_t)nE * g->n_bins * F4));
+    CK(dalloc(&h->N4, (size_t)g->n_bins * F4));
     CK(dalloc(&h->mu, 3 * nE));
     if (h->basis) {
         CK(dalloc(&h->mu_in, 3 * nE));
         CK(dalloc(&h->xo, P));
     }
     CK(dalloc(&h->g, L));
-    CK(dalloc(&h->c, L));
-    CK(dalloc(&h->y, L));
+    CK(dalloc(&h->c, (size_t)L * F4));
+    CK(dalloc(&h->y, (size_t)L * F4));
     CK(dalloc(&h->x, P));
     CK(dalloc(&h->xbar, P));
     CK(dalloc(&h->dtpl_part, h->n_part));
@@ -279,15 +292,19 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     CK(cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming));
     cudaStream_t st = h->cap_stream;
 
-    // spectral tables: s reordered to [nE][n_bins] float4 so consecutive rays read consecutive entries
+    // spectral tables: s reordered to [nE][n_bins] window vectors (4 F4 floats, zero padded)
+    // so consecutive rays read consecutive entries
     {
-        std::vector<float> s4((size_t)nE * g->n_bins * 4);
+        const int S = 4 * F4;
+        std::vector<float> s4((size_t)nE * g->n_bins * S, 0.0f), N4((size_t)g->n_bins * S, 0.0f);
         for (int b = 0; b < g->n_bins; ++b)
             for (int i = 0; i < nE; ++i)
-                for (int w = 0; w < 4; ++w)
-                    s4[((size_t)i * g->n_bins + b) * 4 + w] = sp->s[((size_t)b * nE + i) * 4 + w];
+                for (int w = 0; w < W; ++w)
+                    s4[((size_t)i * g->n_bins + b) * S + w] = sp->s[((size_t)b * nE + i) * W + w];
+        for (int b = 0; b < g->n_bins; ++b)
+            for (int w = 0; w < W; ++w) N4[(size_t)b * S + w] = sp->N[(size_t)b * W + w];
         CK(cudaMemcpy(h->s4, s4.data(), s4.size() * sizeof(float), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(h->N4, sp->N, sizeof(float) * 4 * g->n_bins, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->N4, N4.data(), N4.size() * sizeof(float), cudaMemcpyHostToDevice));
         if (h->basis) {
             std::vector<double> mu_t;
             if (!mu_pc_basis(mu, nE, h->Mb, mu_t)) return OSSCIR_E_INVALID;
@@ -317,8 +334,8 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     CK(dalloc(&h->exc_ent, run));
     CK(launch_exc_pass(C, G, h->rec, h->r64, nullptr, h->exc_off, h->exc_ent, st));
     CK(launch_chord(C, h->exc(), h->rec, h->chord, st));
-    CK(cudaMemsetAsync(h->c, 0, sizeof(float4) * L, st));
-    CK(cudaMemsetAsync(h->y, 0, sizeof(float4) * L, st));
+    CK(cudaMemsetAsync(h->c, 0, sizeof(float4) * L * F4, st));
+    CK(cudaMemsetAsync(h->y, 0, sizeof(float4) * L * F4, st));
     CK(cudaMemsetAsync(h->x, 0, sizeof(float4) * P, st));
     CK(cudaMemsetAsync(h->xbar, 0, sizeof(float4) * P, st));
     CK(cudaMemsetAsync(h->dtpl_out, 0, sizeof(double) * 2, st));
@@ -675,11 +692,13 @@ osscir_status osscir_simulate(osscir_t h, const float* f, float* chat, void* str
 osscir_status osscir_set_counts(osscir_t h, const float* c, void* stream) {
     if (!h || !c) return OSSCIR_E_INVALID;
     cudaStream_t st = as_stream(stream);
-    CK(cudaMemcpyAsync(h->c, c, sizeof(float4) * h->L, cudaMemcpyDeviceToDevice, st));
+    const size_t ray_bytes = sizeof(float4) * h->wf4() * h->L;
+    CK(cudaMemcpyAsync(h->c, c, ray_bytes, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemsetAsync(h->bad_counts, 0, sizeof(int), st));
-    k_check_counts<<<std::min((h->L + 255) / 256, 1024), 256, 0, st>>>(h->c, h->L, h->bad_counts);
+    k_check_counts<<<std::min((h->L + 255) / 256, 1024), 256, 0, st>>>(
+        reinterpret_cast<const float*>(h->c), h->L, 4 * h->wf4(), h->nw, h->bad_counts);
     CK(cudaGetLastError());
-    CK(cudaMemsetAsync(h->y, 0, sizeof(float4) * h->L, st));
+    CK(cudaMemsetAsync(h->y, 0, ray_bytes, st));
     CK(cudaMemsetAsync(h->x, 0, sizeof(float4) * h->P, st));
     CK(cudaMemsetAsync(h->xbar, 0, sizeof(float4) * h->P, st));
     h->iter = 0;
@@ -725,10 +744,11 @@ osscir_status osscir_mocca_apply(osscir_t h, const float* chan, void* stream) {
 osscir_status osscir_reconstruct(osscir_t h, const float* c_host, int n_iters, float* maps_out_host,
                                  void* stream) {
     if (!h || !c_host || !maps_out_host || n_iters < 0) return OSSCIR_E_INVALID;
-    if (!counts_valid(c_host, (size_t)4 * h->L)) return OSSCIR_E_INVALID;
+    if (!counts_valid(c_host, h->L, 4 * h->wf4(), h->nw)) return OSSCIR_E_INVALID;
     cudaStream_t st = as_stream(stream);
-    CK(cudaMemcpyAsync(h->c, c_host, sizeof(float4) * h->L, cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(h->y, 0, sizeof(float4) * h->L, st));
+    const size_t ray_bytes = sizeof(float4) * h->wf4() * h->L;
+    CK(cudaMemcpyAsync(h->c, c_host, ray_bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(h->y, 0, ray_bytes, st));
     CK(cudaMemsetAsync(h->x, 0, sizeof(float4) * h->P, st));
     CK(cudaMemsetAsync(h->xbar, 0, sizeof(float4) * h->P, st));
     h->iter = 0;
@@ -770,7 +790,7 @@ osscir_status osscir_get_state(osscir_t h, float* x, float* xbar, float* y, int*
     cudaStream_t st = as_stream(stream);
     CK(cudaMemcpyAsync(x, h->x, sizeof(float4) * h->P, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(xbar, h->xbar, sizeof(float4) * h->P, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(y, h->y, sizeof(float4) * h->L, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(y, h->y, sizeof(float4) * h->wf4() * h->L, cudaMemcpyDeviceToDevice, st));
     if (iter) *iter = h->iter;
     return OSSCIR_OK;
 }
@@ -781,7 +801,7 @@ osscir_status osscir_set_state(osscir_t h, const float* x, const float* xbar, co
     cudaStream_t st = as_stream(stream);
     CK(cudaMemcpyAsync(h->x, x, sizeof(float4) * h->P, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(h->xbar, xbar, sizeof(float4) * h->P, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(h->y, y, sizeof(float4) * h->L, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(h->y, y, sizeof(float4) * h->wf4() * h->L, cudaMemcpyDeviceToDevice, st));
     h->iter = iter;
     h->phase = 0;
     return OSSCIR_OK;

@@ -200,9 +200,12 @@ __global__ void k_backproject4(GeomC C, ExcTable E, const RayRec* rec, const Vie
 }
 
 // c^(f) (Eq. finalModel) for every ray; with c != nullptr also the D_TPL block partials.
+// W windows; chat and c hold win_f4<W>() float4 per ray.
+template <int W>
 __global__ void __launch_bounds__(kFwdThreads) k_counts(GeomC C, ExcTable E, const RayRec* rec, SpecD S,
                                                         const float4* f, float4* chat, const float4* c,
                                                         double* part) {
+    constexpr int F4 = win_f4<W>();
     __shared__ float sm[kSmemStride * kMaxEnergies];
     load_mu_smem(S, sm);
     __syncthreads();
@@ -215,26 +218,29 @@ __global__ void __launch_bounds__(kFwdThreads) k_counts(GeomC C, ExcTable E, con
         const float4 gs = acc.sum();
         const float g0 = gs.x, g1 = gs.y, g2 = gs.z;
         const int b = l % C.n_bins, nb = C.n_bins;
-        float Ds[4] = {0.f, 0.f, 0.f, 0.f}, Dc[4] = {0.f, 0.f, 0.f, 0.f};
+        float Ds[W], Dc[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) Ds[w] = Dc[w] = 0.f;
         for (int i = 0; i < S.n_energies; ++i) {
             const float* q = sm + kSmemStride * i;
             const float p = fmaf(q[2], g2, fmaf(q[1], g1, q[0] * g0));
             float e0, e1, e2;
             sexp3(-p, S.exp_model != 0, e0, e1, e2);
-            const float4 s = __ldg(S.s4 + (size_t)i * nb + b);
-            neumaier(Ds[0], Dc[0], s.x * e0);
-            neumaier(Ds[1], Dc[1], s.y * e0);
-            neumaier(Ds[2], Dc[2], s.z * e0);
-            neumaier(Ds[3], Dc[3], s.w * e0);
+            float sv[W];
+            win_load<W, true>(S.s4 + F4 * ((size_t)i * nb + b), sv);
+#pragma unroll
+            for (int w = 0; w < W; ++w) neumaier(Ds[w], Dc[w], sv[w] * e0);
         }
-        const float4 N = __ldg(S.N4 + b);
-        const float4 ch = make_float4(N.x * (Ds[0] + Dc[0]), N.y * (Ds[1] + Dc[1]), N.z * (Ds[2] + Dc[2]),
-                                      N.w * (Ds[3] + Dc[3]));
-        if (chat) chat[l] = ch;
+        float Nv[W], ch[W];
+        win_load<W, true>(S.N4 + F4 * b, Nv);
+#pragma unroll
+        for (int w = 0; w < W; ++w) ch[w] = Nv[w] * (Ds[w] + Dc[w]);
+        if (chat) win_store<W>(chat + F4 * (size_t)l, ch);
         if (c) {
-            const float4 cc = c[l];
-            dsum = (double)dtpl_term(ch.x, cc.x) + (double)dtpl_term(ch.y, cc.y) + (double)dtpl_term(ch.z, cc.z) +
-                   (double)dtpl_term(ch.w, cc.w);
+            float cv[W];
+            win_load<W>(c + F4 * (size_t)l, cv);
+#pragma unroll
+            for (int w = 0; w < W; ++w) dsum += (double)dtpl_term(ch[w], cv[w]);
         }
     }
     if (part) warp_partial(C, blockIdx.x, warp_view(blockIdx.y, kFwdThreads / 32), dsum, part);
@@ -438,6 +444,15 @@ __device__ __forceinline__ bool inv_sym3(const double a[6], double o[6]) {
     return true;
 }
 
+// Sum of W double-float terms as a fixed tree: the first four pairwise, then the rest in order.
+template <int W>
+__device__ __forceinline__ dfl df_tree(const dfl (&v)[W]) {
+    dfl acc = df_add(df_add(v[0], v[1]), df_add(v[2], v[3]));
+#pragma unroll
+    for (int w = 4; w < W; ++w) acc = df_add(acc, v[w]);
+    return acc;
+}
+
 // Dual step of one ray that meets the image (see the file header).
 //   al: window-effective attenuations alpha (FP32), sinv: Sigma^-1 (FP32),
 //   cw: counts (FP32, exact), r: residuals (double-float), Bt: sum_i beta_i mu_i mu_i^T
@@ -450,16 +465,16 @@ __device__ __forceinline__ bool inv_sym3(const double a[6], double o[6]) {
 // number near 1e7): the Hessian H = sum_w c_w alpha_w alpha_w^T - Bt from exact
 // products, its Sylvester test, and the algebra after the clip; only a Hessian
 // that fails the test goes through the FP64 eigen-clip.  Returns y' in yo.
-template <bool KEEP>
-__device__ void ray_dual(const float al[4][3], const float sinv[4], const float cw[4], const dfl r[4],
-                         const float Bt[6], const float y[4], float yo[4], float Bm[4][4]) {
+template <bool KEEP, int W>
+__device__ void ray_dual(const float (&al)[W][3], const float (&sinv)[W], const float (&cw)[W], const dfl (&r)[W],
+                         const float Bt[6], const float (&y)[W], float (&yo)[W], float (&Bm)[W][W]) {
     const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
     dfl H[6];
 #pragma unroll
     for (int e = 0; e < 6; ++e) {
         dfl acc = {-Bt[e], 0.0f};
 #pragma unroll
-        for (int w = 0; w < 4; ++w) acc = df_add(acc, df_mulf(df_2prod(al[w][ij[e][0]], al[w][ij[e][1]]), cw[w]));
+        for (int w = 0; w < W; ++w) acc = df_add(acc, df_mulf(df_2prod(al[w][ij[e][0]], al[w][ij[e][1]]), cw[w]));
         H[e] = acc;
     }
     {
@@ -483,7 +498,7 @@ __device__ void ray_dual(const float al[4][3], const float sinv[4], const float 
     for (int e = 0; e < 6; ++e) {
         dfl acc = df_2prod(al[0][ij[e][0]], al[0][ij[e][1]]);
 #pragma unroll
-        for (int w = 1; w < 4; ++w) acc = df_add(acc, df_2prod(al[w][ij[e][0]], al[w][ij[e][1]]));
+        for (int w = 1; w < W; ++w) acc = df_add(acc, df_2prod(al[w][ij[e][0]], al[w][ij[e][1]]));
         A[e] = acc;
     }
     // A^-1 by the adjugate
@@ -498,10 +513,10 @@ __device__ void ray_dual(const float al[4][3], const float sinv[4], const float 
         const dfl det = df_add(df_add(df_mul(A[0], c00), df_mul(A[1], c01)), df_mul(A[2], c02));
         if (!(det.hi != 0.0f) || !isfinite(det.hi)) {   // degenerate alpha: no curvature term, y' = r
 #pragma unroll
-            for (int w = 0; w < 4; ++w) yo[w] = df_f(r[w]);
+            for (int w = 0; w < W; ++w) yo[w] = df_f(r[w]);
             if (KEEP)
-                for (int w = 0; w < 4; ++w)
-                    for (int j = 0; j < 4; ++j) Bm[w][j] = 0.0f;
+                for (int w = 0; w < W; ++w)
+                    for (int j = 0; j < W; ++j) Bm[w][j] = 0.0f;
             return;
         }
         const dfl id = df_rcp(det);
@@ -509,29 +524,34 @@ __device__ void ray_dual(const float al[4][3], const float sinv[4], const float 
         Ai[3] = df_mul(c11, id); Ai[4] = df_mul(c12, id); Ai[5] = df_mul(c22, id);
     }
     const int sidx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};   // packed index of (i, j)
-    dfl G[3][4], Gs[3][4];
+    dfl G[3][W], Gs[3][W];
 #pragma unroll
     for (int m = 0; m < 3; ++m)
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
+        for (int w = 0; w < W; ++w) {
             G[m][w] = df_add(df_add(df_mulf(Ai[sidx[m][0]], al[w][0]), df_mulf(Ai[sidx[m][1]], al[w][1])),
                              df_mulf(Ai[sidx[m][2]], al[w][2]));
             Gs[m][w] = df_mulf(G[m][w], sinv[w]);
         }
-    dfl d[4];
+    dfl d[W];
 #pragma unroll
-    for (int w = 0; w < 4; ++w) d[w] = df_sub(dfl{y[w], 0.0f}, r[w]);
+    for (int w = 0; w < W; ++w) d[w] = df_sub(dfl{y[w], 0.0f}, r[w]);
     dfl F[6], phi[3];
 #pragma unroll
     for (int e = 0; e < 6; ++e) {
         const int m = ij[e][0], n = ij[e][1];
-        F[e] = df_add(df_add(df_mul(Gs[m][0], G[n][0]), df_mul(Gs[m][1], G[n][1])),
-                      df_add(df_mul(Gs[m][2], G[n][2]), df_mul(Gs[m][3], G[n][3])));
+        dfl t[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) t[w] = df_mul(Gs[m][w], G[n][w]);
+        F[e] = df_tree(t);
     }
 #pragma unroll
-    for (int m = 0; m < 3; ++m)
-        phi[m] = df_add(df_add(df_mul(Gs[m][0], d[0]), df_mul(Gs[m][1], d[1])),
-                        df_add(df_mul(Gs[m][2], d[2]), df_mul(Gs[m][3], d[3])));
+    for (int m = 0; m < 3; ++m) {
+        dfl t[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) t[w] = df_mul(Gs[m][w], d[w]);
+        phi[m] = df_tree(t);
+    }
     // Mx = I + H+ F (3 x 3), rhs = H+ phi
     dfl Mx[3][3], rhs[3];
 #pragma unroll
@@ -563,12 +583,12 @@ __device__ void ray_dual(const float al[4][3], const float sinv[4], const float 
     for (int i = 0; i < 3; ++i)
         z[i] = df_mul(idet, df_add(df_add(df_mul(C[i][0], rhs[0]), df_mul(C[i][1], rhs[1])), df_mul(C[i][2], rhs[2])));
 #pragma unroll
-    for (int w = 0; w < 4; ++w)
+    for (int w = 0; w < W; ++w)
         yo[w] = df_f(df_add(r[w], df_add(df_add(df_mul(G[0][w], z[0]), df_mul(G[1][w], z[1])), df_mul(G[2][w], z[2]))));
     if (KEEP) {
         // the linear map of the prox: y' = r + B (u - r), column j from the same solve with
         // Sigma^-1 e_j in place of Sigma^-1 (y - r), i.e. right-hand side H+ Gs[:, j]
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < W; ++j) {
             dfl q[3], zj[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i)
@@ -578,7 +598,7 @@ __device__ void ray_dual(const float al[4][3], const float sinv[4], const float 
             for (int i = 0; i < 3; ++i)
                 zj[i] = df_mul(idet, df_add(df_add(df_mul(C[i][0], q[0]), df_mul(C[i][1], q[1])), df_mul(C[i][2], q[2])));
 #pragma unroll
-            for (int w = 0; w < 4; ++w)
+            for (int w = 0; w < W; ++w)
                 Bm[w][j] = df_f(df_add(df_add(df_mul(G[0][w], zj[0]), df_mul(G[1][w], zj[1])), df_mul(G[2][w], zj[2])));
         }
     }
@@ -611,9 +631,11 @@ __global__ void __launch_bounds__(kFwdThreads, 8) k_mocca_proj(GeomC C, ExcTable
 
 // a2-a5 and the per-ray half of a8: spectral model, curvature, dual step.
 // Returns the ray's D_TPL terms; sm holds the block's mu table (load_mu_smem).
-template <bool KEEP>
+template <bool KEEP, int W>
 __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const SpecD& S, const StepParams& P,
                                            const SolveD& D, const float* sm, int l) {
+    static_assert(!KEEP || W == 4, "nested MOCCA keeps models of four windows");
+    constexpr int F4 = win_f4<W>();
     double dsum = 0.0;
     {
         const float4 r1 = rec[l].r1;
@@ -626,15 +648,18 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
         // summed in two levels: plain FP32 over kDFold energies, the partials
         // compensated (Neumaier)
         const int b = l % C.n_bins, nb = C.n_bins, nE = S.n_energies;
-        float Ds[4] = {0.f, 0.f, 0.f, 0.f}, Dc[4] = {0.f, 0.f, 0.f, 0.f}, An[4][3], U[4][6];
+        float Ds[W], Dc[W], An[W][3], U[W][6];
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
+        for (int w = 0; w < W; ++w) {
+            Ds[w] = Dc[w] = 0.f;
             An[w][0] = An[w][1] = An[w][2] = 0.f;
 #pragma unroll
             for (int k = 0; k < 6; ++k) U[w][k] = 0.f;
         }
         for (int i0 = 0; i0 < nE; i0 += kDFold) {
-            float Pd[4] = {0.f, 0.f, 0.f, 0.f};
+            float Pd[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) Pd[w] = 0.f;
             const int i1 = min(nE, i0 + kDFold);
 #pragma unroll 2   // two energies in flight: the s-table loads overlap
             for (int i = i0; i < i1; ++i) {
@@ -644,11 +669,11 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
                 const float p = fmaf(qa.z, g2, fmaf(qa.y, g1, qa.x * g0));
                 float e0, e1, e2;
                 sexp3(-p, S.exp_model != 0, e0, e1, e2);
-                const float4 s4 = __ldg(S.s4 + (size_t)i * nb + b);
-                const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+                float sv[W];
+                win_load<W, true>(S.s4 + F4 * ((size_t)i * nb + b), sv);
                 const float mm[6] = {qa.w, qb.x, qb.y, qb.z, qb.w, qc.x};
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
+                for (int w = 0; w < W; ++w) {
                     Pd[w] = fmaf(sv[w], e0, Pd[w]);
                     const float a = sv[w] * e1, c2 = sv[w] * e2;
                     An[w][0] = fmaf(a, qa.x, An[w][0]);
@@ -659,17 +684,17 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
                 }
             }
 #pragma unroll
-            for (int w = 0; w < 4; ++w) neumaier(Ds[w], Dc[w], Pd[w]);
+            for (int w = 0; w < W; ++w) neumaier(Ds[w], Dc[w], Pd[w]);
         }
-        const float4 N = __ldg(S.N4 + b);
-        const float4 cc = D.c[l];
-        const float4 yy = D.y[l];
-        const float Nv[4] = {N.x, N.y, N.z, N.w}, cv[4] = {cc.x, cc.y, cc.z, cc.w};
-        float al[4][3], qw[4], nw[4];
-        dfl rw[4];   // r = c - N D exactly to double-float precision (N D is an exact product)
+        float Nv[W], cv[W], y[W];
+        win_load<W, true>(S.N4 + F4 * b, Nv);
+        win_load<W>(D.c + F4 * (size_t)l, cv);
+        win_load<W>(D.y + F4 * (size_t)l, y);
+        float al[W][3], qw[W], nw[W];
+        dfl rw[W];   // r = c - N D exactly to double-float precision (N D is an exact product)
         float dt = 0.f;
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
+        for (int w = 0; w < W; ++w) {
             const float Dw = Ds[w] + Dc[w];
             const float invD = 1.0f / Dw;
 #pragma unroll
@@ -682,49 +707,51 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
         }
         dsum = (double)dt;
         const float X1 = __ldg(D.chord + l);
-        const float y[4] = {yy.x, yy.y, yy.z, yy.w};
-        float yo[4];
-        float Bm[4][4], sinv[4];   // the prox map and Sigma^-1, kept for nested MOCCA
+        float yo[W];
+        float Bm[W][W], sinv[W];   // the prox map and Sigma^-1, kept for nested MOCCA
         // a5: dual step matrix.  m-block SPC: (Sigma^-1)_w = lambda sum_k sqrt(sum_m K^2)
         // = lambda |alpha_w| (X 1)_l;  diagonal SPC: lambda sum_mk |K| = lambda (sum_m |alpha_wm|) (X 1)_l
         auto sigma_inv = [&]() {
 #pragma unroll
-            for (int w = 0; w < 4; ++w)
+            for (int w = 0; w < W; ++w)
                 sinv[w] = P.lambda * X1 *
                           (P.spc == 0 ? nw[w] : fabsf(al[w][0]) + fabsf(al[w][1]) + fabsf(al[w][2]));
         };
         if (!(X1 > 0.f)) {   // the ray misses the image: Sigma^-1 = 0, the dual is kept
 #pragma unroll
-            for (int w = 0; w < 4; ++w) yo[w] = y[w];
+            for (int w = 0; w < W; ++w) yo[w] = y[w];
         } else if (P.model == 1) {   // W = 0: y' = y - Sigma Sigma^-1 (y - r) = r
 #pragma unroll
-            for (int w = 0; w < 4; ++w) yo[w] = df_f(rw[w]);
+            for (int w = 0; w < W; ++w) yo[w] = df_f(rw[w]);
             if (KEEP) {
                 sigma_inv();
-                for (int w = 0; w < 4; ++w)
-                    for (int j = 0; j < 4; ++j) Bm[w][j] = 0.0f;
+                for (int w = 0; w < W; ++w)
+                    for (int j = 0; j < W; ++j) Bm[w][j] = 0.0f;
             }
         } else if (P.model == 3) {   // W = diag(c): y'_w = r_w + c_w sinv_w / (c_w sinv_w + 1) (y_w - r_w)
             sigma_inv();
 #pragma unroll
-            for (int w = 0; w < 4; ++w) {
+            for (int w = 0; w < W; ++w) {
                 const float cs = cv[w] * sinv[w], f = cs / (cs + 1.0f);
                 yo[w] = df_f(df_add(rw[w], df_mulf(df_sub(dfl{y[w], 0.0f}, rw[w]), f)));
                 if (KEEP)
-                    for (int j = 0; j < 4; ++j) Bm[w][j] = j == w ? f : 0.0f;
+                    for (int j = 0; j < W; ++j) Bm[w][j] = j == w ? f : 0.0f;
             }
         } else {
             // model 0: sum_i beta_i mu_i mu_i^T = sum_w (r_w / D_w) U_w is subtracted from
             // sum_w c_w alpha_w alpha_w^T; model 2 (Gauss-Newton) keeps the first term alone
             float Bt[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k)
-                Bt[k] = P.model == 2 ? 0.0f
-                                     : fmaf(qw[3], U[3][k], fmaf(qw[2], U[2][k], fmaf(qw[1], U[1][k], qw[0] * U[0][k])));
+            for (int k = 0; k < 6; ++k) {
+                float t = qw[0] * U[0][k];
+#pragma unroll
+                for (int w = 1; w < W; ++w) t = fmaf(qw[w], U[w][k], t);
+                Bt[k] = P.model == 2 ? 0.0f : t;
+            }
             sigma_inv();
-            ray_dual<KEEP>(al, sinv, cv, rw, Bt, y, yo, Bm);
+            ray_dual<KEEP, W>(al, sinv, cv, rw, Bt, y, yo, Bm);
         }
-        if (KEEP) {
+        if constexpr (KEEP) {
             float4* M = D.model + (size_t)kModelStride * l;
 #pragma unroll
             for (int m = 0; m < 3; ++m) M[m] = make_float4(al[0][m], al[1][m], al[2][m], al[3][m]);
@@ -737,13 +764,13 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
                 for (int w = 0; w < 4; ++w) M[7 + w] = make_float4(Bm[w][0], Bm[w][1], Bm[w][2], Bm[w][3]);
             }
         }
-        const float yf[4] = {(float)yo[0], (float)yo[1], (float)yo[2], (float)yo[3]};
-        D.y[l] = make_float4(yf[0], yf[1], yf[2], yf[3]);
+        win_store<W>(D.y + F4 * (size_t)l, yo);
+        const float (&yf)[W] = yo;
         // b = alpha^T y';  the ray's share of T^-1: m-block SPC S = sum_w alpha_w alpha_w^T / |alpha_w|,
         // diagonal SPC S = diag(sum_w |alpha_wm|)
         float bb[3] = {0.f, 0.f, 0.f}, Sm[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
+        for (int w = 0; w < W; ++w) {
 #pragma unroll
             for (int m = 0; m < 3; ++m) bb[m] = fmaf(al[w][m], yf[w], bb[m]);
             if (P.spc == 0) {
@@ -766,14 +793,14 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
     return dsum;
 }
 
-template <bool KEEP>
-__global__ void __launch_bounds__(kFwdThreads, 4) k_mocca_ray(GeomC C, RayRec* rec, SpecD S, StepParams P,
-                                                              SolveD D, int v0, int v1) {
+template <bool KEEP, int W>
+__global__ void __launch_bounds__(kFwdThreads, W == 4 ? 4 : 3) k_mocca_ray(GeomC C, RayRec* rec, SpecD S,
+                                                                         StepParams P, SolveD D, int v0, int v1) {
     __shared__ float sm[kSmemStride * kMaxEnergies];
     load_mu_smem(S, sm);
     __syncthreads();
     const int l = ray_in_views(C, blockIdx.x, blockIdx.y, kFwdThreads / 32, v0, v1);
-    const double dsum = l >= 0 ? ray_step<KEEP>(C, rec, S, P, D, sm, l) : 0.0;
+    const double dsum = l >= 0 ? ray_step<KEEP, W>(C, rec, S, P, D, sm, l) : 0.0;
     warp_partial(C, blockIdx.x, v0 + warp_view(blockIdx.y, kFwdThreads / 32), dsum, D.dtpl_part, v1);
 }
 
@@ -1551,7 +1578,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) k_batch_ray(const SolveDesc* _
         const GeomC C = d.C;
         const int nbx = (C.n_bins + 31) >> 5, bx = w.y % nbx, by = w.y / nbx;
         const int l = ray_at(C, bx, by, kFwdThreads / 32);
-        const double dsum = l >= 0 ? ray_step<false>(C, d.rec, d.S, d.P, d.D, sm, l) : 0.0;
+        const double dsum = l >= 0 ? ray_step<false, 4>(C, d.rec, d.S, d.P, d.D, sm, l) : 0.0;
         warp_partial(C, bx, warp_view(by, kFwdThreads / 32), dsum, d.D.dtpl_part);
     }
 }
@@ -1603,7 +1630,10 @@ cudaError_t launch_backproject4(const GeomC& C, const ExcTable& E, const RayRec*
 
 cudaError_t launch_counts(const GeomC& C, const ExcTable& E, const RayRec* rec, const SpecD& S, const float4* f,
                           float4* chat, const float4* c, double* dtpl_part, cudaStream_t st) {
-    k_counts<<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, E, rec, S, f, chat, c, dtpl_part);
+    if (S.n_windows == 5)
+        k_counts<5><<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, E, rec, S, f, chat, c, dtpl_part);
+    else
+        k_counts<4><<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, E, rec, S, f, chat, c, dtpl_part);
     return cudaGetLastError();
 }
 
@@ -1619,13 +1649,17 @@ cudaError_t launch_mocca_proj(const GeomC& C, const ExcTable& E, const RayRec* r
 cudaError_t launch_mocca_ray(const GeomC& C, RayRec* rec, const SpecD& S, const StepParams& P, const SolveD& D,
                              cudaStream_t st, int v0, int v1) {
     if (v1 < 0) v1 = C.n_views;
-    k_mocca_ray<false><<<fwd_grid(C.n_bins, v1 - v0), kFwdThreads, 0, st>>>(C, rec, S, P, D, v0, v1);
+    if (S.n_windows == 5)
+        k_mocca_ray<false, 5><<<fwd_grid(C.n_bins, v1 - v0), kFwdThreads, 0, st>>>(C, rec, S, P, D, v0, v1);
+    else
+        k_mocca_ray<false, 4><<<fwd_grid(C.n_bins, v1 - v0), kFwdThreads, 0, st>>>(C, rec, S, P, D, v0, v1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mocca_ray_keep(const GeomC& C, RayRec* rec, const SpecD& S, const StepParams& P,
                                   const SolveD& D, cudaStream_t st) {
-    k_mocca_ray<true><<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, rec, S, P, D, 0, C.n_views);
+    if (S.n_windows != 4) return cudaErrorInvalidValue;   // nested MOCCA keeps four-window models
+    k_mocca_ray<true, 4><<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, rec, S, P, D, 0, C.n_views);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@ struct osscir_ctx {
     osscir::GeomD g64{};
     osscir::GeomC gc{};
     int P = 0, L = 0, nE = 0;
+    int nw = 4;   // energy windows W (4 or 5)
     osscir::StepParams params{};
     // per-geometry tables
     osscir::RayRec* rec = nullptr;
@@ -24,8 +25,8 @@ struct osscir_ctx {
     int2* exc_ent = nullptr;
     int exc_n = 0;
     // spectral tables
-    float4* s4 = nullptr;
-    float4* N4 = nullptr;
+    float4* s4 = nullptr;   // [nE][n_bins] window vectors
+    float4* N4 = nullptr;   // [n_bins] window vectors
     float* mu = nullptr;      // [3][nE] the curves the iteration uses (mu-PC: the transformed ones)
     float* mu_in = nullptr;   // [3][nE] the caller's curves, kept apart only for mu-PC (else null)
     // mu-PC (spc = 2): the iteration runs in the basis f' = M^-1 f with M = (mu mu^T)^(-1/2)
@@ -35,8 +36,8 @@ struct osscir_ctx {
     float4* xo = nullptr;
     // solver state
     float4* g = nullptr;
-    float4* c = nullptr;
-    float4* y = nullptr;
+    float4* c = nullptr;   // [L] window vectors
+    float4* y = nullptr;   // [L] window vectors
     float4* x = nullptr;
     float4* xbar = nullptr;
     double* dtpl_part = nullptr;
@@ -82,9 +83,11 @@ struct osscir_ctx {
     cudaEvent_t fork = nullptr, join = nullptr;
 
     osscir::ExcTable exc() const { return osscir::ExcTable{exc_off, exc_ent}; }
-    osscir::SpecD spec() const { return osscir::SpecD{nE, s4, N4, mu, exp_model}; }
+    osscir::SpecD spec() const { return osscir::SpecD{nE, s4, N4, mu, exp_model, nw}; }
     // the spectral tables with the caller's attenuation curves (for maps in the caller's basis)
-    osscir::SpecD spec_in() const { return osscir::SpecD{nE, s4, N4, mu_in ? mu_in : mu, exp_model}; }
+    osscir::SpecD spec_in() const { return osscir::SpecD{nE, s4, N4, mu_in ? mu_in : mu, exp_model, nw}; }
+    // float4 per ray of the window arrays c, y (and of the caller's counts): 1 for 4 windows, 2 for 5
+    int wf4() const { return nw > 4 ? 2 : 1; }
     osscir::SolveD solve() const {
         return osscir::SolveD{g, c, y, x, xbar, chord, dtpl_part, model, bad_counts ? bad_counts + 1 : nullptr};
     }

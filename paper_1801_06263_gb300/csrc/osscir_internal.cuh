@@ -15,8 +15,37 @@
 
 namespace osscir {
 
-constexpr int NW = 4;  // energy windows
 constexpr int NM = 3;  // basis materials
+
+// Window vectors.  A per-ray quantity over the W energy windows (counts, duals,
+// spectral weights) is stored in whole float4s: one for W = 4, two for W = 5
+// (components W..7 zero), so every load is an aligned 16-byte load.
+template <int W>
+constexpr int win_f4() { return (W + 3) / 4; }
+
+template <int W, bool LDG = false>
+__device__ __forceinline__ void win_load(const float4* p, float (&v)[W]) {
+    static_assert(W >= 4 && W <= 8, "4 to 8 windows");
+    const float4 a = LDG ? __ldg(p) : p[0];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    if constexpr (W > 4) {
+        const float4 b = LDG ? __ldg(p + 1) : p[1];
+        const float t[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int w = 4; w < W; ++w) v[w] = t[w - 4];
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void win_store(float4* p, const float (&v)[W]) {
+    p[0] = make_float4(v[0], v[1], v[2], v[3]);
+    if constexpr (W > 4) {
+        float t[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int w = 4; w < W; ++w) t[w - 4] = v[w];
+        p[1] = make_float4(t[0], t[1], t[2], t[3]);
+    }
+}
 
 // Pixel grid: n x n pixels of side h, planes at x0 + i h (i = 0..n), x0 = -n h / 2.
 struct GridF {

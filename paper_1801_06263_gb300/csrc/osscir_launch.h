@@ -23,10 +23,11 @@ struct GeomD {
 // Spectral tables on the device.
 struct SpecD {
     int n_energies;
-    const float4* s4;   // [nE][n_bins]: (s_{1..4,b,i})
-    const float4* N4;   // [n_bins]
+    const float4* s4;   // [nE][n_bins] window vectors (win_f4 float4 each): s_{w,b,i}
+    const float4* N4;   // [n_bins] window vectors: N_{w,b}
     const float* mu;    // [3][nE]
     int exp_model;      // 0: softexp (Eq. finalModel), 1: exp for every energy (Eq. fullModel)
+    int n_windows;      // W: 4 or 5 (the per-ray arrays c, y, chat hold win_f4<W> float4 per ray)
 };
 
 // MOCCA per-solve parameters.

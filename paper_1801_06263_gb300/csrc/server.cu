@@ -474,6 +474,7 @@ osscir_status osscir_submit(osscir_server_t s, const osscir_request* req, uint64
     const osscir_status v = osscir::ctx_validate(&req->geom, &req->spectra, req->mu, &req->params);
     if (v != OSSCIR_OK) return v;
     if (req->params.inner > 1) return OSSCIR_E_INVALID;   // nested solves are not served
+    if (req->spectra.n_windows != 0 && req->spectra.n_windows != 4) return OSSCIR_E_INVALID;   // four windows
     Ticket* t = new (std::nothrow) Ticket();
     if (!t) return OSSCIR_E_NOMEM;
     const osscir_geometry& g = req->geom;

@@ -19,6 +19,9 @@ data are not available, Sec. 3):
   * four overlapping windows 20-40-50-65-120 keV whose inner edges are
     jittered per detector bin (the per-pixel response variation of Sec. 3)
     with Gaussian (sigma = 5 keV) roll-off;
+  * the five-window variant (Sec. 1 recalls an earlier simulation with five
+    ideal windows, sharp edges and no overlap, without giving the edges): the
+    same layout with 65-120 keV split at 80 keV, 20-40-50-65-80-120 keV;
   * s_{w,b,i} normalised so that sum_i s = 1 (Eq. fullModel), and
     N_{w,b} = N0 * sum_i Phi_i R_{w,b}(E_i).
 """
@@ -39,6 +42,7 @@ MU_B = {"PMMA": 0.022, "Al": 0.06, "Gd": 0.3}
 GD_K_EDGE_KEV = 50.2
 GD_K_JUMP = 5.0
 WINDOW_EDGES_KEV = (20.0, 40.0, 50.0, 65.0, 120.0)
+WINDOW_EDGES_5_KEV = (20.0, 40.0, 50.0, 65.0, 80.0, 120.0)
 WINDOW_ROLLOFF_KEV = 5.0
 KVP = 120.0
 FILTER_AL_MM = 1.0
@@ -137,26 +141,37 @@ def _erf(x):
     return np.vectorize(math.erf, otypes=[np.float64])(x)
 
 
-def window_responses(E_keV: np.ndarray, n_bins: int, seed: int = 7, ideal: bool = False) -> np.ndarray:
+def window_edges(n_windows: int = N_WINDOWS) -> tuple:
+    """Nominal window edges (keV) of the four- or five-window layout."""
+    if n_windows == 4:
+        return WINDOW_EDGES_KEV
+    if n_windows == 5:
+        return WINDOW_EDGES_5_KEV
+    raise ValueError("4 or 5 windows")
+
+
+def window_responses(E_keV: np.ndarray, n_bins: int, seed: int = 7, ideal: bool = False,
+                     n_windows: int = N_WINDOWS) -> np.ndarray:
     """R[b, i, w]: window responses with per-bin jittered inner edges and Gaussian
     roll-off; ideal=True gives sharp windows [lo, hi) (the last one closed) with
     the nominal edges in every bin, so each energy falls in exactly one window
     (the ideal, non-overlapping photon-counting response the paper contrasts with
     its realistic overlapping windows, Sec. 1)."""
     E = np.asarray(E_keV, dtype=np.float64)
+    edges0 = window_edges(n_windows)
     if ideal:
-        R = np.zeros((n_bins, E.size, N_WINDOWS))
-        for w in range(N_WINDOWS):
-            lo, hi = WINDOW_EDGES_KEV[w], WINDOW_EDGES_KEV[w + 1]
-            inside = (E >= lo) & ((E < hi) if w < N_WINDOWS - 1 else (E <= hi))
+        R = np.zeros((n_bins, E.size, n_windows))
+        for w in range(n_windows):
+            lo, hi = edges0[w], edges0[w + 1]
+            inside = (E >= lo) & ((E < hi) if w < n_windows - 1 else (E <= hi))
             R[:, inside, w] = 1.0
         return R
     rng = np.random.default_rng(seed + 1)
-    edges = np.tile(np.asarray(WINDOW_EDGES_KEV), (n_bins, 1))
-    edges[:, 1:-1] += rng.uniform(-1.0, 1.0, size=(n_bins, len(WINDOW_EDGES_KEV) - 2))
+    edges = np.tile(np.asarray(edges0), (n_bins, 1))
+    edges[:, 1:-1] += rng.uniform(-1.0, 1.0, size=(n_bins, len(edges0) - 2))
     sq = math.sqrt(2.0) * WINDOW_ROLLOFF_KEV
-    R = np.empty((n_bins, E.size, N_WINDOWS))
-    for w in range(N_WINDOWS):
+    R = np.empty((n_bins, E.size, n_windows))
+    for w in range(n_windows):
         lo = edges[:, w][:, None]
         hi = edges[:, w + 1][:, None]
         R[:, :, w] = 0.5 * (_erf((E[None, :] - lo) / sq) - _erf((E[None, :] - hi) / sq))
@@ -166,8 +181,8 @@ def window_responses(E_keV: np.ndarray, n_bins: int, seed: int = 7, ideal: bool 
 @dataclasses.dataclass
 class Spectra:
     energies: np.ndarray   # [nE] keV
-    s: np.ndarray          # [n_bins, nE, 4], sum over energies = 1 per (bin, window)
-    N: np.ndarray          # [n_bins, 4] incident photons per window
+    s: np.ndarray          # [n_bins, nE, W], sum over energies = 1 per (bin, window)
+    N: np.ndarray          # [n_bins, W] incident photons per window
     mu: np.ndarray         # [3, nE] 1/mm
 
     @property
@@ -176,10 +191,11 @@ class Spectra:
 
 
 def make_spectra(n_bins: int, photons_per_ray: float, *, seed: int = 7,
-                 E_keV: np.ndarray | None = None, ideal_windows: bool = False) -> Spectra:
+                 E_keV: np.ndarray | None = None, ideal_windows: bool = False,
+                 n_windows: int = N_WINDOWS) -> Spectra:
     E = energies_keV() if E_keV is None else np.asarray(E_keV, dtype=np.float64)
     phi = source_spectrum(E, seed)
-    R = window_responses(E, n_bins, seed, ideal=ideal_windows)
+    R = window_responses(E, n_bins, seed, ideal=ideal_windows, n_windows=n_windows)
     weighted = phi[None, :, None] * R                  # [b, i, w]
     tot = weighted.sum(axis=1)                         # [b, w]
     s = weighted / tot[:, None, :]

@@ -58,7 +58,7 @@ def model_matrices(geom, sp, X, f0, c):
     Row index of data space: w * L + l;  column index of image space: m * P + k;
     (l, i) index of the Z-space: l * nE + i.
     """
-    L, P, nE = geom.n_rays, geom.n_pixels, sp.s.shape[1]
+    L, P, nE, nw = geom.n_rays, geom.n_pixels, sp.s.shape[1], sp.s.shape[2]
     mu = sp.mu
     Z = np.zeros((L * nE, 3 * P))
     for m in range(3):
@@ -66,10 +66,10 @@ def model_matrices(geom, sp, X, f0, c):
     zf = Z @ f0.T.reshape(-1)                                    # (Zf)_{l,i}
     e0, e1, e2 = sexp(-zf, 0), sexp(-zf, 1), sexp(-zf, 2)
     bins = np.arange(L) % geom.n_bins
-    A = np.zeros((4 * L, L * nE))
-    B = np.zeros((4 * L, L * nE))
-    chat = np.zeros(4 * L)
-    for w in range(4):
+    A = np.zeros((nw * L, L * nE))
+    B = np.zeros((nw * L, L * nE))
+    chat = np.zeros(nw * L)
+    for w in range(nw):
         for l in range(L):
             s = sp.s[bins[l], :, w]
             seg = slice(l * nE, (l + 1) * nE)
@@ -85,7 +85,7 @@ def model_matrices(geom, sp, X, f0, c):
 
 def one_iteration(geom, sp, X, c, x, xbar, y, lam, spc="block", model="hessian"):
     """One MOCCA iteration in matrix form (reading of the step in the oracle header)."""
-    L, P, nE = geom.n_rays, geom.n_pixels, sp.s.shape[1]
+    L, P, nE, nw = geom.n_rays, geom.n_pixels, sp.s.shape[1], sp.s.shape[2]
     M = model_matrices(geom, sp, X, xbar, c)
     K, r, Z, A, B = M["K"], M["r"], M["Z"], M["A"], M["B"]
     Btr = B.T @ r
@@ -93,8 +93,8 @@ def one_iteration(geom, sp, X, c, x, xbar, y, lam, spc="block", model="hessian")
     # per-ray clipped Hessian in the ray's line integrals g (3x3)
     ynew = y.copy()
     for l in range(L):
-        rows = [w * L + l for w in range(4)]
-        Kl = K[rows]                                          # [4, 3P]
+        rows = [w * L + l for w in range(nw)]
+        Kl = K[rows]                                          # [W, 3P]
         if not np.any(X[l]):
             continue
         k0 = int(np.flatnonzero(X[l])[0])
@@ -107,7 +107,7 @@ def one_iteration(geom, sp, X, c, x, xbar, y, lam, spc="block", model="hessian")
         Hp = V @ np.diag(np.maximum(lamH, 0)) @ V.T
         if spc == "block":
             sinv = lam * np.array([np.sum(np.sqrt(sum(Kl[w, m * P:(m + 1) * P] ** 2 for m in range(3))))
-                                   for w in range(4)])
+                                   for w in range(nw)])
         else:
             sinv = lam * np.abs(Kl).sum(axis=1)
         Sig = np.diag(1.0 / sinv)
@@ -115,7 +115,7 @@ def one_iteration(geom, sp, X, c, x, xbar, y, lam, spc="block", model="hessian")
             G = np.linalg.pinv(alpha)
             W = G.T @ Hp @ G
         else:
-            W = np.zeros((4, 4))
+            W = np.zeros((nw, nw))
         yl = y[l]
         ynew[l] = yl - Sig @ np.linalg.solve(W + Sig, yl - r[rows])
     yv = ynew.T.reshape(-1)
@@ -123,7 +123,7 @@ def one_iteration(geom, sp, X, c, x, xbar, y, lam, spc="block", model="hessian")
     xn = x.copy()
     for k in range(P):
         cols = [m * P + k for m in range(3)]
-        Kk = K[:, cols]                                       # [4L, 3]
+        Kk = K[:, cols]                                       # [W L, 3]
         if spc == "block":
             nrm = np.sqrt((Kk ** 2).sum(axis=1))
             ok = nrm > 0

@@ -83,6 +83,29 @@ def test_create_rejects_bad_box_and_model(lib):
             _lib.osscir_create(g, sp.s, sp.N, sp.mu, 1e-6, inner=inner)
 
 
+def test_create_rejects_unsupported_window_counts(lib):
+    """Four or five windows; five are refused for nested solves (their kept models hold four)."""
+    g, _ = _args()
+    for nw in (3, 6):
+        sp = inputs.make_spectra(g.n_bins, 1e4, n_windows=5)
+        s = np.concatenate([sp.s] * 2, axis=2)[:, :, :nw] if nw > 5 else sp.s[:, :, :nw]
+        N = np.concatenate([sp.N] * 2, axis=1)[:, :nw] if nw > 5 else sp.N[:, :nw]
+        with pytest.raises(_lib.OsscirError) as e:
+            _lib.osscir_create(g, s, N, sp.mu, 1e-6)
+        assert e.value.status == _lib.OSSCIR_E_INVALID
+    sp5 = inputs.make_spectra(g.n_bins, 1e4, n_windows=5)
+    with pytest.raises(_lib.OsscirError) as e:
+        _lib.osscir_create(g, sp5.s, sp5.N, sp5.mu, 1e-6, inner=3)
+    assert e.value.status == _lib.OSSCIR_E_INVALID
+    bad = sp5.s.copy()
+    bad[:, :, 4] *= 1.01   # the fifth window's response must be normalised too
+    with pytest.raises(_lib.OsscirError) as e:
+        _lib.osscir_create(g, bad, sp5.N, sp5.mu, 1e-6)
+    assert e.value.status == _lib.OSSCIR_E_INVALID
+    with pytest.raises(ValueError):   # N must match s's window count
+        _lib.osscir_create(g, sp5.s, sp5.N[:, :4], sp5.mu, 1e-6)
+
+
 def test_null_handle_calls_are_rejected(lib):
     null = ct.c_void_p(0)
     assert lib.osscir_mocca_step(null, 1, None) == _lib.OSSCIR_E_INVALID

@@ -48,21 +48,22 @@ def test_solve_matches_lapack(orc, n):
     np.testing.assert_allclose(orc.solve(M, b), np.linalg.solve(M, b), rtol=1e-13, atol=1e-13)
 
 
-def _ray(rng):
-    alpha = np.abs(rng.normal(size=(4, 3))) * np.array([0.03, 0.1, 20.0])
+def _ray(rng, nw=4):
+    alpha = np.abs(rng.normal(size=(nw, 3))) * np.array([0.03, 0.1, 20.0])
     H = _sym(rng, (3e4, 50.0, -0.5))
-    r = rng.normal(scale=100.0, size=4)
-    sinv = rng.uniform(0.5, 5.0, size=4)
-    y = rng.normal(scale=50.0, size=4)
+    r = rng.normal(scale=100.0, size=nw)
+    sinv = rng.uniform(0.5, 5.0, size=nw)
+    y = rng.normal(scale=50.0, size=nw)
     return alpha, H, r, sinv, y
 
 
+@pytest.mark.parametrize("nw", [4, 5])
 @pytest.mark.parametrize("seed", range(5))
-def test_dual_step_is_the_prox_of_the_local_model(orc, seed):
+def test_dual_step_is_the_prox_of_the_local_model(orc, seed, nw):
     """y' solves the optimality condition of the preconditioned dual prox of
     Q(z) = r^T (z - z0) + 1/2 (z - z0)^T W (z - z0):  y' = r + W Sigma^-1 (y - y')."""
     rng = np.random.default_rng(seed)
-    alpha, H, r, sinv, y = _ray(rng)
+    alpha, H, r, sinv, y = _ray(rng, nw)
     Hp = orc.clip_psd3(H)
     yp = orc.dual_update(alpha, Hp, r, sinv, y)
     G = np.linalg.pinv(alpha)
@@ -81,13 +82,14 @@ def test_dual_step_without_curvature_returns_residual(orc):
                                rtol=1e-14, atol=1e-12)
 
 
+@pytest.mark.parametrize("nw", [4, 5])
 @pytest.mark.parametrize("seed", range(3))
-def test_separable_dual_step_is_the_windowwise_prox(orc, seed):
-    """W = diag(c) makes the 4 x 4 prox separable: y'_w = r_w + c_w / (c_w + sigma_w) (y_w - r_w),
+def test_separable_dual_step_is_the_windowwise_prox(orc, seed, nw):
+    """W = diag(c) makes the W x W prox separable: y'_w = r_w + c_w / (c_w + sigma_w) (y_w - r_w),
     sigma_w = 1 / (Sigma^-1)_w, which the oracle's general solve must reproduce."""
     rng = np.random.default_rng(20 + seed)
-    alpha, H, r, sinv, y = _ray(rng)
-    c = rng.uniform(10.0, 1e5, size=4)
+    alpha, H, r, sinv, y = _ray(rng, nw)
+    c = rng.uniform(10.0, 1e5, size=nw)
     yp = orc.dual_update(alpha, np.zeros((3, 3)), r, sinv, y, model="separable", c=c)
     sig = 1.0 / sinv
     np.testing.assert_allclose(yp, r + c / (c + sig) * (y - r), rtol=1e-12, atol=1e-12 * np.abs(y).max())

@@ -17,31 +17,33 @@ from paper_1801_06263_gb300 import inputs
 import _dense
 
 
-def _tiny(seed=0, n=5, views=4, bins=7):
+def _tiny(seed=0, n=5, views=4, bins=7, n_windows=4, ideal=False):
     geom = inputs.make_geometry(n, 0.9, views, bins, bin_mm=None)
-    sp = inputs.make_spectra(geom.n_bins, 3e4, seed=seed + 3)
+    sp = inputs.make_spectra(geom.n_bins, 3e4, seed=seed + 3, n_windows=n_windows, ideal_windows=ideal)
     f = inputs.disk_phantom(geom, radius_mm=1.8, insert_mm=0.5, gd_levels=(0.005, 0.01))
     return geom, sp, f
 
 
-def _random_state(geom, seed):
+def _random_state(geom, seed, nw=4):
     rng = np.random.default_rng(seed)
     x = np.abs(rng.normal(size=(geom.n_pixels, 3))) * np.array([0.8, 0.3, 0.004])
     xbar = x + rng.normal(size=x.shape) * np.array([0.05, 0.02, 0.0005])
-    y = rng.normal(scale=200.0, size=(geom.n_rays, 4))
+    y = rng.normal(scale=200.0, size=(geom.n_rays, nw))
     return x, xbar, y
 
 
-@pytest.mark.parametrize("spc,model", [("block", "hessian"), ("block", "gradient"),
-                                       ("diagonal", "hessian")])
-def test_one_iteration_matches_dense_restatement(orc, spc, model):
-    geom, sp, f = _tiny()
+@pytest.mark.parametrize("spc,model,n_windows,ideal", [("block", "hessian", 4, False), ("block", "gradient", 4, False),
+                                                       ("diagonal", "hessian", 4, False),
+                                                       ("block", "hessian", 5, True), ("block", "hessian", 5, False),
+                                                       ("diagonal", "hessian", 5, True)])
+def test_one_iteration_matches_dense_restatement(orc, spc, model, n_windows, ideal):
+    geom, sp, f = _tiny(n_windows=n_windows, ideal=ideal)
     c = inputs.poisson_counts(orc.counts(geom, sp, f), 4)
-    x, xbar, y = _random_state(geom, 1)
+    x, xbar, y = _random_state(geom, 1, n_windows)
     X = _dense.dense_X(geom)
     lam = 3e-6
     want_x, want_xbar, want_y = _dense.one_iteration(geom, sp, X, c, x, xbar, y, lam, spc, model)
-    st = orc.State(geom)
+    st = orc.State(geom, n_windows)
     st.x[:], st.xbar[:], st.y[:] = x, xbar, y
     st, _ = orc.mocca(geom, sp, c, 1, lam, st, spc=spc, model=model)
     np.testing.assert_allclose(st.y, want_y, rtol=0, atol=1e-8 * np.abs(want_y).max())
@@ -51,15 +53,16 @@ def test_one_iteration_matches_dense_restatement(orc, spc, model):
         np.testing.assert_allclose(st.xbar[:, m], want_xbar[:, m], rtol=0, atol=1e-7 * sc)
 
 
+@pytest.mark.parametrize("n_windows", [4, 5])
 @pytest.mark.parametrize("spc", ["block", "diagonal"])
-def test_step_condition_M_is_psd(orc, spc):
-    geom, sp, f = _tiny(1, n=6, views=5, bins=8)
+def test_step_condition_M_is_psd(orc, spc, n_windows):
+    geom, sp, f = _tiny(1, n=6, views=5, bins=8, n_windows=n_windows, ideal=n_windows == 5)
     lam = 2.7e-4
     sinv, Tinv, alpha = orc.step_matrices(geom, sp, f, lam, spc=spc)
     X = _dense.dense_X(geom)
-    L, P = geom.n_rays, geom.n_pixels
-    K = np.zeros((4 * L, 3 * P))
-    for w in range(4):
+    L, P, nw = geom.n_rays, geom.n_pixels, n_windows
+    K = np.zeros((nw * L, 3 * P))
+    for w in range(nw):
         for m in range(3):
             K[w * L:(w + 1) * L, m * P:(m + 1) * P] = alpha[:, w, m][:, None] * X
     Ti = np.zeros((3 * P, 3 * P))
@@ -72,7 +75,7 @@ def test_step_condition_M_is_psd(orc, spc):
     assert ev.min() >= -1e-10 * np.abs(ev).max()
     if spc == "block":   # Sigma^-1 written out from its definition over the dense K
         want = lam * np.array([[np.sum(np.sqrt(sum(K[w * L + l, m * P:(m + 1) * P] ** 2 for m in range(3))))
-                                for w in range(4)] for l in range(L)])
+                                for w in range(nw)] for l in range(L)])
         np.testing.assert_allclose(sinv, want, rtol=1e-12, atol=0)
 
 
@@ -269,3 +272,18 @@ def test_gauss_newton_curvature_equals_the_hessian_at_zero_residual(orc):
     np.testing.assert_allclose(out[1][0], out[0][0], rtol=1e-9, atol=1e-9 * np.abs(out[0][0]).max())
     # and the curvature does act here: without it (W = 0) the step is different
     assert np.abs(out[2][1] - out[0][1]).max() > 1e-3 * np.abs(out[0][1]).max()
+
+
+def test_five_ideal_windows_converge(orc):
+    """The ideal five-window response (Sec. 1: the earlier one-step simulation
+    that converged readily) on noiseless data made with the model itself: D_TPL
+    falls by more than 1e8 and the maps approach the truth."""
+    w = inputs.workload("tiny_16")
+    sp = inputs.make_spectra(w.geom.n_bins, 1e5, ideal_windows=True, n_windows=5)
+    c = orc.counts(w.geom, sp, w.f_true)
+    assert c.shape == (w.geom.n_rays, 5)
+    st, hist = orc.mocca(w.geom, sp, c, 2000, 3e-6)   # a step ratio at which four windows diverge here
+    assert np.all(np.isfinite(hist))
+    assert hist[-1] < 1e-8 * hist[0]
+    errs = [np.linalg.norm(st.x[:, m] - w.f_true[:, m]) / np.linalg.norm(w.f_true[:, m]) for m in range(3)]
+    assert max(errs) < 0.06, errs

@@ -236,3 +236,28 @@ def test_overlap_worsens_the_conditioning(orc):
         cond = [np.linalg.cond(orc.ray_terms(sp, b, g[l])["alpha"].T @ orc.ray_terms(sp, b, g[l])["alpha"])
                 for sp in (real, ideal)]
         assert cond[0] > 1.2 * cond[1], cond
+
+
+def test_five_ideal_windows_split_the_last_four_window_bin(orc):
+    """Sharp windows are additive over disjoint energy ranges: with the same source
+    and photons, the five-window layout equals the four-window one in the first
+    three windows, and its last two windows (65-80 and 80-120 keV) add up to the
+    four-window 65-120 keV window, for any maps (Eq. fullModel is linear in the
+    per-energy photon flux)."""
+    geom = inputs.make_geometry(12, 0.8, 8, 20)
+    f = inputs.disk_phantom(geom, radius_mm=3.5, insert_mm=1.0)
+    for counts_model in ("softexp", "exp"):
+        c4 = orc.counts(geom, inputs.make_spectra(geom.n_bins, 1e5, ideal_windows=True), f,
+                        counts_model=counts_model)
+        c5 = orc.counts(geom, inputs.make_spectra(geom.n_bins, 1e5, ideal_windows=True, n_windows=5), f,
+                        counts_model=counts_model)
+        np.testing.assert_allclose(c5[:, :3], c4[:, :3], rtol=1e-13, atol=0)
+        np.testing.assert_allclose(c5[:, 3] + c5[:, 4], c4[:, 3], rtol=1e-13, atol=0)
+        assert (c5[:, 3] > 0).all() and (c5[:, 4] > 0).all()
+
+
+def test_five_ideal_windows_partition_the_energies():
+    R = inputs.window_responses(inputs.energies_keV(), 3, ideal=True, n_windows=5)
+    assert R.shape[2] == 5 and (R.sum(axis=2) == 1.0).all()
+    E = inputs.energies_keV()
+    assert (R[0, (E >= 65) & (E < 80), 3] == 1).all() and (R[0, E >= 80, 4] == 1).all()
