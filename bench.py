@@ -351,6 +351,7 @@ def run_gpu(args):
     finite = bool(torch.isfinite(maps_host).all().item())
 
     nested = run_nested(args, w, c) if args.nested else None
+    five = run_five_windows(args, w, f4, rank) if args.five_windows > 0 else None
     served = run_served(args, w, R, chat, rank) if args.served > 0 else None
     batched = run_batched(args, rank) if args.batch > 0 else None
     mixed = run_served_mixed(args, rank) if args.mixed > 0 else None
@@ -449,6 +450,7 @@ def run_gpu(args):
                 "recon_per_s": e2e_rate / SOLVE_ITERS},
         "plain_recon_per_s": e2e_rate / SOLVE_ITERS,
         "nested": nested,
+        "five_windows": five,
         "served": served,
         "batched": batched,
         "served_mixed": mixed,
@@ -490,6 +492,36 @@ def run_nested(args, w, c):
         R.close()
         out[str(k)] = {"ms_per_iteration": ms / done, "trajectory": rows}
     return out
+
+
+def run_five_windows(args, w, f4, rank):
+    """The headline solve with five ideal windows (20-40-50-65-80-120 keV) in place
+    of four: device time per iteration and per kernel, L2 flushed between steps."""
+    import statistics as st
+    import torch
+    from paper_1801_06263_gb300 import Reconstructor, _lib, inputs
+
+    sp = inputs.make_spectra(w.geom.n_bins, w.photons_per_ray, ideal_windows=True, n_windows=5)
+    R = Reconstructor(w.geom, sp, LAMBDA)
+    c = _lib.osscir_poisson_noise(R.simulate(f4), w.noise_seed + 5 + (rank << 32))
+    R.set_counts(c)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    R.step(3)
+    kms, ms = [], []
+    for k in range(args.five_windows):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        R.step(1)
+        b.record(stream)
+        kms.append(_lib.osscir_last_kernel_ms(R.handle))
+        ms.append(a.elapsed_time(b))
+    d = R.dtpl(1)
+    R.close()
+    return {"ms_per_iteration": st.mean(ms), "kernel_ms": [st.mean(k[i] for k in kms) for i in range(3)],
+            "iterations": args.five_windows, "dtpl_last": d, "windows": "20-40-50-65-80-120 keV, ideal",
+            "counts_per_ray_bytes": 32}
 
 
 def run_batched(args, rank):
@@ -708,6 +740,8 @@ def main():
                     help="Poisson arrival rates of the mixed served sweep, requests/s")
     ap.add_argument("--batch-steps", type=int, default=5, help="timed iterations of the batched measurement")
     ap.add_argument("--rate", type=float, default=1.5, help="Poisson request arrival rate, requests/s")
+    ap.add_argument("--five-windows", type=int, default=20,
+                    help="timed iterations of the five-window solve (0: skip)")
     ap.add_argument("--nested", type=int, nargs="*", default=[1, 2, 4, 8],
                     help="iterations per local model for the nested MOCCA leg (none: skip)")
     args = ap.parse_args()
