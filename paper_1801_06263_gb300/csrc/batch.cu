@@ -441,7 +441,7 @@ osscir_status autotune(osscir_batch* b) {
     // every solve's state (x_n, xbar_n, y_n) is saved and put back afterwards;
     // g, b, S, the D_TPL partials and D_TPL itself are recomputed by the next iteration
     size_t total = 0;
-    for (const osscir_ctx* h : b->ctx) total += sizeof(float4) * (2 * (size_t)h->P + h->L) + sizeof(double);
+    for (const osscir_ctx* h : b->ctx) total += sizeof(float4) * (3 * (size_t)h->P + h->L) + sizeof(double);
     char* save = nullptr;
     CK(cudaMalloc(reinterpret_cast<void**>(&save), total));
     cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -451,8 +451,8 @@ osscir_status autotune(osscir_batch* b) {
         size_t off = 0;
         for (osscir_ctx* h : b->ctx) {
             void* buf[4] = {h->x, h->xbar, h->y, h->dtpl_out + 1};
-            const size_t sz[4] = {sizeof(float4) * h->P, sizeof(float4) * h->P, sizeof(float4) * h->L,
-                                  sizeof(double)};
+            const size_t sz[4] = {sizeof(float4) * h->P, sizeof(float4) * 2 * h->P, sizeof(float4) * h->L,
+                                  sizeof(double)};   // xbar with its column-major copy
             for (int i = 0; i < 4; ++i) {
                 const cudaError_t e = out ? cudaMemcpyAsync(save + off, buf[i], sz[i], cudaMemcpyDeviceToDevice, st)
                                           : cudaMemcpyAsync(buf[i], save + off, sz[i], cudaMemcpyDeviceToDevice, st);

@@ -54,7 +54,7 @@ void free_ctx(osscir_ctx* h) {
     void* ptrs[] = {h->rec,     h->r64,    h->views,     h->chord,    h->exc_off,    h->exc_ent,  h->s4,
                     h->N4,      h->mu,     h->mu_in,     h->g,        h->c,          h->y,        h->x,
                     h->xbar,    h->xo,     h->dtpl_part, h->dtpl_out, h->bad_counts, h->model,    h->fwd_row,
-                    h->fwd_cnt, h->fwd_pairs, h->bp_span, h->bp_row,  h->bp_cnt,   h->bp_w,
+                    h->fwd_cnt, h->fwd_k0, h->fwd_w, h->fwd_d, h->bp_span, h->bp_row,  h->bp_cnt,   h->bp_w,
                     h->bp_slot, h->bp_roff,   h->bp_rays, h->bp_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -280,7 +280,7 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     CK(dalloc(&h->c, (size_t)L * F4));
     CK(dalloc(&h->y, (size_t)L * F4));
     CK(dalloc(&h->x, P));
-    CK(dalloc(&h->xbar, P));
+    CK(dalloc(&h->xbar, 2 * (size_t)P));   // row-major, then the column-major copy
     CK(dalloc(&h->dtpl_part, h->n_part));
     CK(dalloc(&h->dtpl_out, 2));
     CK(dalloc(&h->bad_counts, 2));
@@ -337,7 +337,7 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
     CK(cudaMemsetAsync(h->c, 0, sizeof(float4) * L * F4, st));
     CK(cudaMemsetAsync(h->y, 0, sizeof(float4) * L * F4, st));
     CK(cudaMemsetAsync(h->x, 0, sizeof(float4) * P, st));
-    CK(cudaMemsetAsync(h->xbar, 0, sizeof(float4) * P, st));
+    CK(cudaMemsetAsync(h->xbar, 0, sizeof(float4) * 2 * P, st));
     CK(cudaMemsetAsync(h->dtpl_out, 0, sizeof(double) * 2, st));
     CK(cudaMemsetAsync(h->bad_counts, 0, 2 * sizeof(int), st));
     CK(cudaStreamSynchronize(st));
@@ -345,13 +345,15 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
 }
 
 void free_tables(osscir_ctx* h) {
-    void* ptrs[] = {h->fwd_row, h->fwd_cnt, h->fwd_pairs, h->bp_span, h->bp_row, h->bp_cnt,
+    void* ptrs[] = {h->fwd_row, h->fwd_cnt, h->fwd_k0, h->fwd_w, h->fwd_d, h->bp_span, h->bp_row, h->bp_cnt,
                     h->bp_w,    h->bp_slot, h->bp_roff,   h->bp_rays, h->bp_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->fwd_row = nullptr;
     h->fwd_cnt = nullptr;
-    h->fwd_pairs = nullptr;
+    h->fwd_k0 = nullptr;
+    h->fwd_w = nullptr;
+    h->fwd_d = nullptr;
     h->bp_span = nullptr;
     h->bp_row = nullptr;
     h->bp_cnt = nullptr;
@@ -413,10 +415,26 @@ osscir_status build_tables(osscir_ctx* h) {
     std::vector<uint32_t> rows(n_fw + 1, 0);
     CKT(cudaMemcpyAsync(rows.data(), h->fwd_row, sizeof(uint32_t) * n_fw, cudaMemcpyDeviceToHost, st));
     CKT(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < n_fw; ++i) rows[i] = (rows[i] + 1) & ~1u;   // even: entries are read two at a time
     if (!prefix_rows(rows, n_fw)) return fail(cudaErrorMemoryAllocation);
     CKT(cudaMemcpyAsync(h->fwd_row, rows.data(), sizeof(uint32_t) * (n_fw + 1), cudaMemcpyHostToDevice, st));
-    CKT(dalloc(&h->fwd_pairs, (size_t)rows[n_fw] * 32));
-    CKT(launch_fp_fwd_fill(C, h->exc(), h->rec, h->fwd_row, h->fwd_pairs, st));
+    CKT(dalloc(&h->fwd_w, (size_t)rows[n_fw] * 32));
+    CKT(dalloc(&h->fwd_d, (size_t)rows[n_fw] * 32));
+    CKT(dalloc(&h->fwd_k0, (size_t)h->L));
+    {
+        int* bad = nullptr;   // a pixel step outside 16 bits: keep the on-the-fly projections
+        CKT(dalloc(&bad, 1));
+        int bad_h = 0;
+        cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = launch_fp_fwd_fill(C, h->exc(), h->rec, h->fwd_row, h->fwd_w, h->fwd_d, h->fwd_k0,
+                                                     bad, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(bad);
+        h->bytes -= sizeof(int);
+        CKT(e);
+        if (bad_h) return fail(cudaErrorMemoryAllocation);
+    }
     // back-projection (blocked): per tile and view the union of candidate bins; the
     // chunk size (views per staged chunk) so that two stage buffers fit in 48 KB;
     // then per-pixel counts and per-warp rows of each (block, chunk), then the pairs
@@ -700,7 +718,7 @@ osscir_status osscir_set_counts(osscir_t h, const float* c, void* stream) {
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(h->y, 0, ray_bytes, st));
     CK(cudaMemsetAsync(h->x, 0, sizeof(float4) * h->P, st));
-    CK(cudaMemsetAsync(h->xbar, 0, sizeof(float4) * h->P, st));
+    CK(cudaMemsetAsync(h->xbar, 0, sizeof(float4) * 2 * h->P, st));
     h->iter = 0;
     h->phase = 0;
     return OSSCIR_OK;
@@ -750,7 +768,7 @@ osscir_status osscir_reconstruct(osscir_t h, const float* c_host, int n_iters, f
     CK(cudaMemcpyAsync(h->c, c_host, ray_bytes, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(h->y, 0, ray_bytes, st));
     CK(cudaMemsetAsync(h->x, 0, sizeof(float4) * h->P, st));
-    CK(cudaMemsetAsync(h->xbar, 0, sizeof(float4) * h->P, st));
+    CK(cudaMemsetAsync(h->xbar, 0, sizeof(float4) * 2 * h->P, st));
     h->iter = 0;
     h->phase = 0;
     const osscir_status s = osscir_mocca_step(h, n_iters, stream);
@@ -801,6 +819,7 @@ osscir_status osscir_set_state(osscir_t h, const float* x, const float* xbar, co
     cudaStream_t st = as_stream(stream);
     CK(cudaMemcpyAsync(h->x, x, sizeof(float4) * h->P, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(h->xbar, xbar, sizeof(float4) * h->P, cudaMemcpyDeviceToDevice, st));
+    CK(launch_xbar_columns(h->gc.grid.n, h->xbar, st));
     CK(cudaMemcpyAsync(h->y, y, sizeof(float4) * h->wf4() * h->L, cudaMemcpyDeviceToDevice, st));
     h->iter = iter;
     h->phase = 0;

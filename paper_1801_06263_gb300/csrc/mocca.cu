@@ -1033,11 +1033,13 @@ __device__ __forceinline__ void bp_finish(const GeomC& C, const StepParams& P, c
 __device__ __forceinline__ void pixel_step(const GeomC& C, const StepParams& P, const SolveD& D, int k,
                                            const float acc[9]) {
     const float4 x = D.x[k];
+    const int n = C.grid.n, kt = n * n + (k % n) * n + k / n;   // the column-major copy of xbar
     const double il = 1.0 / (double)P.lambda;
     double T[6] = {acc[3] * il, acc[4] * il, acc[5] * il, acc[6] * il, acc[7] * il, acc[8] * il};
     const double tr = T[0] + T[3] + T[5];
     if (!(tr > 0.0)) {
         D.xbar[k] = x;
+        D.xbar[kt] = x;
         return;
     }
     T[0] += 1e-12 * tr;
@@ -1060,7 +1062,9 @@ __device__ __forceinline__ void pixel_step(const GeomC& C, const StepParams& P, 
     }
     const float4 xn = make_float4((float)t[0], (float)t[1], (float)t[2], 0.f);
     D.x[k] = xn;
-    D.xbar[k] = make_float4(2.f * xn.x - x.x, 2.f * xn.y - x.y, 2.f * xn.z - x.z, 0.f);
+    const float4 xb = make_float4(2.f * xn.x - x.x, 2.f * xn.y - x.y, 2.f * xn.z - x.z, 0.f);
+    D.xbar[k] = xb;
+    D.xbar[kt] = xb;
 }
 
 // The back-projection and primal step of every pixel over the views [V0, V1);
@@ -1123,55 +1127,102 @@ __global__ void __launch_bounds__(kFwdThreads) k_fp_fwd_count(GeomC C, ExcTable 
     if ((threadIdx.x & 31) == 0 && v < C.n_views) warp_rows[v * ((C.n_bins + 31) >> 5) + blockIdx.x] = (uint32_t)n;
 }
 
-// Forward table, pass 2: lane r of warp w writes its j-th pair (pixel, weight)
-// in visiting order at slot row fwd_row[w] + j.
+// Forward table, pass 2: lane r of warp w writes its j-th pair (weight, pixel
+// step) in visiting order, two per slot row from fwd_row[w] (see FpTables).
+// The pixels index the xbar copy in which the warp's gathers are close: when
+// most of its rays run along x, neighbouring lanes sit in neighbouring rows of
+// one column, so the column-major copy (P + ix n + iy); else the row-major one.
 __global__ void __launch_bounds__(kFwdThreads) k_fp_fwd_fill(GeomC C, ExcTable E, const RayRec* rec,
-                                                             const uint32_t* __restrict__ fwd_row, int2* pairs) {
+                                                             const uint32_t* __restrict__ fwd_row, float* fwd_w,
+                                                             int16_t* fwd_d, int* fwd_k0, int* bad) {
     const int l = ray_of_thread(C);
+    const bool along_x = l >= 0 && !ray_rows(rec[l].r0);
+    const unsigned vote = __ballot_sync(0xffffffffu, along_x), live = __ballot_sync(0xffffffffu, l >= 0);
+    const bool col = 2 * __popc(vote) > __popc(live);
     if (l < 0) return;
     const int v = warp_view(blockIdx.y, kFwdThreads / 32);
     const size_t row = fwd_row[v * ((C.n_bins + 31) >> 5) + blockIdx.x];
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, n = C.grid.n;
     const float4 r0 = rec[l].r0, r1 = rec[l].r1;
-    int j = 0;
-    ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int k, float w) {
-        pairs[(row + j) * 32 + lane] = make_int2(k, __float_as_int(w));
+    int j = 0, prev = -1;
+    ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int kr, float w) {
+        const int k = col ? n * n + (kr % n) * n + kr / n : kr;
+        const size_t at = (row + (j & ~1)) * 32 + 2 * lane + (j & 1);
+        if (j == 0) {
+            fwd_k0[l] = k;
+            prev = k;
+        }
+        const int d = k - prev;
+        if (d < -32768 || d > 32767) *bad = 1;
+        fwd_w[at] = w;
+        fwd_d[at] = (int16_t)d;
+        prev = k;
         ++j;
     });
+    if (j == 0) fwd_k0[l] = 0;
 }
 
 // a1 from the forward table for ray l of warp wi = v nbg + bx: the same line sums
-// as proj_ray, in the same order.  The table is read four entries at a time, the
-// next four loaded while the current four's gathers of xbar are added, so a
-// table load is always in flight.
+// as proj_ray, in the same order.  The table is read four entries (two loads of
+// two) at a time, the next four loaded while the current four's gathers of xbar
+// are added, so a table load is always in flight.
 __device__ __forceinline__ void fp_proj_ray(const FpTables& T, const SolveD& D, int l, int wi) {
     const int lane = threadIdx.x & 31;
-    const int2* p = T.fwd_pairs + (size_t)T.fwd_row[wi] * 32 + lane;
+    const size_t base = (size_t)T.fwd_row[wi] * 32;
+    const float2* pw = reinterpret_cast<const float2*>(T.fwd_w + base) + lane;
+    const short2* pd = reinterpret_cast<const short2*>(T.fwd_d + base) + lane;
     const int n = __ldg(T.fwd_cnt + l);
+    int k = __ldg(T.fwd_k0 + l);
     LineSum acc;
     int j = 0;
     if (n >= 4) {
-        int2 a[4];
+        float2 w[2];
+        short2 d[2];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = __ldg(p + 32 * u);
+        for (int u = 0; u < 2; ++u) {
+            w[u] = __ldg(pw + 32 * u);
+            d[u] = __ldg(pd + 32 * u);
+        }
         for (; j + 3 < n; j += 4) {
-            p += 128;
-            int2 nx[4];
+            pw += 64;
+            pd += 64;
+            float2 wn[2];
+            short2 dn[2];
             const bool more = j + 7 < n;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) nx[u] = more ? __ldg(p + 32 * u) : make_int2(0, 0);
+            for (int u = 0; u < 2; ++u) {
+                wn[u] = more ? __ldg(pw + 32 * u) : make_float2(0.f, 0.f);
+                dn[u] = more ? __ldg(pd + 32 * u) : make_short2(0, 0);
+            }
+            int kk[4];
+            kk[0] = k + d[0].x;
+            kk[1] = kk[0] + d[0].y;
+            kk[2] = kk[1] + d[1].x;
+            kk[3] = kk[2] + d[1].y;
+            k = kk[3];
             float4 x[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = __ldg(D.xbar + a[u].x);
+            for (int u = 0; u < 4; ++u) x[u] = __ldg(D.xbar + kk[u]);
+            acc.add(w[0].x, x[0]);
+            acc.add(w[0].y, x[1]);
+            acc.add(w[1].x, x[2]);
+            acc.add(w[1].y, x[3]);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) acc.add(__int_as_float(a[u].y), x[u]);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) a[u] = nx[u];
+            for (int u = 0; u < 2; ++u) {
+                w[u] = wn[u];
+                d[u] = dn[u];
+            }
         }
     }
-    for (; j < n; ++j, p += 32) {
-        const int2 a = __ldg(p);
-        acc.add(__int_as_float(a.y), __ldg(D.xbar + a.x));
+    for (; j < n; j += 2, pw += 32, pd += 32) {
+        const float2 w = __ldg(pw);
+        const short2 d = __ldg(pd);
+        k += d.x;
+        acc.add(w.x, __ldg(D.xbar + k));
+        if (j + 1 < n) {
+            k += d.y;
+            acc.add(w.y, __ldg(D.xbar + k));
+        }
     }
     const float4 gs = acc.sum();
     D.g[l] = make_float4(gs.x, gs.y, gs.z, 0.f);
@@ -1529,7 +1580,7 @@ __global__ void __launch_bounds__(kBatchProjMaxThreads) k_batch_proj(const Solve
         const int bx = centre_out(w.y / nby, nbx);
         const int l = ray_at(C, bx, w.y % nby, vb);
         if (l >= 0) {
-            if (d.T.fwd_pairs) fp_proj_ray(d.T, d.D, l, (l / C.n_bins) * nbx + bx);   // the solve's table
+            if (d.T.fwd_w) fp_proj_ray(d.T, d.D, l, (l / C.n_bins) * nbx + bx);   // the solve's table
             else proj_ray(C, d.E, d.rec, d.D, l);
         }
     }
@@ -1612,6 +1663,13 @@ __global__ void __launch_bounds__(kReduceThreads) k_batch_dtpl(const SolveDesc* 
 }
 
 inline int blocks(int n, int t) { return (n + t - 1) / t; }
+
+// The column-major copy of xbar (P + ix n + iy) from the row-major maps.
+__global__ void k_xbar_columns(int n, float4* xbar) {
+    const int P = n * n;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P; k += gridDim.x * blockDim.x)
+        xbar[P + (k % n) * n + k / n] = xbar[k];
+}
 
 }  // namespace
 
@@ -1702,6 +1760,12 @@ cudaError_t launch_mocca_bp_partial(const GeomC& C, const ExcTable& E, const Ray
     return cudaGetLastError();
 }
 
+cudaError_t launch_xbar_columns(int n, float4* xbar, cudaStream_t st) {
+    const int P = n * n, blocks = (P + 255) / 256 < 4096 ? (P + 255) / 256 : 4096;
+    k_xbar_columns<<<blocks, 256, 0, st>>>(n, xbar);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fp_fwd_count(const GeomC& C, const ExcTable& E, const RayRec* rec, int* cnt,
                                 uint32_t* warp_rows, cudaStream_t st) {
     k_fp_fwd_count<<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, E, rec, cnt, warp_rows);
@@ -1709,11 +1773,11 @@ cudaError_t launch_fp_fwd_count(const GeomC& C, const ExcTable& E, const RayRec*
 }
 
 cudaError_t launch_fp_fwd_fill(const GeomC& C, const ExcTable& E, const RayRec* rec, const uint32_t* fwd_row,
-                               int2* pairs, cudaStream_t st) {
-    k_fp_fwd_fill<<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, E, rec, fwd_row, pairs);
+                               float* fwd_w, int16_t* fwd_d, int* fwd_k0, int* bad, cudaStream_t st) {
+    k_fp_fwd_fill<<<fwd_grid(C.n_bins, C.n_views), kFwdThreads, 0, st>>>(C, E, rec, fwd_row, fwd_w, fwd_d, fwd_k0,
+                                                                         bad);
     return cudaGetLastError();
 }
-
 cudaError_t launch_fpb_span(const GeomC& C, const ViewF* views, uint32_t* span, cudaStream_t st) {
     k_fpb_span<<<bt_tiles(C.grid.n), kBTThreads, 0, st>>>(C, views, span);
     return cudaGetLastError();

@@ -55,7 +55,9 @@ struct osscir_ctx {
     int fp_state = 0;   // 0 not built yet, 1 built, -1 not used (no room on the device)
     uint32_t* fwd_row = nullptr;
     int* fwd_cnt = nullptr;
-    int2* fwd_pairs = nullptr;
+    int* fwd_k0 = nullptr;
+    float* fwd_w = nullptr;   // null: the forward projection stays on the fly
+    int16_t* fwd_d = nullptr;
     uint32_t* bp_span = nullptr;
     uint32_t* bp_row = nullptr;
     uint16_t* bp_cnt = nullptr;
@@ -67,7 +69,7 @@ struct osscir_ctx {
     int bp_groups = 1, bp_chunk = 0, bp_nch = 0, bp_slots = 0;
     size_t fp_bytes = 0;
     osscir::FpTables fp() const {
-        return osscir::FpTables{fwd_row, fwd_cnt, fwd_pairs, bp_span, bp_row,    bp_cnt,   bp_w,
+        return osscir::FpTables{fwd_row, fwd_cnt, fwd_k0,  fwd_w,   fwd_d,     bp_span, bp_row, bp_cnt, bp_w,
                                 bp_slot, bp_roff, bp_rays,   bp_part, bp_groups, bp_chunk, bp_nch, bp_slots};
     }
     const osscir::FpTables* fp_or_null() const { return fp_state == 1 ? &fp_tab : nullptr; }

@@ -45,7 +45,7 @@ struct SolveD {
     const float4* c;    // [L] measured counts
     float4* y;          // [L] dual
     float4* x;          // [P] x_n
-    float4* xbar;       // [P] 2 x_n - x_{n-1}
+    float4* xbar;       // [2P] 2 x_n - x_{n-1}: pixel iy n + ix, then a column-major copy at P + ix n + iy
     const float* chord; // [L] (X 1)_l
     double* dtpl_part;  // [fwd blocks]
     float4* model;      // [L][kModelStride] local models kept for nested MOCCA, or null
@@ -71,10 +71,13 @@ inline int bt_tiles(int n) { return ((n + kBTX - 1) / kBTX) * ((n + kBTY - 1) / 
 // Footprint tables of one geometry: the pairs (l, k) of X with their weights,
 // in the order each projector visits them.
 //   Forward (ray-major): warp w = (view v, 32-bin group bx), w = v nbg + bx with
-//   nbg = ceil(n_bins / 32), lane r = bin 32 bx + r.  The j-th pair of ray l (in
-//   the visiting order of ray_weights) is fwd_pairs[(fwd_row[w] + j) 32 + r] =
-//   (pixel k, weight bits), fwd_cnt[l] pairs; fwd_row is the prefix sum of the
-//   warps' largest counts.
+//   nbg = ceil(n_bins / 32), lane r = bin 32 bx + r.  Ray l has fwd_cnt[l] pairs
+//   in the visiting order of ray_weights; its j-th pair is the weight fwd_w[i]
+//   and the pixel k_j = fwd_k0[l] + sum_{i <= j} fwd_d[i] (fwd_d: the 16-bit step
+//   from the previous pixel, 0 for the first), at i = (fwd_row[w] + j - j mod 2)
+//   32 + 2 r + j mod 2: two pairs side by side, so a lane reads two with one load
+//   (6 bytes a pair).  fwd_row is the prefix sum of the warps' largest counts,
+//   each rounded up to even.
 //   Back-projection (blocked): block b = t G + g (tile t, view group g of G =
 //   bp_groups); the group's views (the split of k_mocca_bp) in chunks of
 //   bp_chunk views, bp_nch chunks per group, entry e = b bp_nch + c.  bp_span
@@ -89,7 +92,9 @@ inline int bt_tiles(int n) { return ((n + kBTX - 1) / kBTX) * ((n + kBTY - 1) / 
 struct FpTables {
     const uint32_t* fwd_row;   // [n_views nbg + 1]
     const int* fwd_cnt;        // [L]
-    const int2* fwd_pairs;
+    const int* fwd_k0;         // [L] first pixel of each ray
+    const float* fwd_w;        // null: the forward projection is computed on the fly
+    const int16_t* fwd_d;
     const uint32_t* bp_span;   // [bt_tiles(n) n_views]
     const uint32_t* bp_row;    // [n_entries 8 + 1]
     const uint16_t* bp_cnt;    // [n_entries 256]
@@ -151,8 +156,11 @@ cudaError_t launch_mocca_bp_partial(const GeomC& C, const ExcTable& E, const Ray
 // rows; back-projection: slot rows per entry), then the fills from the row offsets.
 cudaError_t launch_fp_fwd_count(const GeomC& C, const ExcTable& E, const RayRec* rec, int* cnt,
                                 uint32_t* warp_rows, cudaStream_t st);
+// Writes the column-major copy of xbar ([2P]: P + ix n + iy) from its row-major half.
+cudaError_t launch_xbar_columns(int n, float4* xbar, cudaStream_t st);
+// Fills fwd_w, fwd_d and fwd_k0; sets *bad if a pixel step does not fit in 16 bits.
 cudaError_t launch_fp_fwd_fill(const GeomC& C, const ExcTable& E, const RayRec* rec, const uint32_t* fwd_row,
-                               int2* pairs, cudaStream_t st);
+                               float* fwd_w, int16_t* fwd_d, int* fwd_k0, int* bad, cudaStream_t st);
 cudaError_t launch_fpb_span(const GeomC& C, const ViewF* views, uint32_t* span, cudaStream_t st);
 cudaError_t launch_fpb_count(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views, int G,
                              int chunk, int nch, uint16_t* cnt, uint32_t* warp_rows, cudaStream_t st);

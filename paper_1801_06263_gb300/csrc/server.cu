@@ -105,11 +105,12 @@ size_t estimate_bytes(const Config& c) {
     const size_t L = (size_t)c.geom.n_views * c.geom.n_bins, P = (size_t)c.geom.n * c.geom.n;
     const size_t per_ray = 64 + 32 + 4 + 4 + 16 + 16 + 8 * 4 / 128 + 2;   // records, FP64 rays, chord, offsets, c, y, partials
     const size_t mu_pc = c.params.spc == 2 ? P * 16 + 12 * c.nE : 0;   // the caller's curves and a maps buffer
-    // footprint tables: about 0.9 n footprint pairs per ray (0.82 n measured at 256 x 256), 8.8 bytes each
+    // footprint tables: about 0.9 n footprint pairs per ray (0.82 n measured at 256 x 256), 6.9 bytes each
     // in the forward table and 7.5 in the back-projection's (with the rows' padding), and the view
     // groups' channel sums (at most 8 groups of 36 bytes per pixel)
-    const size_t tables = (size_t)(0.9 * c.geom.n * (double)L * 16.3) + P * 288 + L * 8;
-    return L * per_ray + P * 32 + (size_t)c.nE * c.geom.n_bins * 16 + c.geom.n_bins * 16 + 12 * c.nE +
+    const size_t tables = (size_t)(0.9 * c.geom.n * (double)L * 14.4) + P * 288 + L * 12;
+    // x, and xbar with its column-major copy: 48 bytes per pixel
+    return L * per_ray + P * 48 + (size_t)c.nE * c.geom.n_bins * 16 + c.geom.n_bins * 16 + 12 * c.nE +
            c.geom.n_views * 8 + (L / 8) * 8 + mu_pc + tables + (1 << 16);
 }
 
@@ -226,7 +227,7 @@ bool osscir_server::begin(Slot* s) {
            cudaMemcpyAsync(h->c, s->h_counts, sizeof(float4) * h->L, cudaMemcpyHostToDevice, st) == cudaSuccess &&
            cudaMemsetAsync(h->y, 0, sizeof(float4) * h->L, st) == cudaSuccess &&
            cudaMemsetAsync(h->x, 0, sizeof(float4) * h->P, st) == cudaSuccess &&
-           cudaMemsetAsync(h->xbar, 0, sizeof(float4) * h->P, st) == cudaSuccess &&
+           cudaMemsetAsync(h->xbar, 0, sizeof(float4) * 2 * h->P, st) == cudaSuccess &&
            cudaMemsetAsync(h->dtpl_out, 0, sizeof(double) * 2, st) == cudaSuccess;
 }
 
