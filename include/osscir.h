@@ -200,7 +200,7 @@ osscir_status osscir_mocca_step(osscir_t h, int n_iters, void *stream);
  * step matrix P_k (T^-1_k = P_k / lambda), into chan.  It does not change the
  * maps.  The caller sums chan over a partition of the views into ranges (one
  * all-reduce of 9 P floats per iteration); osscir_mocca_apply then takes every
- * pixel's primal step (the FP64 3x3 solve of the m-block SPC, the optional box,
+ * pixel's primal step (the 3x3 solve of the m-block SPC, the optional box,
  * the extrapolation) from the summed channels and counts the iteration.  With
  * the views of all ranges summed, the iterates equal osscir_mocca_step's up to
  * the order of the floating-point additions.

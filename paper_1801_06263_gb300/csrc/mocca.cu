@@ -13,7 +13,7 @@
 //       per-ray products b = alpha^T y' and S = sum_w alpha_w alpha_w^T / |alpha_w|.
 //   k_mocca_bp (pixel-driven):  v_k = sum_l X_lk b_l (= K^T y') and
 //       P_k = sum_l X_lk S_l (so T^-1_k = P_k / lambda, the m-block SPC), the
-//       FP64 3x3 solve, the primal step (optionally onto a box) and the
+//       3x3 solve (double-float), the primal step (optionally onto a box) and the
 //       extrapolation xbar' = 2 x' - x.
 #include "osscir_internal.cuh"
 #include "osscir_launch.h"
@@ -426,22 +426,6 @@ __device__ void clip_psd3(double h[6]) {
         h[0] = lhi * v[0] * v[0]; h[1] = lhi * v[0] * v[1]; h[2] = lhi * v[0] * v[2];
         h[3] = lhi * v[1] * v[1]; h[4] = lhi * v[1] * v[2]; h[5] = lhi * v[2] * v[2];
     }
-}
-
-// Inverse of a symmetric 3x3 (adjugate / determinant); returns false if singular.
-__device__ __forceinline__ bool inv_sym3(const double a[6], double o[6]) {
-    const double c00 = a[3] * a[5] - a[4] * a[4];
-    const double c01 = a[2] * a[4] - a[1] * a[5];
-    const double c02 = a[1] * a[4] - a[2] * a[3];
-    const double c11 = a[0] * a[5] - a[2] * a[2];
-    const double c12 = a[1] * a[2] - a[0] * a[4];
-    const double c22 = a[0] * a[3] - a[1] * a[1];
-    const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
-    if (!(det != 0.0) || !isfinite(det)) return false;
-    const double id = 1.0 / det;
-    o[0] = c00 * id; o[1] = c01 * id; o[2] = c02 * id;
-    o[3] = c11 * id; o[4] = c12 * id; o[5] = c22 * id;
-    return true;
 }
 
 // Sum of W double-float terms as a fixed tree: the first four pairwise, then the rest in order.
@@ -1028,39 +1012,67 @@ __device__ __forceinline__ void bp_finish(const GeomC& C, const StepParams& P, c
 }
 
 // a7 for pixel k from its nine back-projected channels: acc[0..2] = v_k = (K^T y')_k,
-// acc[3..8] = P_k (packed 00 01 02 11 12 22), T^-1_k = P_k / lambda; FP64 solve,
-// primal step (optionally onto the box) and the extrapolation xbar' = 2 x' - x.
+// acc[3..8] = P_k (packed 00 01 02 11 12 22), T^-1_k = P_k / lambda; the primal
+// step x' = x - T_k v_k (optionally onto the box) and the extrapolation
+// xbar' = 2 x' - x.  T_k = lambda (P_k + 1e-12 tr(P_k) I)^-1 (the regularisation
+// that keeps T positive definite) is applied by the adjugate in double-float
+// arithmetic on P_k scaled by an exact power of two near 1 / tr(P_k), so that the
+// cubed entries stay inside the FP32 exponent range; T_k has a condition number
+// near 6e6, and the ~48-bit double-float solve keeps the step to FP32 accuracy.
+// Only a step that leaves the box goes to the FP64 active-set solve.
 __device__ __forceinline__ void pixel_step(const GeomC& C, const StepParams& P, const SolveD& D, int k,
                                            const float acc[9]) {
     const float4 x = D.x[k];
     const int n = C.grid.n, kt = n * n + (k % n) * n + k / n;   // the column-major copy of xbar
-    const double il = 1.0 / (double)P.lambda;
-    double T[6] = {acc[3] * il, acc[4] * il, acc[5] * il, acc[6] * il, acc[7] * il, acc[8] * il};
-    const double tr = T[0] + T[3] + T[5];
-    if (!(tr > 0.0)) {
+    const double trd = (double)acc[3] + (double)acc[6] + (double)acc[8];
+    if (!(trd > 0.0)) {
         D.xbar[k] = x;
         D.xbar[kt] = x;
         return;
     }
-    T[0] += 1e-12 * tr;
-    T[3] += 1e-12 * tr;
-    T[5] += 1e-12 * tr;
-    double Ti[6];
-    double t[3] = {(double)x.x, (double)x.y, (double)x.z};
-    if (inv_sym3(T, Ti)) {
-        const double vv[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
-        t[0] -= Ti[0] * vv[0] + Ti[1] * vv[1] + Ti[2] * vv[2];
-        t[1] -= Ti[1] * vv[0] + Ti[3] * vv[1] + Ti[4] * vv[2];
-        t[2] -= Ti[2] * vv[0] + Ti[4] * vv[1] + Ti[5] * vv[2];
+    int e;
+    frexpf((float)trd, &e);
+    const float sc = ldexpf(1.0f, -e);   // tr(P) sc in [0.5, 1)
+    const float p1 = acc[4] * sc, p2 = acc[5] * sc, p4 = acc[7] * sc;
+    const float reg = 1e-12f * ((acc[3] * sc + acc[6] * sc) + acc[8] * sc);
+    const dfl p0 = df_2sum(acc[3] * sc, reg), p3 = df_2sum(acc[6] * sc, reg), p5 = df_2sum(acc[8] * sc, reg);
+    const dfl P1 = {p1, 0.0f}, P2 = {p2, 0.0f};
+    const dfl c00 = df_sub(df_mul(p3, p5), df_2prod(p4, p4));
+    const dfl c01 = df_sub(df_2prod(p2, p4), df_mulf(p5, p1));
+    const dfl c02 = df_sub(df_2prod(p1, p4), df_mulf(p3, p2));
+    const dfl c11 = df_sub(df_mul(p0, p5), df_2prod(p2, p2));
+    const dfl c12 = df_sub(df_2prod(p1, p2), df_mulf(p0, p4));
+    const dfl c22 = df_sub(df_mul(p0, p3), df_2prod(p1, p1));
+    const dfl det = df_add(df_add(df_mul(p0, c00), df_mul(P1, c01)), df_mul(P2, c02));
+    dfl t[3] = {{x.x, 0.0f}, {x.y, 0.0f}, {x.z, 0.0f}};
+    if (det.hi != 0.0f && isfinite(det.hi)) {
+        const dfl f = df_mulf(df_rcp(det), P.lambda * sc);   // lambda sc / det
+        const dfl u0 = df_add(df_add(df_mulf(c00, acc[0]), df_mulf(c01, acc[1])), df_mulf(c02, acc[2]));
+        const dfl u1 = df_add(df_add(df_mulf(c01, acc[0]), df_mulf(c11, acc[1])), df_mulf(c12, acc[2]));
+        const dfl u2 = df_add(df_add(df_mulf(c02, acc[0]), df_mulf(c12, acc[1])), df_mulf(c22, acc[2]));
+        t[0] = df_sub(t[0], df_mul(u0, f));
+        t[1] = df_sub(t[1], df_mul(u1, f));
+        t[2] = df_sub(t[2], df_mul(u2, f));
     }
-    if (P.use_box &&
-        (t[0] < P.lo[0] || t[0] > P.hi[0] || t[1] < P.lo[1] || t[1] > P.hi[1] || t[2] < P.lo[2] || t[2] > P.hi[2])) {
+    float xo3[3] = {df_f(t[0]), df_f(t[1]), df_f(t[2])};
+    if (P.use_box && (xo3[0] < P.lo[0] || xo3[0] > P.hi[0] || xo3[1] < P.lo[1] || xo3[1] > P.hi[1] ||
+                      xo3[2] < P.lo[2] || xo3[2] > P.hi[2])) {
+        const double il = 1.0 / (double)P.lambda;
+        double T[6] = {acc[3] * il, acc[4] * il, acc[5] * il, acc[6] * il, acc[7] * il, acc[8] * il};
+        const double tr = T[0] + T[3] + T[5];
+        T[0] += 1e-12 * tr;
+        T[3] += 1e-12 * tr;
+        T[5] += 1e-12 * tr;
         const double Q[3][3] = {{T[0], T[1], T[2]}, {T[1], T[3], T[4]}, {T[2], T[4], T[5]}};
+        const double td[3] = {(double)t[0].hi + (double)t[0].lo, (double)t[1].hi + (double)t[1].lo,
+                              (double)t[2].hi + (double)t[2].lo};
         double xo[3];
-        box_prox3(Q, t, P.lo, P.hi, xo);
-        t[0] = xo[0]; t[1] = xo[1]; t[2] = xo[2];
+        box_prox3(Q, td, P.lo, P.hi, xo);
+        xo3[0] = (float)xo[0];
+        xo3[1] = (float)xo[1];
+        xo3[2] = (float)xo[2];
     }
-    const float4 xn = make_float4((float)t[0], (float)t[1], (float)t[2], 0.f);
+    const float4 xn = make_float4(xo3[0], xo3[1], xo3[2], 0.f);
     D.x[k] = xn;
     const float4 xb = make_float4(2.f * xn.x - x.x, 2.f * xn.y - x.y, 2.f * xn.z - x.z, 0.f);
     D.xbar[k] = xb;
