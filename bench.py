@@ -63,20 +63,25 @@ def _measured(key, default=None):
 
 # Unit counts per SM of this GPU generation (the SM count and the clock come
 # from the device at run time): 128 FP32 lanes (one FMA = 2 flop per clock
-# each), 4 warp schedulers (one warp instruction issued per clock each), and
-# 128 bytes per clock from L1 to the register file.
-FP32_LANES_PER_SM, SCHEDULERS_PER_SM, L1_BYTES_PER_CLK_PER_SM = 128, 4, 128
+# each), 4 warp schedulers (one warp instruction issued per clock each),
+# 128 bytes per clock from L1 to the register file, and one L1 data-pipe
+# wavefront per clock (ncu's l1tex__data_pipe_lsu_wavefronts peak).
+FP32_LANES_PER_SM, SCHEDULERS_PER_SM, L1_BYTES_PER_CLK_PER_SM, L1_WAVEFRONTS_PER_CLK_PER_SM = 128, 4, 128, 1
 # Per launch of each per-iteration kernel, from one ncu --set full capture
-# (cold cache) of the medium_256 workload: DRAM bytes (read + write) and warp
-# instructions executed.  Valid only for that workload and for the kernel
-# sources they were taken on (source_sha, see _source_sha).
+# (cold cache) of the medium_256 workload: DRAM bytes (read + write), warp
+# instructions executed and L1 data-pipe wavefronts (ncu's percentage of peak x
+# elapsed SM cycles x the capturing GPU's SMs).  Valid only for that workload and for
+# the kernel sources they were taken on (source_sha, see _source_sha).
 NCU_WORKLOAD = "medium_256"
+_SHA = "8e9acdd2e1d068ce"
 NCU_COUNTS = {
-    "k_fp_proj": {"dram_bytes": 471092736 + 4667648, "warp_instructions": 36490880, "source_sha": "5d35a0ffd9d037b6"},
-    "k_mocca_ray": {"dram_bytes": 23002624 + 2304, "warp_instructions": 113676145, "source_sha": "5d35a0ffd9d037b6"},
+    "k_fp_proj": {"dram_bytes": 363441664 + 4134400, "warp_instructions": 41112016,
+                  "l1_wavefronts": 23248308, "source_sha": _SHA},
+    "k_mocca_ray": {"dram_bytes": 23001088 + 768, "warp_instructions": 113644965,
+                    "l1_wavefronts": 8277459, "source_sha": _SHA},
     # the back-projection's two launches: k_fpb_bp and k_fpb_finish
-    "k_fpb_bp": {"dram_bytes": 428959488 + 16539648 + 19964928, "warp_instructions": 78614524 + 1333248,
-                 "source_sha": "5d35a0ffd9d037b6"},
+    "k_fpb_bp": {"dram_bytes": 428922112 + 16520448 + 19972864, "warp_instructions": 78614524 + 1998848,
+                 "l1_wavefronts": 42567818 + 264250, "source_sha": _SHA},
 }
 
 
@@ -99,6 +104,7 @@ def device_roofs(dev, sm_mhz):
             "fp32_tflops": sms * FP32_LANES_PER_SM * 2 * ghz / 1e3,
             "issue_per_s": sms * SCHEDULERS_PER_SM * ghz * 1e9,
             "l1_tbps": sms * L1_BYTES_PER_CLK_PER_SM * ghz / 1e3,
+            "l1_wavefronts_per_s": sms * L1_WAVEFRONTS_PER_CLK_PER_SM * ghz * 1e9,
             "source": f"{sms} SMs (device) x per-SM unit counts x {sm_mhz:.0f} MHz (median SM clock sampled "
                       "during the timed steps)"}
 
@@ -364,12 +370,13 @@ def run_gpu(args):
     G = bp_view_groups(P, w.geom.n_views)
     if table_bytes:
         # footprint tables: the projections stream them.  Algorithmic HBM bytes per
-        # launch: forward 8 B per footprint pair (pixel, weight) + xbar read (16 B per
-        # pixel) + g written and the counts read (20 B per ray); back-projection 6 B per
-        # pair (weight, stage slot) + the view groups' channel sums written and read
-        # (2 x 36 B per pixel and group) + x, xbar read and written (48 B per pixel)
+        # launch: forward 6 B per footprint pair (weight, 16-bit pixel step) + xbar read
+        # (16 B per pixel) + g written and the pair count and first pixel read (24 B per
+        # ray); back-projection 6 B per pair (weight, stage slot) + the view groups'
+        # channel sums written and read (2 x 36 B per pixel and group) + x read and
+        # written, xbar and its column-major copy written (64 B per pixel)
         names = ("k_fp_proj", "k_mocca_ray", "k_fpb_bp")
-        alg = (8.0 * nnz + 16.0 * P + 20.0 * L, None, 6.0 * nnz + 72.0 * G * P + 48.0 * P)
+        alg = (6.0 * nnz + 16.0 * P + 24.0 * L, None, 6.0 * nnz + 72.0 * G * P + 64.0 * P)
     else:
         names = ("k_mocca_proj", "k_mocca_ray", "k_mocca_bp")
         alg = (None, None, None)
@@ -402,7 +409,13 @@ def run_gpu(args):
             row["issue_frac"] = ncu[k]["warp_instructions"] / (sec * roofs["issue_per_s"])
             row["dram_bytes"] = ncu[k]["dram_bytes"]
             row["dram_frac"] = ncu[k]["dram_bytes"] / sec / 1e9 / HBM_PEAK_GBPS
-        row["binding"] = "hbm" if v["bytes"] else "instruction issue"
+            row["l1_wavefronts"] = ncu[k]["l1_wavefronts"]
+            row["l1_frac"] = ncu[k]["l1_wavefronts"] / (sec * roofs["l1_wavefronts_per_s"])
+            # the binding roof: the unit the kernel keeps busiest
+            fr = {"hbm": row["dram_frac"], "instruction issue": row["issue_frac"], "L1 data pipe": row["l1_frac"]}
+            row["binding"] = max(fr, key=fr.get)
+        else:
+            row["binding"] = "hbm" if v["bytes"] else "instruction issue"
         kernels[k] = row
     traffic = ncu[dom]["dram_bytes"] if ncu.get(dom) else None
     if kern[dom]["bytes"]:
@@ -410,6 +423,11 @@ def run_gpu(args):
         roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": HBM_PEAK_GBPS, "unit": "GB/s",
                     "frac": ach / HBM_PEAK_GBPS, "traffic": traffic, "peak_source": HBM_PEAK_SOURCE,
                     "algorithmic_bytes": kern[dom]["bytes"]}
+        if ncu.get(dom):
+            ach_w = ncu[dom]["l1_wavefronts"] / (kern[dom]["ms"] * 1e-3)
+            roofline["binding"] = {"unit": "L1 data-pipe wavefronts", "wavefronts": ncu[dom]["l1_wavefronts"],
+                                   "achieved": ach_w / 1e12, "peak": roofs["l1_wavefronts_per_s"] / 1e12,
+                                   "peak_unit": "T wavefronts/s", "frac": ach_w / roofs["l1_wavefronts_per_s"]}
     else:
         ach = kern[dom]["flop"] / (kern[dom]["ms"] * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": roofs["fp32_tflops"],

@@ -51,4 +51,13 @@ def test_roofs_come_from_the_device_and_the_sampled_clock(monkeypatch):
     assert abs(r["fp32_tflops"] - 76 * 128 * 2 * 1.5e9 / 1e12) < 1e-9
     assert abs(r["issue_per_s"] - 76 * 4 * 1.5e9) < 1.0
     assert abs(r["l1_tbps"] - 76 * 128 * 1.5e9 / 1e12) < 1e-9
+    assert abs(r["l1_wavefronts_per_s"] - 76 * 1.5e9) < 1.0
     assert "76 SMs" in r["source"] and "1500 MHz" in r["source"]
+
+
+def test_kept_ncu_counts_are_complete():
+    """Every kept ncu figure names the kernel code it was taken on (the bench drops
+    the figures whose source hash no longer matches)."""
+    for k, v in bench.NCU_COUNTS.items():
+        assert len(v["source_sha"]) == 16, k
+        assert v["dram_bytes"] > 0 and v["warp_instructions"] > 0 and v["l1_wavefronts"] > 0
