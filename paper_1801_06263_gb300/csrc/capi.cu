@@ -54,7 +54,7 @@ void free_ctx(osscir_ctx* h) {
     void* ptrs[] = {h->rec,     h->r64,    h->views,     h->chord,    h->exc_off,    h->exc_ent,  h->s4,
                     h->N4,      h->mu,     h->mu_in,     h->g,        h->c,          h->y,        h->x,
                     h->xbar,    h->xo,     h->dtpl_part, h->dtpl_out, h->bad_counts, h->model,    h->fwd_row,
-                    h->fwd_cnt, h->fwd_k0, h->fwd_w, h->fwd_d, h->bp_span, h->bp_row,  h->bp_cnt,   h->bp_w,
+                    h->fwd_cnt, h->fwd_k0, h->fwd_w, h->fwd_d, h->bp_span, h->bp_row,  h->bp_w,
                     h->bp_slot, h->bp_roff,   h->bp_rays, h->bp_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -345,7 +345,7 @@ osscir_status build(osscir_ctx* h, const osscir_geometry* g, const osscir_spectr
 }
 
 void free_tables(osscir_ctx* h) {
-    void* ptrs[] = {h->fwd_row, h->fwd_cnt, h->fwd_k0, h->fwd_w, h->fwd_d, h->bp_span, h->bp_row, h->bp_cnt,
+    void* ptrs[] = {h->fwd_row, h->fwd_cnt, h->fwd_k0, h->fwd_w, h->fwd_d, h->bp_span, h->bp_row,
                     h->bp_w,    h->bp_slot, h->bp_roff,   h->bp_rays, h->bp_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -356,7 +356,6 @@ void free_tables(osscir_ctx* h) {
     h->fwd_d = nullptr;
     h->bp_span = nullptr;
     h->bp_row = nullptr;
-    h->bp_cnt = nullptr;
     h->bp_w = nullptr;
     h->bp_slot = nullptr;
     h->bp_roff = nullptr;
@@ -492,9 +491,8 @@ osscir_status build_tables(osscir_ctx* h) {
         CKT(dalloc(&h->bp_rays, rays.size()));
         CKT(cudaMemcpyAsync(h->bp_roff, roff.data(), sizeof(uint32_t) * (n_e + 1), cudaMemcpyHostToDevice, st));
         CKT(cudaMemcpyAsync(h->bp_rays, rays.data(), sizeof(int) * rays.size(), cudaMemcpyHostToDevice, st));
-        CKT(dalloc(&h->bp_cnt, n_e * kBTThreads));
         CKT(dalloc(&h->bp_row, n_e * (kBTThreads / 32) + 1));
-        CKT(launch_fpb_count(C, h->exc(), h->rec, h->views, G, chunk, nch, h->bp_cnt, h->bp_row, st));
+        CKT(launch_fpb_count(C, h->exc(), h->rec, h->views, G, chunk, nch, h->bp_row, st));
         const size_t n_w = n_e * (kBTThreads / 32);
         std::vector<uint32_t> brow(n_w + 1, 0);
         CKT(cudaMemcpyAsync(brow.data(), h->bp_row, sizeof(uint32_t) * n_w, cudaMemcpyDeviceToHost, st));
@@ -505,6 +503,9 @@ osscir_status build_tables(osscir_ctx* h) {
         CKT(dalloc(&h->bp_w, (size_t)brow[n_w] * 32));
         CKT(dalloc(&h->bp_slot, (size_t)brow[n_w] * 32));
         CKT(dalloc(&h->bp_part, (size_t)G * 9 * h->P));
+        // rows a pixel does not fill: no slot (0xffff), weight 0
+        CKT(cudaMemsetAsync(h->bp_slot, 0xff, sizeof(uint16_t) * (size_t)brow[n_w] * 32, st));
+        CKT(cudaMemsetAsync(h->bp_w, 0, sizeof(float) * (size_t)brow[n_w] * 32, st));
         CKT(launch_fpb_fill(C, h->exc(), h->rec, h->views, h->bp_span, G, chunk, nch, h->bp_row, h->bp_w,
                             h->bp_slot, st));
         h->bp_chunk = chunk;

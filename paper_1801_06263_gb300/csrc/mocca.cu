@@ -1349,10 +1349,17 @@ __device__ __forceinline__ int chunk_offsets(const uint32_t* span, int t, int n_
     return total;
 }
 
-// Table pass 1: each pixel's pair count per chunk, and per (chunk, warp) the largest.
+// The table rows of a warp are aligned per view: view u of a chunk takes K_u rows,
+// the largest number of pairs any of the warp's pixels has in u, so that at every
+// row the warp's lanes read stage slots of one view (neighbouring slots, few bank
+// conflicts); a pixel with fewer pairs in u leaves the rest of them empty (slot
+// kBTNoSlot).
+constexpr uint16_t kBTNoSlot = 0xffff;
+
+// Table pass 1: per (block, chunk) and warp the number of rows, the sum of K_u.
 __global__ void __launch_bounds__(kBTThreads) k_fpb_count(GeomC C, ExcTable E, const RayRec* rec,
                                                           const ViewF* views, int G, int chunk, int nch,
-                                                          uint16_t* cnt, uint32_t* warp_rows) {
+                                                          uint32_t* warp_rows) {
     const int b = blockIdx.x, t = b / G, g = b % G, tid = threadIdx.x;
     int ix, iy;
     bt_pixel(C.grid.n, t, tid, ix, iy);
@@ -1360,16 +1367,20 @@ __global__ void __launch_bounds__(kBTThreads) k_fpb_count(GeomC C, ExcTable E, c
     for (int c = 0; c < nch; ++c) {
         int u0, u1;
         chunk_views(C.n_views, g, G, chunk, c, u0, u1);
-        int n = 0;
-        if (valid) pixel_pairs(C, E, rec, views, ix, iy, u0, u1, [&](int, float) { ++n; });
+        uint32_t rows = 0;
+        for (int u = u0; u < u1; ++u) {
+            int n = 0;
+            if (valid) pixel_pairs(C, E, rec, views, ix, iy, u, u + 1, [&](int, float) { ++n; });
+            rows += (uint32_t)__reduce_max_sync(0xffffffffu, n);
+        }
         const size_t e = (size_t)b * nch + c;
-        cnt[e * kBTThreads + tid] = (uint16_t)n;
-        n = __reduce_max_sync(0xffffffffu, n);
-        if ((tid & 31) == 0) warp_rows[e * (kBTThreads / 32) + (tid >> 5)] = (uint32_t)n;
+        if ((tid & 31) == 0) warp_rows[e * (kBTThreads / 32) + (tid >> 5)] = rows;
     }
 }
 
-// Table pass 2: the pairs (stage slot, weight) at slot row bp_row[(e, warp)] + j.
+// Table pass 2: the pairs (stage slot, weight) at their rows: view u of the chunk
+// from the warp's row offset of u, pair j of a lane at row bp_row[(e, warp)] + j
+// (two rows side by side per lane).  The slots start as kBTNoSlot (memset).
 __global__ void __launch_bounds__(kBTThreads) k_fpb_fill(GeomC C, ExcTable E, const RayRec* rec,
                                                          const ViewF* views, const uint32_t* __restrict__ span,
                                                          int G, int chunk, int nch,
@@ -1378,7 +1389,7 @@ __global__ void __launch_bounds__(kBTThreads) k_fpb_fill(GeomC C, ExcTable E, co
     const int b = blockIdx.x, t = b / G, g = b % G, tid = threadIdx.x, lane = tid & 31;
     int ix, iy;
     bt_pixel(C.grid.n, t, tid, ix, iy);
-    if (ix >= C.grid.n || iy >= C.grid.n) return;
+    const bool valid = ix < C.grid.n && iy < C.grid.n;
     for (int c = 0; c < nch; ++c) {
         int u0, u1;
         chunk_views(C.n_views, g, G, chunk, c, u0, u1);
@@ -1386,15 +1397,23 @@ __global__ void __launch_bounds__(kBTThreads) k_fpb_fill(GeomC C, ExcTable E, co
         chunk_offsets(span, t, C.n_views, u0, u1, off, tlo, wid);
         const size_t e = (size_t)b * nch + c;
         const size_t row = bp_row[e * (kBTThreads / 32) + (tid >> 5)];
-        int j = 0;
-        pixel_pairs(C, E, rec, views, ix, iy, u0, u1, [&](int l, float w) {
-            const int u = l / C.n_bins, i = u - u0;
-            const int slot = off[i] + (l - u * C.n_bins) - tlo[i];
-            const size_t at = (row + (j & ~1)) * 32 + 2 * lane + (j & 1);   // entries j, j + 1 side by side
-            bp_w[at] = w;
-            bp_slot[at] = (uint16_t)slot;
-            ++j;
-        });
+        int j0 = 0;   // the warp's first row of view u
+        for (int u = u0; u < u1; ++u) {
+            int n = 0;
+            if (valid) pixel_pairs(C, E, rec, views, ix, iy, u, u + 1, [&](int, float) { ++n; });
+            const int K = __reduce_max_sync(0xffffffffu, n);
+            int j = j0;
+            if (valid)
+                pixel_pairs(C, E, rec, views, ix, iy, u, u + 1, [&](int l, float w) {
+                    const int i = u - u0;
+                    const int slot = off[i] + (l - u * C.n_bins) - tlo[i];
+                    const size_t at = (row + (j & ~1)) * 32 + 2 * lane + (j & 1);   // rows j, j + 1 side by side
+                    bp_w[at] = w;
+                    bp_slot[at] = (uint16_t)slot;
+                    ++j;
+                });
+            j0 += K;
+        }
     }
 }
 
@@ -1476,10 +1495,14 @@ __device__ __forceinline__ void fpb_block(const GeomC& C, const FpTables& T, con
         }
         __syncthreads();   // chunk c staged by every thread
         const size_t e = e0 + c;
-        const int n = __ldg(T.bp_cnt + e * kBTThreads + tid);
-        const size_t row = __ldg(T.bp_row + e * (kBTThreads / 32) + (tid >> 5));   // even
+        const uint32_t* rp = T.bp_row + e * (kBTThreads / 32) + (tid >> 5);
+        const size_t row = __ldg(rp);                  // even
+        const int n = (int)(__ldg(rp + 1) - row);      // the warp's rows (even): the same for every lane
         const float2* wp = reinterpret_cast<const float2*>(T.bp_w + row * 32) + lane;
         const ushort2* sp = reinterpret_cast<const ushort2*>(T.bp_slot + row * 32) + lane;
+        auto take = [&](float w, unsigned s) {
+            if (s != kBTNoSlot && (!PARTIAL || (B.ray[s] >= l_lo && B.ray[s] < l_hi))) bp_accumulate_slot(acc, w, B, s);
+        };
         int j = 0;
         for (; j + 7 < n; j += 8) {   // eight table entries (four loads of two) in flight
             float2 w[4];
@@ -1491,10 +1514,8 @@ __device__ __forceinline__ void fpb_block(const GeomC& C, const FpTables& T, con
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (!PARTIAL || (B.ray[sl[q].x] >= l_lo && B.ray[sl[q].x] < l_hi))
-                    bp_accumulate_slot(acc, w[q].x, B, sl[q].x);
-                if (!PARTIAL || (B.ray[sl[q].y] >= l_lo && B.ray[sl[q].y] < l_hi))
-                    bp_accumulate_slot(acc, w[q].y, B, sl[q].y);
+                take(w[q].x, sl[q].x);
+                take(w[q].y, sl[q].y);
             }
             wp += 128;
             sp += 128;
@@ -1502,9 +1523,8 @@ __device__ __forceinline__ void fpb_block(const GeomC& C, const FpTables& T, con
         for (; j < n; j += 2, wp += 32, sp += 32) {
             const float2 w = __ldg(wp);
             const ushort2 sl = __ldg(sp);
-            if (!PARTIAL || (B.ray[sl.x] >= l_lo && B.ray[sl.x] < l_hi)) bp_accumulate_slot(acc, w.x, B, sl.x);
-            if (j + 1 < n && (!PARTIAL || (B.ray[sl.y] >= l_lo && B.ray[sl.y] < l_hi)))
-                bp_accumulate_slot(acc, w.y, B, sl.y);
+            take(w.x, sl.x);
+            take(w.y, sl.y);
         }
         __syncthreads();   // this buffer is read by everyone before chunk c + 2 overwrites it
     }
@@ -1796,8 +1816,8 @@ cudaError_t launch_fpb_span(const GeomC& C, const ViewF* views, uint32_t* span, 
 }
 
 cudaError_t launch_fpb_count(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views, int G,
-                             int chunk, int nch, uint16_t* cnt, uint32_t* warp_rows, cudaStream_t st) {
-    k_fpb_count<<<bt_tiles(C.grid.n) * G, kBTThreads, 0, st>>>(C, E, rec, views, G, chunk, nch, cnt, warp_rows);
+                             int chunk, int nch, uint32_t* warp_rows, cudaStream_t st) {
+    k_fpb_count<<<bt_tiles(C.grid.n) * G, kBTThreads, 0, st>>>(C, E, rec, views, G, chunk, nch, warp_rows);
     return cudaGetLastError();
 }
 

@@ -60,7 +60,6 @@ struct osscir_ctx {
     int16_t* fwd_d = nullptr;
     uint32_t* bp_span = nullptr;
     uint32_t* bp_row = nullptr;
-    uint16_t* bp_cnt = nullptr;
     float* bp_w = nullptr;   // null: the back-projection stays on the fly
     uint16_t* bp_slot = nullptr;
     uint32_t* bp_roff = nullptr;
@@ -69,7 +68,7 @@ struct osscir_ctx {
     int bp_groups = 1, bp_chunk = 0, bp_nch = 0, bp_slots = 0;
     size_t fp_bytes = 0;
     osscir::FpTables fp() const {
-        return osscir::FpTables{fwd_row, fwd_cnt, fwd_k0,  fwd_w,   fwd_d,     bp_span, bp_row, bp_cnt, bp_w,
+        return osscir::FpTables{fwd_row, fwd_cnt, fwd_k0,  fwd_w,   fwd_d,     bp_span, bp_row, bp_w,
                                 bp_slot, bp_roff, bp_rays,   bp_part, bp_groups, bp_chunk, bp_nch, bp_slots};
     }
     const osscir::FpTables* fp_or_null() const { return fp_state == 1 ? &fp_tab : nullptr; }

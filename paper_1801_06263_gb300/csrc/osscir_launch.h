@@ -83,11 +83,13 @@ inline int bt_tiles(int n) { return ((n + kBTX - 1) / kBTX) * ((n + kBTY - 1) / 
 //   bp_chunk views, bp_nch chunks per group, entry e = b bp_nch + c.  bp_span
 //   [t n_views + u] = tlo | span << 16: the union of the tile's candidate bins in
 //   view u.  An entry's rays, view after view (ray (u, tlo + i)), are its stage
-//   slots: bp_rays[bp_roff[e] + slot], at most bp_slots of them.  Thread r's
-//   pairs (stage slot, weight) of entry e, bp_cnt[256 e + r] of them in the order
-//   of bp_pixel_sum, go two per slot row: pair j at (bp_slot, bp_w)[(row + j - j
-//   mod 2) 32 + 2 (r mod 32) + j mod 2], row = bp_row[8 e + r / 32] (the rows of
-//   a warp are even in number, so that a lane reads two pairs with one load).
+//   slots: bp_rays[bp_roff[e] + slot], at most bp_slots of them.  The rows of
+//   warp w of entry e, bp_row[8 e + w] .. bp_row[8 e + w + 1] (an even number, so
+//   that a lane reads two rows with one load), are aligned per view: view u of
+//   the chunk takes as many rows as the warp's largest pair count in u.  Thread
+//   r's pairs (stage slot, weight) in the order of bp_pixel_sum sit at rows j of
+//   their view, (bp_slot, bp_w)[(row + j - j mod 2) 32 + 2 (r mod 32) + j mod 2];
+//   the rows a pixel does not fill hold the slot 0xffff.
 //   bp_part: [G][9][P] scratch for the groups' channel sums.
 struct FpTables {
     const uint32_t* fwd_row;   // [n_views nbg + 1]
@@ -97,7 +99,6 @@ struct FpTables {
     const int16_t* fwd_d;
     const uint32_t* bp_span;   // [bt_tiles(n) n_views]
     const uint32_t* bp_row;    // [n_entries 8 + 1]
-    const uint16_t* bp_cnt;    // [n_entries 256]
     const float* bp_w;         // null: the back-projection is computed on the fly
     const uint16_t* bp_slot;
     const uint32_t* bp_roff;   // [n_entries + 1]
@@ -163,7 +164,7 @@ cudaError_t launch_fp_fwd_fill(const GeomC& C, const ExcTable& E, const RayRec* 
                                float* fwd_w, int16_t* fwd_d, int* fwd_k0, int* bad, cudaStream_t st);
 cudaError_t launch_fpb_span(const GeomC& C, const ViewF* views, uint32_t* span, cudaStream_t st);
 cudaError_t launch_fpb_count(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views, int G,
-                             int chunk, int nch, uint16_t* cnt, uint32_t* warp_rows, cudaStream_t st);
+                             int chunk, int nch, uint32_t* warp_rows, cudaStream_t st);
 cudaError_t launch_fpb_fill(const GeomC& C, const ExcTable& E, const RayRec* rec, const ViewF* views,
                             const uint32_t* span, int G, int chunk, int nch, const uint32_t* bp_row, float* bp_w,
                             uint16_t* bp_slot, cudaStream_t st);
