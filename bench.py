@@ -114,8 +114,11 @@ KERNEL_SOURCES = ("mocca.cu", "osscir_internal.cuh", "osscir_launch.h")
 
 def _source_sha() -> str:
     """Hash of the code of the per-iteration kernels (the traffic figures are tied to it):
-    the sources with comments and blank lines removed, so that a comment edit keeps it."""
+    the sources with comments and blank lines removed, so that a comment edit keeps it,
+    and the compiler flags."""
+    from paper_1801_06263_gb300 import build as _b
     h = hashlib.sha256()
+    h.update(" ".join(_b.FLAGS).encode())
     for f in KERNEL_SOURCES:
         text = open(os.path.join(ROOT, "paper_1801_06263_gb300", "csrc", f)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)

@@ -18,7 +18,11 @@ LIB = os.path.join(OUT, "libosscir.so")
 SOURCES = ["batch.cu", "capi.cu", "geometry.cu", "mocca.cu", "noalloc.cu", "noise.cu", "server.cu"]
 HEADERS = ["osscir_internal.cuh", "osscir_launch.h", "osscir_ctx.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# -fmad=false: no implicit contraction of a * b + c.  Every fused multiply-add
+# is an explicit fmaf / fma in the source, so each kernel computes the same
+# roundings whatever its register budget or inlining context; the plain,
+# batched and served forms rely on that to give bit-identical iterates.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-fmad=false"]
 
 
 def _nvcc() -> str:

@@ -319,12 +319,12 @@ __device__ __forceinline__ dfl df_rcp(dfl x) {
 __device__ __forceinline__ bool eigvec3(const double h[6], double lam, double v[3]) {
     const double a00 = h[0] - lam, a11 = h[3] - lam, a22 = h[5] - lam;
     // rows r0 = (a00, h1, h2), r1 = (h1, a11, h4), r2 = (h2, h4, a22)
-    const double c0x = h[1] * h[4] - h[2] * a11, c0y = h[2] * h[1] - a00 * h[4], c0z = a00 * a11 - h[1] * h[1];
-    const double c1x = h[1] * a22 - h[2] * h[4], c1y = h[2] * h[2] - a00 * a22, c1z = a00 * h[4] - h[1] * h[2];
-    const double c2x = a11 * a22 - h[4] * h[4], c2y = h[4] * h[2] - h[1] * a22, c2z = h[1] * h[4] - a11 * h[2];
-    const double n0 = c0x * c0x + c0y * c0y + c0z * c0z;
-    const double n1 = c1x * c1x + c1y * c1y + c1z * c1z;
-    const double n2 = c2x * c2x + c2y * c2y + c2z * c2z;
+    const double c0x = fma(h[1], h[4], -h[2] * a11), c0y = fma(h[2], h[1], -a00 * h[4]), c0z = fma(a00, a11, -h[1] * h[1]);
+    const double c1x = fma(h[1], a22, -h[2] * h[4]), c1y = fma(h[2], h[2], -a00 * a22), c1z = fma(a00, h[4], -h[1] * h[2]);
+    const double c2x = fma(a11, a22, -h[4] * h[4]), c2y = fma(h[4], h[2], -h[1] * a22), c2z = fma(h[1], h[4], -a11 * h[2]);
+    const double n0 = fma(c0x, c0x, fma(c0y, c0y, c0z * c0z));
+    const double n1 = fma(c1x, c1x, fma(c1y, c1y, c1z * c1z));
+    const double n2 = fma(c2x, c2x, fma(c2y, c2y, c2z * c2z));
     double bx = c0x, by = c0y, bz = c0z, best = n0;
     if (n1 > best) { bx = c1x; by = c1y; bz = c1z; best = n1; }
     if (n2 > best) { bx = c2x; by = c2y; bz = c2z; best = n2; }
@@ -382,11 +382,11 @@ __device__ void clip_psd3_jacobi(double h[6]) {
 // (trace, deviatoric part, arccos of half the normalised determinant) and the
 // eigenvectors of the eigenvalues to remove (or to keep) from cross products.
 __device__ void clip_psd3(double h[6]) {
-    const double m2 = h[0] * h[3] - h[1] * h[1];
-    const double det = h[0] * (h[3] * h[5] - h[4] * h[4]) - h[1] * (h[1] * h[5] - h[4] * h[2]) +
-                       h[2] * (h[1] * h[4] - h[3] * h[2]);
+    const double m2 = fma(h[0], h[3], -h[1] * h[1]);
+    const double det = fma(h[0], fma(h[3], h[5], -h[4] * h[4]),
+                           fma(-h[1], fma(h[1], h[5], -h[4] * h[2]), h[2] * fma(h[1], h[4], -h[3] * h[2])));
     if (h[0] > 0.0 && m2 > 0.0 && det > 0.0) return;
-    const double p1 = h[1] * h[1] + h[2] * h[2] + h[4] * h[4];
+    const double p1 = fma(h[1], h[1], fma(h[2], h[2], h[4] * h[4]));
     if (p1 == 0.0) {   // diagonal
         h[0] = fmax(h[0], 0.0);
         h[3] = fmax(h[3], 0.0);
@@ -395,14 +395,14 @@ __device__ void clip_psd3(double h[6]) {
     }
     const double q = (h[0] + h[3] + h[5]) / 3.0;
     const double a0 = h[0] - q, a3 = h[3] - q, a5 = h[5] - q;
-    const double p = sqrt((a0 * a0 + a3 * a3 + a5 * a5 + 2.0 * p1) / 6.0);
+    const double p = sqrt(fma(a0, a0, fma(a3, a3, fma(a5, a5, 2.0 * p1))) / 6.0);
     const double ip = 1.0 / p;
     const double b0 = a0 * ip, b1 = h[1] * ip, b2 = h[2] * ip, b3 = a3 * ip, b4 = h[4] * ip, b5 = a5 * ip;
-    double r = 0.5 * (b0 * (b3 * b5 - b4 * b4) - b1 * (b1 * b5 - b4 * b2) + b2 * (b1 * b4 - b3 * b2));
+    double r = 0.5 * fma(b0, fma(b3, b5, -b4 * b4), fma(-b1, fma(b1, b5, -b4 * b2), b2 * fma(b1, b4, -b3 * b2)));
     r = fmin(fmax(r, -1.0), 1.0);
     const double phi = acos(r) / 3.0;
-    const double lhi = q + 2.0 * p * cos(phi);
-    const double llo = q + 2.0 * p * cos(phi + 2.0943951023931954923);   // + 2 pi / 3
+    const double lhi = fma(2.0 * p, cos(phi), q);
+    const double llo = fma(2.0 * p, cos(phi + 2.0943951023931954923), q);   // + 2 pi / 3
     const double lmid = 3.0 * q - lhi - llo;
     const int neg = (lhi < 0.0) + (lmid < 0.0) + (llo < 0.0);
     if (neg == 0) return;
@@ -416,8 +416,9 @@ __device__ void clip_psd3(double h[6]) {
             clip_psd3_jacobi(h);
             return;
         }
-        h[0] -= llo * v[0] * v[0]; h[1] -= llo * v[0] * v[1]; h[2] -= llo * v[0] * v[2];
-        h[3] -= llo * v[1] * v[1]; h[4] -= llo * v[1] * v[2]; h[5] -= llo * v[2] * v[2];
+        const double s0 = -llo * v[0], s1 = -llo * v[1], s2 = -llo * v[2];
+        h[0] = fma(s0, v[0], h[0]); h[1] = fma(s0, v[1], h[1]); h[2] = fma(s0, v[2], h[2]);
+        h[3] = fma(s1, v[1], h[3]); h[4] = fma(s1, v[2], h[4]); h[5] = fma(s2, v[2], h[5]);
     } else {          // H+ = lhi u u^T
         if (!eigvec3(h, lhi, v)) {
             clip_psd3_jacobi(h);
