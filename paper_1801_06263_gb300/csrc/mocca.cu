@@ -1281,11 +1281,16 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 // the chunk, in the order of bp_pixel_sum.  A ray's record is read from L2 once
 // per tile and view and then from shared memory by every pixel that meets it.
 
-// The pixel of thread `tid` in tile t.
+// The pixel of thread `tid` in tile t: warp w takes a 4 x 8 patch of the 16 x 16
+// tile (four patches across, two down), lane l pixel (l mod 4, l / 4) of it.  A
+// compact patch needs few neighbouring bins in any view, so the lanes' reads of
+// the staged slots at one table row hit few banks (measured: 0.147 ms against
+// 0.160 ms with a warp on two rows of 16, 0.156 ms with 8 x 4 patches).
 __device__ __forceinline__ void bt_pixel(int n, int t, int tid, int& ix, int& iy) {
-    const int ntx = (n + kBTX - 1) / kBTX;
-    ix = (t % ntx) * kBTX + tid % kBTX;
-    iy = (t / ntx) * kBTY + tid / kBTX;
+    static_assert(kBTX == 16 && kBTY == 16, "the warp patches tile 16 x 16");
+    const int ntx = (n + kBTX - 1) / kBTX, w = tid >> 5, l = tid & 31;
+    ix = (t % ntx) * kBTX + (w & 3) * 4 + (l & 3);
+    iy = (t / ntx) * kBTY + (w >> 2) * 8 + (l >> 2);
 }
 
 // The views [u0, u1) of chunk c of group g (views [V0, V1) of the whole range
