@@ -296,11 +296,6 @@ __device__ __forceinline__ dfl df_mulf(dfl x, float y) {
     return df_fast2sum(p.hi, __fmaf_rn(x.lo, y, p.lo));
 }
 
-__device__ __forceinline__ dfl df_of(double a) {
-    const float h = __double2float_rn(a);
-    return {h, __double2float_rn(a - (double)h)};
-}
-
 __device__ __forceinline__ float df_f(dfl x) { return __fadd_rn(x.hi, x.lo); }
 
 // 1 / x: r + r (1 - x r) with r the FP32 reciprocal of x.hi.
@@ -376,22 +371,41 @@ __device__ void clip_psd3_jacobi(double h[6]) {
     }
 }
 
-// Negative-curvature removal H+ = V max(Lambda, 0) V^T.  A positive-definite H
-// (Sylvester's criterion) is returned unchanged.  Otherwise the eigenvalues
-// come from the closed form of Smith (1961) for symmetric 3x3 matrices
-// (trace, deviatoric part, arccos of half the normalised determinant) and the
-// eigenvectors of the eigenvalues to remove (or to keep) from cross products.
-__device__ void clip_psd3(double h[6]) {
+
+// Sum of W double-float terms as a fixed tree: the first four pairwise, then the rest in order.
+template <int W>
+__device__ __forceinline__ dfl df_tree(const dfl (&v)[W]) {
+    dfl acc = df_add(df_add(v[0], v[1]), df_add(v[2], v[3]));
+#pragma unroll
+    for (int w = 4; w < W; ++w) acc = df_add(acc, v[w]);
+    return acc;
+}
+
+// sqrt of a positive double-float: s = sqrt(hi) corrected by one Newton step,
+// s + (x - s^2) / (2 s) (Karp and Markstein 1997), the correction in FP32.
+__device__ __forceinline__ dfl df_sqrt(dfl x) {
+    const float s = __fsqrt_rn(x.hi);
+    const float e = df_f(df_sub(x, df_2prod(s, s)));
+    return df_fast2sum(s, __fmul_rn(e, __fdiv_rn(0.5f, s)));
+}
+
+__device__ __forceinline__ dfl df_neg(dfl x) { return dfl{-x.hi, -x.lo}; }
+
+// Negative-curvature removal of H (FP64, packed) as its terms: returns 0 if H is
+// positive semi-definite (H+ = H), 1 if one eigenvalue is negative (H+ = H - lam
+// v v^T), 2 if two are (H+ = lam v v^T, lam the positive one), 3 if all three are
+// (H+ = 0), and 4 if the closed form met a near repeated root (H+ in h, by Jacobi).
+__device__ int clip_terms(double h[6], double& lam, double v[3]) {
     const double m2 = fma(h[0], h[3], -h[1] * h[1]);
     const double det = fma(h[0], fma(h[3], h[5], -h[4] * h[4]),
                            fma(-h[1], fma(h[1], h[5], -h[4] * h[2]), h[2] * fma(h[1], h[4], -h[3] * h[2])));
-    if (h[0] > 0.0 && m2 > 0.0 && det > 0.0) return;
+    if (h[0] > 0.0 && m2 > 0.0 && det > 0.0) return 0;
     const double p1 = fma(h[1], h[1], fma(h[2], h[2], h[4] * h[4]));
     if (p1 == 0.0) {   // diagonal
         h[0] = fmax(h[0], 0.0);
         h[3] = fmax(h[3], 0.0);
         h[5] = fmax(h[5], 0.0);
-        return;
+        return 4;
     }
     const double q = (h[0] + h[3] + h[5]) / 3.0;
     const double a0 = h[0] - q, a3 = h[3] - q, a5 = h[5] - q;
@@ -405,37 +419,14 @@ __device__ void clip_psd3(double h[6]) {
     const double llo = fma(2.0 * p, cos(phi + 2.0943951023931954923), q);   // + 2 pi / 3
     const double lmid = 3.0 * q - lhi - llo;
     const int neg = (lhi < 0.0) + (lmid < 0.0) + (llo < 0.0);
-    if (neg == 0) return;
-    if (neg == 3) {
-        h[0] = h[1] = h[2] = h[3] = h[4] = h[5] = 0.0;
-        return;
+    if (neg == 0) return 0;
+    if (neg == 3) return 3;
+    lam = neg == 1 ? llo : lhi;
+    if (!eigvec3(h, lam, v)) {
+        clip_psd3_jacobi(h);
+        return 4;
     }
-    double v[3];
-    if (neg == 1) {   // H+ = H - llo v v^T
-        if (!eigvec3(h, llo, v)) {
-            clip_psd3_jacobi(h);
-            return;
-        }
-        const double s0 = -llo * v[0], s1 = -llo * v[1], s2 = -llo * v[2];
-        h[0] = fma(s0, v[0], h[0]); h[1] = fma(s0, v[1], h[1]); h[2] = fma(s0, v[2], h[2]);
-        h[3] = fma(s1, v[1], h[3]); h[4] = fma(s1, v[2], h[4]); h[5] = fma(s2, v[2], h[5]);
-    } else {          // H+ = lhi u u^T
-        if (!eigvec3(h, lhi, v)) {
-            clip_psd3_jacobi(h);
-            return;
-        }
-        h[0] = lhi * v[0] * v[0]; h[1] = lhi * v[0] * v[1]; h[2] = lhi * v[0] * v[2];
-        h[3] = lhi * v[1] * v[1]; h[4] = lhi * v[1] * v[2]; h[5] = lhi * v[2] * v[2];
-    }
-}
-
-// Sum of W double-float terms as a fixed tree: the first four pairwise, then the rest in order.
-template <int W>
-__device__ __forceinline__ dfl df_tree(const dfl (&v)[W]) {
-    dfl acc = df_add(df_add(v[0], v[1]), df_add(v[2], v[3]));
-#pragma unroll
-    for (int w = 4; w < W; ++w) acc = df_add(acc, v[w]);
-    return acc;
+    return neg;
 }
 
 // Dual step of one ray that meets the image (see the file header).
@@ -444,39 +435,31 @@ __device__ __forceinline__ dfl df_tree(const dfl (&v)[W]) {
 //   with beta_i = softexp''_i sum_w r_w s_wi / D_w (FP32, packed), y: dual.
 // With G = (alpha^T alpha)^-1 alpha^T and W = G^T H+ G, the prox
 //   y' = y - Sigma (W + Sigma)^-1 (y - r)
-// equals r + G^T z with (I + H+ F) z = H+ G Sigma^-1 (y - r), F = G Sigma^-1 G^T
-// (push-through identity: the rank-3 update is solved in the 3-dim space of g).
-// Everything is double-float (the Gram matrix alpha^T alpha has a condition
-// number near 1e7): the Hessian H = sum_w c_w alpha_w alpha_w^T - Bt from exact
-// products, its Sylvester test, and the algebra after the clip; only a Hessian
-// that fails the test goes through the FP64 eigen-clip.  Returns y' in yo.
+// is taken in an orthonormal basis of the range of alpha.  With R the Cholesky
+// factor of alpha^T alpha (R^T R = alpha^T alpha, upper triangular) and
+// Q = alpha R^-1 (orthonormal columns), W = Q M Q^T with M = R^-T H+ R^-1, and by
+// the push-through identity y' = r + Q z, (I + M S) z = M Q^T Sigma^-1 (y - r),
+// S = Q^T Sigma^-1 Q.  alpha^T alpha has a condition number near 1e7, so it, R
+// and Q are double-float; the anisotropy of alpha then sits in R, and M =
+// Q^T diag(c) Q - R^-T Bt R^-1 (= R^-T H R^-1), its Sylvester test and the 3x3
+// solve are FP32 (to FP32 accuracy in y' relative to y - r, measured against the
+// FP64 prox).  M has the inertia of H; when its test fails, H is formed in
+// double-float, the FP64 eigen-clip finds its negative part, and M takes the
+// same correction in this basis: M - lam w w^T with w = R^-T v (one negative
+// eigenvalue), lam w w^T (two), 0 (three).  Returns y' in yo; with KEEP the
+// prox's linear map y' = r + Bm (u - r), Bm = Q (I + M S)^-1 M Q^T Sigma^-1.
 template <bool KEEP, int W>
 __device__ void ray_dual(const float (&al)[W][3], const float (&sinv)[W], const float (&cw)[W], const dfl (&r)[W],
                          const float Bt[6], const float (&y)[W], float (&yo)[W], float (&Bm)[W][W]) {
     const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
-    dfl H[6];
+    const int sidx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};   // packed index of (i, j)
+    auto degenerate = [&]() {   // alpha without full rank: no curvature term, y' = r
 #pragma unroll
-    for (int e = 0; e < 6; ++e) {
-        dfl acc = {-Bt[e], 0.0f};
-#pragma unroll
-        for (int w = 0; w < W; ++w) acc = df_add(acc, df_mulf(df_2prod(al[w][ij[e][0]], al[w][ij[e][1]]), cw[w]));
-        H[e] = acc;
-    }
-    {
-        // Sylvester's criterion in double-float; otherwise the FP64 clip
-        const dfl m2 = df_sub(df_mul(H[0], H[3]), df_mul(H[1], H[1]));
-        const dfl det = df_add(df_sub(df_mul(H[0], df_sub(df_mul(H[3], H[5]), df_mul(H[4], H[4]))),
-                                      df_mul(H[1], df_sub(df_mul(H[1], H[5]), df_mul(H[4], H[2])))),
-                               df_mul(H[2], df_sub(df_mul(H[1], H[4]), df_mul(H[3], H[2]))));
-        if (!(H[0].hi > 0.0f && m2.hi > 0.0f && det.hi > 0.0f)) {
-            double Hd[6];
-#pragma unroll
-            for (int e = 0; e < 6; ++e) Hd[e] = (double)H[e].hi + (double)H[e].lo;
-            clip_psd3(Hd);
-#pragma unroll
-            for (int e = 0; e < 6; ++e) H[e] = df_of(Hd[e]);
-        }
-    }
+        for (int w = 0; w < W; ++w) yo[w] = df_f(r[w]);
+        if (KEEP)
+            for (int w = 0; w < W; ++w)
+                for (int j = 0; j < W; ++j) Bm[w][j] = 0.0f;
+    };
     // A = alpha^T alpha (the products of two floats are exact)
     dfl A[6];
 #pragma unroll
@@ -486,105 +469,181 @@ __device__ void ray_dual(const float (&al)[W][3], const float (&sinv)[W], const 
         for (int w = 1; w < W; ++w) acc = df_add(acc, df_2prod(al[w][ij[e][0]], al[w][ij[e][1]]));
         A[e] = acc;
     }
-    // A^-1 by the adjugate
-    dfl Ai[6];
-    {
-        const dfl c00 = df_sub(df_mul(A[3], A[5]), df_mul(A[4], A[4]));
-        const dfl c01 = df_sub(df_mul(A[2], A[4]), df_mul(A[1], A[5]));
-        const dfl c02 = df_sub(df_mul(A[1], A[4]), df_mul(A[2], A[3]));
-        const dfl c11 = df_sub(df_mul(A[0], A[5]), df_mul(A[2], A[2]));
-        const dfl c12 = df_sub(df_mul(A[1], A[2]), df_mul(A[0], A[4]));
-        const dfl c22 = df_sub(df_mul(A[0], A[3]), df_mul(A[1], A[1]));
-        const dfl det = df_add(df_add(df_mul(A[0], c00), df_mul(A[1], c01)), df_mul(A[2], c02));
-        if (!(det.hi != 0.0f) || !isfinite(det.hi)) {   // degenerate alpha: no curvature term, y' = r
-#pragma unroll
-            for (int w = 0; w < W; ++w) yo[w] = df_f(r[w]);
-            if (KEEP)
-                for (int w = 0; w < W; ++w)
-                    for (int j = 0; j < W; ++j) Bm[w][j] = 0.0f;
-            return;
-        }
-        const dfl id = df_rcp(det);
-        Ai[0] = df_mul(c00, id); Ai[1] = df_mul(c01, id); Ai[2] = df_mul(c02, id);
-        Ai[3] = df_mul(c11, id); Ai[4] = df_mul(c12, id); Ai[5] = df_mul(c22, id);
+    // Cholesky A = R^T R; a pivot that is not positive: alpha is degenerate
+    if (!(A[0].hi > 0.0f) || !isfinite(A[0].hi)) {
+        degenerate();
+        return;
     }
-    const int sidx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};   // packed index of (i, j)
-    dfl G[3][W], Gs[3][W];
+    const dfl r00 = df_sqrt(A[0]), i00 = df_rcp(r00);
+    const dfl r01 = df_mul(A[1], i00), r02 = df_mul(A[2], i00);
+    const dfl t11 = df_sub(A[3], df_mul(r01, r01));
+    if (!(t11.hi > 0.0f) || !isfinite(t11.hi)) {
+        degenerate();
+        return;
+    }
+    const dfl r11 = df_sqrt(t11), i11 = df_rcp(r11);
+    const dfl r12 = df_mul(df_sub(A[4], df_mul(r01, r02)), i11);
+    const dfl t22 = df_sub(df_sub(A[5], df_mul(r02, r02)), df_mul(r12, r12));
+    if (!(t22.hi > 0.0f) || !isfinite(t22.hi)) {
+        degenerate();
+        return;
+    }
+    const dfl i22 = df_rcp(df_sqrt(t22));
+    // R^-1 = [[i00, u01, u02], [0, i11, u12], [0, 0, i22]]
+    const dfl u01 = df_neg(df_mul(df_mul(r01, i00), i11));
+    const dfl u12 = df_neg(df_mul(df_mul(r12, i11), i22));
+    const dfl u02 = df_mul(df_sub(df_mul(r01, r12), df_mul(r02, r11)), df_mul(df_mul(i00, i11), i22));
+    const float Ri[3][3] = {{df_f(i00), df_f(u01), df_f(u02)}, {0.0f, df_f(i11), df_f(u12)}, {0.0f, 0.0f, df_f(i22)}};
+    // Q = alpha R^-1, rounded to FP32
+    float q[W][3];
 #pragma unroll
-    for (int m = 0; m < 3; ++m)
+    for (int w = 0; w < W; ++w) {
+        q[w][0] = df_f(df_mulf(i00, al[w][0]));
+        q[w][1] = df_f(df_add(df_mulf(u01, al[w][0]), df_mulf(i11, al[w][1])));
+        q[w][2] = df_f(df_add(df_add(df_mulf(u02, al[w][0]), df_mulf(u12, al[w][1])), df_mulf(i22, al[w][2])));
+    }
+    // M = Q^T diag(c) Q - R^-T Bt R^-1 (FP32, packed)
+    float M[6];
+    {
+        const float Bf[3][3] = {{Bt[0], Bt[1], Bt[2]}, {Bt[1], Bt[3], Bt[4]}, {Bt[2], Bt[4], Bt[5]}};
+        float T[3][3];   // Bt R^-1
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            G[m][w] = df_add(df_add(df_mulf(Ai[sidx[m][0]], al[w][0]), df_mulf(Ai[sidx[m][1]], al[w][1])),
-                             df_mulf(Ai[sidx[m][2]], al[w][2]));
-            Gs[m][w] = df_mulf(G[m][w], sinv[w]);
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                float t = 0.0f;
+#pragma unroll
+                for (int k = 0; k <= j; ++k) t = fmaf(Bf[i][k], Ri[k][j], t);
+                T[i][j] = t;
+            }
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+            const int a = ij[e][0], b = ij[e][1];
+            float qcq = 0.0f, rbr = 0.0f;
+#pragma unroll
+            for (int w = 0; w < W; ++w) qcq = fmaf(__fmul_rn(cw[w], q[w][a]), q[w][b], qcq);
+#pragma unroll
+            for (int k = 0; k <= a; ++k) rbr = fmaf(Ri[k][a], T[k][b], rbr);
+            M[e] = __fsub_rn(qcq, rbr);
         }
-    dfl d[W];
+    }
+    {
+        // Sylvester's criterion on M; otherwise the negative part of H in FP64
+        const float m2 = fmaf(M[0], M[3], -__fmul_rn(M[1], M[1]));
+        const float det = fmaf(M[0], fmaf(M[3], M[5], -__fmul_rn(M[4], M[4])),
+                               fmaf(-M[1], fmaf(M[1], M[5], -__fmul_rn(M[4], M[2])),
+                                    __fmul_rn(M[2], fmaf(M[1], M[4], -__fmul_rn(M[3], M[2])))));
+        if (!(M[0] > 0.0f && m2 > 0.0f && det > 0.0f)) {
+            // H = sum_w c_w alpha_w alpha_w^T - Bt from exact products, in double-float
+            double Hd[6];
 #pragma unroll
-    for (int w = 0; w < W; ++w) d[w] = df_sub(dfl{y[w], 0.0f}, r[w]);
-    dfl F[6], phi[3];
+            for (int e = 0; e < 6; ++e) {
+                dfl acc = {-Bt[e], 0.0f};
+#pragma unroll
+                for (int w = 0; w < W; ++w)
+                    acc = df_add(acc, df_mulf(df_2prod(al[w][ij[e][0]], al[w][ij[e][1]]), cw[w]));
+                Hd[e] = (double)acc.hi + (double)acc.lo;
+            }
+            double lam = 0.0, v[3] = {0.0, 0.0, 0.0};
+            const int kind = clip_terms(Hd, lam, v);
+            if (kind == 1 || kind == 2) {   // w = R^-T v; M - lam w w^T, or lam w w^T
+                float wv[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    float t = 0.0f;
+#pragma unroll
+                    for (int k = 0; k <= a; ++k) t = fmaf(Ri[k][a], (float)v[k], t);
+                    wv[a] = t;
+                }
+                const float lf = (float)lam;
+#pragma unroll
+                for (int e = 0; e < 6; ++e) {
+                    const float t = __fmul_rn(__fmul_rn(lf, wv[ij[e][0]]), wv[ij[e][1]]);
+                    M[e] = kind == 1 ? __fsub_rn(M[e], t) : t;
+                }
+            } else if (kind == 3) {
+#pragma unroll
+                for (int e = 0; e < 6; ++e) M[e] = 0.0f;
+            } else if (kind == 4) {   // H+ itself (diagonal H or the Jacobi fallback): M = R^-T H+ R^-1 in FP64
+                const double Rd[3][3] = {{(double)i00.hi + i00.lo, (double)u01.hi + u01.lo, (double)u02.hi + u02.lo},
+                                         {0.0, (double)i11.hi + i11.lo, (double)u12.hi + u12.lo},
+                                         {0.0, 0.0, (double)i22.hi + i22.lo}};
+                double Td[3][3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        double t = 0.0;
+#pragma unroll
+                        for (int k = 0; k <= j; ++k) t = fma(Hd[sidx[i][k]], Rd[k][j], t);
+                        Td[i][j] = t;
+                    }
+#pragma unroll
+                for (int e = 0; e < 6; ++e) {
+                    double t = 0.0;
+#pragma unroll
+                    for (int k = 0; k <= ij[e][0]; ++k) t = fma(Rd[k][ij[e][0]], Td[k][ij[e][1]], t);
+                    M[e] = (float)t;
+                }
+            }
+        }
+    }
+    // S = Q^T Sigma^-1 Q, phi = Q^T Sigma^-1 (y - r)
+    float S[6], phi[3] = {0.0f, 0.0f, 0.0f}, sd[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) sd[w] = __fmul_rn(sinv[w], df_f(df_sub(dfl{y[w], 0.0f}, r[w])));
 #pragma unroll
     for (int e = 0; e < 6; ++e) {
-        const int m = ij[e][0], n = ij[e][1];
-        dfl t[W];
+        float t = 0.0f;
 #pragma unroll
-        for (int w = 0; w < W; ++w) t[w] = df_mul(Gs[m][w], G[n][w]);
-        F[e] = df_tree(t);
+        for (int w = 0; w < W; ++w) t = fmaf(__fmul_rn(sinv[w], q[w][ij[e][0]]), q[w][ij[e][1]], t);
+        S[e] = t;
     }
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        dfl t[W];
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int w = 0; w < W; ++w) t[w] = df_mul(Gs[m][w], d[w]);
-        phi[m] = df_tree(t);
-    }
-    // Mx = I + H+ F (3 x 3), rhs = H+ phi
-    dfl Mx[3][3], rhs[3];
+        for (int w = 0; w < W; ++w) phi[a] = fmaf(q[w][a], sd[w], phi[a]);
+    // Mx = I + M S, rhs = M phi; z = Mx^-1 rhs by the adjugate (C[i][j] the cofactor of Mx[j][i])
+    float Mx[3][3], rhs[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            dfl acc = df_add(df_add(df_mul(H[sidx[i][0]], F[sidx[0][j]]), df_mul(H[sidx[i][1]], F[sidx[1][j]])),
-                             df_mul(H[sidx[i][2]], F[sidx[2][j]]));
-            if (i == j) acc = df_add(acc, dfl{1.0f, 0.0f});
-            Mx[i][j] = acc;
-        }
-        rhs[i] = df_add(df_add(df_mul(H[sidx[i][0]], phi[0]), df_mul(H[sidx[i][1]], phi[1])),
-                        df_mul(H[sidx[i][2]], phi[2]));
+        for (int j = 0; j < 3; ++j)
+            Mx[i][j] = fmaf(M[sidx[i][2]], S[sidx[2][j]],
+                            fmaf(M[sidx[i][1]], S[sidx[1][j]], fmaf(M[sidx[i][0]], S[sidx[0][j]], i == j ? 1.0f : 0.0f)));
+        rhs[i] = fmaf(M[sidx[i][2]], phi[2], fmaf(M[sidx[i][1]], phi[1], __fmul_rn(M[sidx[i][0]], phi[0])));
     }
-    // z = Mx^-1 rhs (adjugate; the eigenvalues of Mx are >= 1).  C[i][j] is the
-    // cofactor of Mx[j][i]; cyclic indices carry the signs.
-    dfl C[3][3];
+    float C[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int r0 = (j + 1) % 3, r1 = (j + 2) % 3, c0 = (i + 1) % 3, c1 = (i + 2) % 3;
-            C[i][j] = df_sub(df_mul(Mx[r0][c0], Mx[r1][c1]), df_mul(Mx[r0][c1], Mx[r1][c0]));
+            C[i][j] = fmaf(Mx[r0][c0], Mx[r1][c1], -__fmul_rn(Mx[r0][c1], Mx[r1][c0]));
         }
-    const dfl idet =
-        df_rcp(df_add(df_add(df_mul(Mx[0][0], C[0][0]), df_mul(Mx[0][1], C[1][0])), df_mul(Mx[0][2], C[2][0])));
-    dfl z[3];
+    const float idet =
+        __frcp_rn(fmaf(Mx[0][2], C[2][0], fmaf(Mx[0][1], C[1][0], __fmul_rn(Mx[0][0], C[0][0]))));
+    float z[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-        z[i] = df_mul(idet, df_add(df_add(df_mul(C[i][0], rhs[0]), df_mul(C[i][1], rhs[1])), df_mul(C[i][2], rhs[2])));
+        z[i] = __fmul_rn(idet, fmaf(C[i][2], rhs[2], fmaf(C[i][1], rhs[1], __fmul_rn(C[i][0], rhs[0]))));
+    // y' = r + Q z
 #pragma unroll
     for (int w = 0; w < W; ++w)
-        yo[w] = df_f(df_add(r[w], df_add(df_add(df_mul(G[0][w], z[0]), df_mul(G[1][w], z[1])), df_mul(G[2][w], z[2]))));
+        yo[w] = df_f(df_add(r[w], dfl{fmaf(q[w][2], z[2], fmaf(q[w][1], z[1], __fmul_rn(q[w][0], z[0]))), 0.0f}));
     if (KEEP) {
-        // the linear map of the prox: y' = r + B (u - r), column j from the same solve with
-        // Sigma^-1 e_j in place of Sigma^-1 (y - r), i.e. right-hand side H+ Gs[:, j]
+        // column j of the prox map: Q Mx^-1 M q_j sinv_j
         for (int j = 0; j < W; ++j) {
-            dfl q[3], zj[3];
+            float mq[3], u[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i)
-                q[i] = df_add(df_add(df_mul(H[sidx[i][0]], Gs[0][j]), df_mul(H[sidx[i][1]], Gs[1][j])),
-                              df_mul(H[sidx[i][2]], Gs[2][j]));
+                mq[i] = fmaf(M[sidx[i][2]], q[j][2], fmaf(M[sidx[i][1]], q[j][1], __fmul_rn(M[sidx[i][0]], q[j][0])));
 #pragma unroll
             for (int i = 0; i < 3; ++i)
-                zj[i] = df_mul(idet, df_add(df_add(df_mul(C[i][0], q[0]), df_mul(C[i][1], q[1])), df_mul(C[i][2], q[2])));
+                u[i] = __fmul_rn(idet, fmaf(C[i][2], mq[2], fmaf(C[i][1], mq[1], __fmul_rn(C[i][0], mq[0]))));
 #pragma unroll
             for (int w = 0; w < W; ++w)
-                Bm[w][j] = df_f(df_add(df_add(df_mul(G[0][w], zj[0]), df_mul(G[1][w], zj[1])), df_mul(G[2][w], zj[2])));
+                Bm[w][j] = __fmul_rn(sinv[j], fmaf(q[w][2], u[2], fmaf(q[w][1], u[1], __fmul_rn(q[w][0], u[0]))));
         }
     }
 }
