@@ -6,11 +6,12 @@
 //   k_mocca_ray (per ray):      the counts model
 //       of Eq. (finalModel) summed over energies (compensated), D_TPL of
 //       Eq. (DTPL), alpha_w = sum_i A_wi mu_i (K = alpha X, Eq. aeq), the per-ray
-//       Hessian of Sec. 2 in g (double-float) with its negative eigenvalues
-//       removed (FP64, for the Hessians that are not positive definite),
-//       the dual step matrix Sigma^-1 = lambda |alpha_w| (X 1)_l, the exact
-//       preconditioned dual prox y' = y - Sigma (W + Sigma)^-1 (y - r), and the
-//       per-ray products b = alpha^T y' and S = sum_w alpha_w alpha_w^T / |alpha_w|.
+//       Hessian of Sec. 2 in g with its negative eigenvalues removed (FP64, for
+//       the Hessians that are not positive definite), the dual step matrix
+//       Sigma^-1 = lambda |alpha_w| (X 1)_l, the exact preconditioned dual prox
+//       y' = y - Sigma (W + Sigma)^-1 (y - r) (taken in an orthonormal basis of
+//       the range of alpha, see ray_dual), and the per-ray products b = alpha^T y'
+//       and S = sum_w alpha_w alpha_w^T / |alpha_w|.
 //   k_mocca_bp (pixel-driven):  v_k = sum_l X_lk b_l (= K^T y') and
 //       P_k = sum_l X_lk S_l (so T^-1_k = P_k / lambda, the m-block SPC), the
 //       3x3 solve (double-float), the primal step (optionally onto a box) and the
@@ -250,8 +251,9 @@ __global__ void __launch_bounds__(kFwdThreads) k_counts(GeomC C, ExcTable E, con
 //
 // A value is the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi) / 2),
 // about 48 significant bits, computed on the FP32 pipe: on this GPU the FP64
-// pipe runs at 1/64 of the FP32 rate, so for the dual algebra (after the FP64
-// eigen-clip) two-float arithmetic is several times cheaper than FP64.  The
+// pipe runs at 1/64 of the FP32 rate, so for the ill-conditioned parts of the
+// dual step and for the pixel step two-float arithmetic is several times
+// cheaper than FP64.  The
 // error-free transformations are Knuth's TwoSum and Dekker's exact product in
 // its FMA form (Dekker 1971); additions are the accurate ("IEEE-style")
 // double-word sum of Hida, Li and Bailey (2001), which keeps its accuracy under
@@ -371,15 +373,6 @@ __device__ void clip_psd3_jacobi(double h[6]) {
     }
 }
 
-
-// Sum of W double-float terms as a fixed tree: the first four pairwise, then the rest in order.
-template <int W>
-__device__ __forceinline__ dfl df_tree(const dfl (&v)[W]) {
-    dfl acc = df_add(df_add(v[0], v[1]), df_add(v[2], v[3]));
-#pragma unroll
-    for (int w = 4; w < W; ++w) acc = df_add(acc, v[w]);
-    return acc;
-}
 
 // sqrt of a positive double-float: s = sqrt(hi) corrected by one Newton step,
 // s + (x - s^2) / (2 s) (Karp and Markstein 1997), the correction in FP32.
