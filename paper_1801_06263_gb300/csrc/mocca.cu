@@ -400,6 +400,31 @@ __device__ int clip_terms(double h[6], double& lam, double v[3]) {
         h[5] = fmax(h[5], 0.0);
         return 4;
     }
+    // One negative eigenvalue (det < 0 with a positive diagonal entry, so not all
+    // three are negative), the common case: the eigenvalue by Newton steps on the
+    // characteristic polynomial p(l) = det(H - l I) = -l^3 + tr l^2 - c2 l + det from
+    // l = det / c2 (the eigenvalue itself when it is small against the others).
+    // p and p' are FP64 and each step's ratio p / p' FP32, so the iterates settle on
+    // the FP64 zero of p; if they do not within eight steps, the closed form below.
+    if (det < 0.0 && (h[0] > 0.0 || h[3] > 0.0 || h[5] > 0.0)) {
+        const double tr = h[0] + h[3] + h[5];
+        const double c2 = fma(h[0], h[3], -h[1] * h[1]) + fma(h[0], h[5], -h[2] * h[2]) + fma(h[3], h[5], -h[4] * h[4]);
+        if (c2 > 0.0) {
+            double l = (double)__fdiv_rn((float)det, (float)c2);
+            bool settled = false;
+            for (int it = 0; it < 8 && !settled; ++it) {
+                const double p = fma(fma(tr - l, l, -c2), l, det);
+                const double dp = fma(fma(-3.0, l, 2.0 * tr), l, -c2);
+                const double step = (double)__fdiv_rn((float)p, (float)dp);
+                l -= step;
+                settled = fabs(step) <= 1e-14 * fabs(l);
+            }
+            if (settled && l < 0.0) {
+                lam = l;
+                if (eigvec3(h, lam, v)) return 1;
+            }
+        }
+    }
     const double q = (h[0] + h[3] + h[5]) / 3.0;
     const double a0 = h[0] - q, a3 = h[3] - q, a5 = h[5] - q;
     const double p = sqrt(fma(a0, a0, fma(a3, a3, fma(a5, a5, 2.0 * p1))) / 6.0);
