@@ -73,15 +73,15 @@ FP32_LANES_PER_SM, SCHEDULERS_PER_SM, L1_BYTES_PER_CLK_PER_SM, L1_WAVEFRONTS_PER
 # elapsed SM cycles x the capturing GPU's SMs).  Valid only for that workload and for
 # the kernel sources they were taken on (source_sha, see _source_sha).
 NCU_WORKLOAD = "medium_256"
-_SHA = "395a4fb9cfb91ad3"
+_SHA = "2e6e06f04db8c615"
 NCU_COUNTS = {
-    "k_fp_proj": {"dram_bytes": 363467264 + 4165888, "warp_instructions": 41112016,
-                  "l1_wavefronts": 23240965, "source_sha": _SHA},
-    "k_mocca_ray": {"dram_bytes": 23001344 + 512, "warp_instructions": 113891715,
-                    "l1_wavefronts": 8227755, "source_sha": _SHA},
+    "k_fp_proj": {"dram_bytes": 363470336 + 4178432, "warp_instructions": 41112016,
+                  "l1_wavefronts": 23246808, "source_sha": _SHA},
+    "k_mocca_ray": {"dram_bytes": 23114752 + 879872, "warp_instructions": 93367586,
+                    "l1_wavefronts": 8978243, "source_sha": _SHA},
     # the back-projection's two launches: k_fpb_bp and k_fpb_finish
-    "k_fpb_bp": {"dram_bytes": 452405248 + 19105280 + 19977984, "warp_instructions": 72114720 + 1998848,
-                 "l1_wavefronts": 26930805 + 264248, "source_sha": _SHA},
+    "k_fpb_bp": {"dram_bytes": 452335872 + 19086336 + 19977984, "warp_instructions": 72114720 + 1998848,
+                 "l1_wavefronts": 26926376 + 264387, "source_sha": _SHA},
 }
 
 
