@@ -855,10 +855,11 @@ __device__ __forceinline__ double ray_step(const GeomC& C, RayRec* rec, const Sp
     return dsum;
 }
 
-// Five resident blocks of 128 threads for four windows (96 registers, a few
-// spills): 0.137 ms at 256x256 against 0.144 ms with four and 0.160 ms with six.
+// Resident blocks of 128 threads: five for four windows (96 registers, a few
+// spills; 0.137 ms at 256x256 against 0.144 ms with four and 0.160 ms with six),
+// four for five windows (128 registers; 0.136 ms against 0.152 ms with three).
 template <bool KEEP, int W>
-__global__ void __launch_bounds__(kFwdThreads, W == 4 ? 5 : 3) k_mocca_ray(GeomC C, RayRec* rec, SpecD S,
+__global__ void __launch_bounds__(kFwdThreads, W == 4 ? 5 : 4) k_mocca_ray(GeomC C, RayRec* rec, SpecD S,
                                                                          StepParams P, SolveD D, int v0, int v1) {
     __shared__ float sm[kSmemStride * kMaxEnergies];
     load_mu_smem(S, sm);
