@@ -73,15 +73,15 @@ FP32_LANES_PER_SM, SCHEDULERS_PER_SM, L1_BYTES_PER_CLK_PER_SM, L1_WAVEFRONTS_PER
 # elapsed SM cycles x the capturing GPU's SMs).  Valid only for that workload and for
 # the kernel sources they were taken on (source_sha, see _source_sha).
 NCU_WORKLOAD = "medium_256"
-_SHA = "2e6e06f04db8c615"
+_SHA = "6ba4d0159ed563d2"
 NCU_COUNTS = {
-    "k_fp_proj": {"dram_bytes": 363470336 + 4178432, "warp_instructions": 41112016,
-                  "l1_wavefronts": 23246808, "source_sha": _SHA},
-    "k_mocca_ray": {"dram_bytes": 23114752 + 879872, "warp_instructions": 93367586,
-                    "l1_wavefronts": 8978243, "source_sha": _SHA},
+    "k_fp_proj": {"dram_bytes": 363443456 + 3909120, "warp_instructions": 41112016,
+                  "l1_wavefronts": 23233377, "source_sha": _SHA},
+    "k_mocca_ray": {"dram_bytes": 23127808 + 950784, "warp_instructions": 93367586,
+                    "l1_wavefronts": 8978432, "source_sha": _SHA},
     # the back-projection's two launches: k_fpb_bp and k_fpb_finish
-    "k_fpb_bp": {"dram_bytes": 452335872 + 19086336 + 19977984, "warp_instructions": 72114720 + 1998848,
-                 "l1_wavefronts": 26926376 + 264387, "source_sha": _SHA},
+    "k_fpb_bp": {"dram_bytes": 452327936 + 19131392 + 19977984, "warp_instructions": 72114720 + 1998848,
+                 "l1_wavefronts": 26935109 + 264333, "source_sha": _SHA},
 }
 
 
