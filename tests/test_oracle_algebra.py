@@ -145,3 +145,29 @@ def test_primal_step_box_matches_bounded_qp(orc, seed, box):
     assert (got >= lo).all() and (got <= hi).all()
     assert obj(got) <= obj(res.x) + 1e-10
     np.testing.assert_allclose(got, res.x, atol=1e-5)
+
+
+@pytest.mark.parametrize("nw", [4, 5])
+@pytest.mark.parametrize("seed", range(4))
+def test_dual_step_in_an_orthonormal_basis_of_alpha(orc, seed, nw):
+    """The identity the GPU's dual step is built on: with R the Cholesky factor of
+    alpha^T alpha and Q = alpha R^-1, W = G^T H+ G = Q M Q^T with M = R^-T H+ R^-1,
+    and the prox y' = y - Sigma (W + Sigma)^-1 (y - r) equals r + Q z with
+    (I + M S) z = M Q^T Sigma^-1 (y - r), S = Q^T Sigma^-1 Q.  Written out here in
+    FP64 and compared with the oracle's prox."""
+    rng = np.random.default_rng(40 + seed)
+    alpha, H, r, sinv, y = _ray(rng, nw)
+    Hp = orc.clip_psd3(H)
+    R = np.linalg.cholesky(alpha.T @ alpha).T
+    Q = alpha @ np.linalg.inv(R)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(3), atol=1e-12)
+    M = np.linalg.inv(R).T @ Hp @ np.linalg.inv(R)
+    S = (Q.T * sinv) @ Q
+    z = np.linalg.solve(np.eye(3) + M @ S, M @ (Q.T @ (sinv * (y - r))))
+    want = orc.dual_update(alpha, Hp, r, sinv, y)
+    # both sides are FP64 on a problem with cond(alpha^T alpha) up to ~1e7 (these alpha
+    # scales): they agree to a few 1e-9 relative, the conditioning's share of FP64
+    np.testing.assert_allclose(r + Q @ z, want, rtol=0, atol=1e-8 * np.abs(want).max())
+    # M has the inertia of H (Sylvester's law), so a test on M picks the Hessians to clip
+    M0 = np.linalg.inv(R).T @ H @ np.linalg.inv(R)
+    assert (np.linalg.eigvalsh(M0) < 0).sum() == (np.linalg.eigvalsh(H) < 0).sum()
