@@ -1222,23 +1222,28 @@ __global__ void __launch_bounds__(kFwdThreads) k_fp_fwd_count(GeomC C, ExcTable 
 
 // Forward table, pass 2: lane r of warp w writes its j-th pair (weight, pixel
 // step) in visiting order, two per slot row from fwd_row[w] (see FpTables).
-// The pixels index the xbar copy in which the warp's gathers are close: when
-// most of its rays run along x, neighbouring lanes sit in neighbouring rows of
-// one column, so the column-major copy (P + ix n + iy); else the row-major one.
+// Each ray's pixels index the xbar copy in which the warp's gathers at one
+// table row are close.  The lanes advance from their first pixels at about the
+// same pace along the slabs, so what matters is the image edge a ray enters
+// by: lanes whose rays enter through a left or right edge start in one column
+// and stay in neighbouring rows of a column (the column-major copy,
+// P + ix n + iy); lanes whose rays enter through the bottom or top edge stay in
+// neighbouring columns of a row (the row-major copy).  A lane chooses from its
+// own first pixel: 7.8 distinct 128-byte lines per warp gather at 256x256,
+// against 12.0 when the warp chose by the rays' direction.
 __global__ void __launch_bounds__(kFwdThreads) k_fp_fwd_fill(GeomC C, ExcTable E, const RayRec* rec,
                                                              const uint32_t* __restrict__ fwd_row, float* fwd_w,
                                                              int16_t* fwd_d, int* fwd_k0, int* bad) {
     const int l = ray_of_thread(C);
-    const bool along_x = l >= 0 && !ray_rows(rec[l].r0);
-    const unsigned vote = __ballot_sync(0xffffffffu, along_x), live = __ballot_sync(0xffffffffu, l >= 0);
-    const bool col = 2 * __popc(vote) > __popc(live);
     if (l < 0) return;
     const int v = warp_view(blockIdx.y, kFwdThreads / 32);
     const size_t row = fwd_row[v * ((C.n_bins + 31) >> 5) + blockIdx.x];
     const int lane = threadIdx.x & 31, n = C.grid.n;
     const float4 r0 = rec[l].r0, r1 = rec[l].r1;
     int j = 0, prev = -1;
+    bool col = false;
     ray_pixels(C, E, r0, r1.x, r1.y, l, [&](int kr, float w) {
+        if (j == 0) col = kr % n == 0 || kr % n == n - 1;   // entered through a left or right edge
         const int k = col ? n * n + (kr % n) * n + kr / n : kr;
         const size_t at = (row + (j & ~1)) * 32 + 2 * lane + (j & 1);
         if (j == 0) {
