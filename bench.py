@@ -73,10 +73,10 @@ FP32_LANES_PER_SM, SCHEDULERS_PER_SM, L1_BYTES_PER_CLK_PER_SM, L1_WAVEFRONTS_PER
 # elapsed SM cycles x the capturing GPU's SMs).  Valid only for that workload and for
 # the kernel sources they were taken on (source_sha, see _source_sha).
 NCU_WORKLOAD = "medium_256"
-_SHA = "6ba4d0159ed563d2"
+_SHA = "3ce579787f18c241"
 NCU_COUNTS = {
-    "k_fp_proj": {"dram_bytes": 363443456 + 3909120, "warp_instructions": 41112016,
-                  "l1_wavefronts": 23233377, "source_sha": _SHA},
+    "k_fp_proj": {"dram_bytes": 363268352 + 4157184, "warp_instructions": 41112016,
+                  "l1_wavefronts": 16529747, "source_sha": _SHA},
     "k_mocca_ray": {"dram_bytes": 23127808 + 950784, "warp_instructions": 93367586,
                     "l1_wavefronts": 8978432, "source_sha": _SHA},
     # the back-projection's two launches: k_fpb_bp and k_fpb_finish
