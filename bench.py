@@ -73,15 +73,15 @@ FP32_LANES_PER_SM, SCHEDULERS_PER_SM, L1_BYTES_PER_CLK_PER_SM, L1_WAVEFRONTS_PER
 # elapsed SM cycles x the capturing GPU's SMs).  Valid only for that workload and for
 # the kernel sources they were taken on (source_sha, see _source_sha).
 NCU_WORKLOAD = "medium_256"
-_SHA = "3ce579787f18c241"
+_SHA = "ab1e85b192311d41"
 NCU_COUNTS = {
-    "k_fp_proj": {"dram_bytes": 363268352 + 4157184, "warp_instructions": 41112016,
-                  "l1_wavefronts": 16529747, "source_sha": _SHA},
-    "k_mocca_ray": {"dram_bytes": 23127808 + 950784, "warp_instructions": 93367586,
-                    "l1_wavefronts": 8978432, "source_sha": _SHA},
+    "k_fp_proj": {"dram_bytes": 363292416 + 4130560, "warp_instructions": 41112016,
+                  "l1_wavefronts": 16524601, "source_sha": _SHA},
+    "k_mocca_ray": {"dram_bytes": 23128576 + 858368, "warp_instructions": 93367586,
+                    "l1_wavefronts": 8977299, "source_sha": _SHA},
     # the back-projection's two launches: k_fpb_bp and k_fpb_finish
-    "k_fpb_bp": {"dram_bytes": 452327936 + 19131392 + 19977984, "warp_instructions": 72114720 + 1998848,
-                 "l1_wavefronts": 26935109 + 264333, "source_sha": _SHA},
+    "k_fpb_bp": {"dram_bytes": 436270336 + 4501248 + 19977984, "warp_instructions": 68896272 + 1998848,
+                 "l1_wavefronts": 26932941 + 264392, "source_sha": _SHA},
 }
 
 
