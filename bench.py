@@ -603,6 +603,24 @@ def run_batched(args, rank):
     table_bytes = sum(_lib.osscir_memory(R.handle)[1] for R in recs)
     alg_bytes = 48.0 * P + 124.0 * L + table_bytes
     best_ms = min(default_ms, tuned_ms)
+    # per kernel of the default configuration (one branch: one launch per kernel for all
+    # solves), the algorithmic bytes of the plain path's table kernels summed over the
+    # solves: forward 6 B per footprint pair + 16 B per pixel + 24 B per ray; back-projection
+    # 6 B per pair + 72 B per pixel and view group + 64 B per pixel
+    from paper_1801_06263_gb300 import osscir_footprint_rays
+    fwd_bytes = bp_bytes = 0.0
+    for R, w in zip(recs, ws):
+        cnt = torch.zeros(w.geom.n_rays, dtype=torch.int32, device="cuda")
+        osscir_footprint_rays(R.handle, 0, w.geom.n_rays, 0, cnt, None, None)
+        nnz = float(cnt.sum().item())
+        Ps, Ls = w.geom.n_pixels, w.geom.n_rays
+        fwd_bytes += 6.0 * nnz + 16.0 * Ps + 24.0 * Ls
+        bp_bytes += 6.0 * nnz + 72.0 * bp_view_groups(Ps, w.geom.n_views) * Ps + 64.0 * Ps
+    per_kernel = {}
+    for name, ms, nbytes in (("proj", kms_default[0], fwd_bytes), ("bp", kms_default[2], bp_bytes)):
+        gbps = nbytes / (ms * 1e-3) / 1e9
+        per_kernel[name] = {"ms": ms, "algorithmic_bytes": nbytes, "achieved_GBps": gbps,
+                            "hbm_frac": gbps / HBM_PEAK_GBPS}
     for R in recs:
         R.close()
     mix = {}
@@ -620,7 +638,7 @@ def run_batched(args, rank):
         "hbm": {"algorithmic_bytes_per_iteration": alg_bytes, "footprint_table_bytes": table_bytes,
                 "achieved_GBps": alg_bytes / (best_ms * 1e-3) / 1e9,
                 "peak_GBps": HBM_PEAK_GBPS, "frac": alg_bytes / (best_ms * 1e-3) / 1e9 / HBM_PEAK_GBPS,
-                "peak_source": HBM_PEAK_SOURCE},
+                "peak_source": HBM_PEAK_SOURCE, "projector_kernels_default_config": per_kernel},
     }
 
 
