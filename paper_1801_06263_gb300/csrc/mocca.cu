@@ -115,9 +115,9 @@ __device__ __forceinline__ void sexp3(float x, bool expm, float& e0, float& e1, 
 }
 
 // Back-projection table entries are read once per iteration: streaming loads
-// that allocate no L1 line (0.147 -> 0.145 ms at 256x256, 1.026 -> 1.018 ms at
-// 512x512; the forward table's entries loaded so were slower, 0.108 -> 0.120 ms,
-// and keep ordinary loads).
+// that allocate no L1 line (measured about 2 % faster at 256x256 and 1 % at
+// 512x512; the forward table's entries loaded so were 10 % slower and keep
+// ordinary loads).
 __device__ __forceinline__ float2 ld_stream(const float2* p) {
     float2 v;
     asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
