@@ -73,15 +73,15 @@ FP32_LANES_PER_SM, SCHEDULERS_PER_SM, L1_BYTES_PER_CLK_PER_SM, L1_WAVEFRONTS_PER
 # elapsed SM cycles x the capturing GPU's SMs).  Valid only for that workload and for
 # the kernel sources they were taken on (source_sha, see _source_sha).
 NCU_WORKLOAD = "medium_256"
-_SHA = "ab1e85b192311d41"
+_SHA = "b6ce277f6d9a2514"
 NCU_COUNTS = {
-    "k_fp_proj": {"dram_bytes": 363292416 + 4130560, "warp_instructions": 41112016,
-                  "l1_wavefronts": 16524601, "source_sha": _SHA},
-    "k_mocca_ray": {"dram_bytes": 23128576 + 858368, "warp_instructions": 93367586,
-                    "l1_wavefronts": 8977299, "source_sha": _SHA},
+    "k_fp_proj": {"dram_bytes": 363276544 + 4203520, "warp_instructions": 41112016,
+                  "l1_wavefronts": 16519622, "source_sha": _SHA},
+    "k_mocca_ray": {"dram_bytes": 23119360 + 892672, "warp_instructions": 93367586,
+                    "l1_wavefronts": 8975038, "source_sha": _SHA},
     # the back-projection's two launches: k_fpb_bp and k_fpb_finish
-    "k_fpb_bp": {"dram_bytes": 436270336 + 4501248 + 19977984, "warp_instructions": 68896272 + 1998848,
-                 "l1_wavefronts": 26932941 + 264392, "source_sha": _SHA},
+    "k_fpb_bp": {"dram_bytes": 436254720 + 4344320 + 19977984, "warp_instructions": 68896272 + 1998848,
+                 "l1_wavefronts": 26924140 + 264357, "source_sha": _SHA},
 }
 
 
@@ -361,6 +361,7 @@ def run_gpu(args):
 
     nested = run_nested(args, w, c) if args.nested else None
     five = run_five_windows(args, w, f4, rank) if args.five_windows > 0 else None
+    vsplit = run_view_split(args, w, c, 1e3 * total_s / args.steps) if args.split else None
     served = run_served(args, w, R, chat, rank) if args.served > 0 else None
     batched = run_batched(args, rank) if args.batch > 0 else None
     mixed = run_served_mixed(args, rank) if args.mixed > 0 else None
@@ -471,6 +472,7 @@ def run_gpu(args):
                 "recon_per_s": e2e_rate / SOLVE_ITERS},
         "plain_recon_per_s": e2e_rate / SOLVE_ITERS,
         "nested": nested,
+        "view_split": vsplit,
         "five_windows": five,
         "served": served,
         "batched": batched,
@@ -513,6 +515,81 @@ def run_nested(args, w, c):
         R.close()
         out[str(k)] = {"ms_per_iteration": ms / done, "trajectory": rows}
     return out
+
+
+def run_view_split(args, w, c, serial_ms):
+    """One solve split by views over N ranks (osscir_mocca_partial per rank's views,
+    the channels summed, osscir_mocca_apply): the rank-local work measured on this
+    one GPU.  Each rank's share and the sum with the primal step are captured as
+    CUDA graphs (so host launch latency does not stand in for device time) and
+    replayed in turn each iteration, so the solve follows the split iteration
+    exactly; CUDA events around each replay.  The sum of the ranks' channels
+    stands in for the all-reduce of 9 P floats, which N GPUs would add (not
+    measured: one GPU here).  L2 is flushed before each iteration;
+    vs_single_graph divides the headline's per-iteration time (also L2-flushed)
+    by the largest rank share plus the primal step."""
+    import statistics
+    import torch
+    from paper_1801_06263_gb300 import Reconstructor, _lib
+    from paper_1801_06263_gb300.split import view_range
+
+    stream = torch.cuda.current_stream()
+    P, V = w.geom.n_pixels, w.geom.n_views
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for N in args.split:
+        R = Reconstructor(w.geom, w.spectra, LAMBDA)
+        R.set_counts(c)
+        ranges = [view_range(V, r, N) for r in range(N)]
+        chans = [torch.zeros((9, P), dtype=torch.float32, device="cuda") for _ in range(N)]
+        total = torch.zeros((9, P), dtype=torch.float32, device="cuda")
+
+        def share(r):
+            _lib.osscir_mocca_partial(R.handle, ranges[r][0], ranges[r][1], chans[r])
+
+        def combine():
+            total.copy_(chans[0])
+            for ch in chans[1:]:
+                total.add_(ch)
+            _lib.osscir_mocca_apply(R.handle, total)
+
+        for _ in range(3):   # eager warm-up: builds the tables
+            for r in range(N):
+                share(r)
+            combine()
+        torch.cuda.synchronize()
+        graphs = []
+        for fn in [lambda r=r: share(r) for r in range(N)] + [combine]:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                fn()
+            graphs.append(g)
+        part_ms, apply_ms = [[] for _ in range(N)], []
+        for it in range(2 + args.split_steps):
+            flush.fill_(it & 0xFF)   # L2 flushed before each iteration, as for the headline steps
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(N + 1)]
+            for k, g in enumerate(graphs):
+                evs[k][0].record(stream)
+                g.replay()
+                evs[k][1].record(stream)
+            torch.cuda.synchronize()
+            if it >= 2:
+                for r in range(N):
+                    part_ms[r].append(evs[r][0].elapsed_time(evs[r][1]))
+                apply_ms.append(evs[N][0].elapsed_time(evs[N][1]))
+        per_rank = [statistics.mean(m) for m in part_ms]
+        ap = statistics.mean(apply_ms)
+        out[str(N)] = {"rank_views": [v1 - v0 for v0, v1 in ranges], "rank_ms": per_rank,
+                       "sum_and_apply_ms": ap, "allreduce_bytes": 36 * P,
+                       "rank_ms_per_iteration": max(per_rank) + ap,
+                       "vs_single_graph": serial_ms / (max(per_rank) + ap),
+                       "finite": bool(torch.isfinite(R.maps()).all().item())}
+        del graphs
+        R.close()
+    return {"note": "rank-local work of an N-way view split measured on one GPU (every share run in turn "
+                    "as a CUDA graph); N GPUs add one all-reduce of allreduce_bytes per iteration, not included",
+            "split": out}
 
 
 def run_five_windows(args, w, f4, rank):
@@ -781,6 +858,9 @@ def main():
     ap.add_argument("--rate", type=float, default=1.5, help="Poisson request arrival rate, requests/s")
     ap.add_argument("--five-windows", type=int, default=20,
                     help="timed iterations of the five-window solve (0: skip)")
+    ap.add_argument("--split", type=int, nargs="*", default=[2, 4, 8],
+                    help="view-split rank counts whose rank-local work is measured (none: skip)")
+    ap.add_argument("--split-steps", type=int, default=10, help="timed iterations per split")
     ap.add_argument("--nested", type=int, nargs="*", default=[1, 2, 4, 8],
                     help="iterations per local model for the nested MOCCA leg (none: skip)")
     args = ap.parse_args()

@@ -1589,11 +1589,28 @@ __device__ __forceinline__ void fpb_block(const GeomC& C, const FpTables& T, con
     const int l_lo = V0 * nb, l_hi = V1 * nb;
     float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const size_t e0 = (size_t)b * nch;
+    // PARTIAL: only the chunks whose views meet [V0, V1), a contiguous run of the
+    // group's chunks (the same for every thread of the block), so a rank streams
+    // the table of its own views only; the per-slot test below keeps the rays of
+    // a chunk that straddles V0 or V1 apart
+    int c_lo = 0, c_hi = nch;
+    if (PARTIAL) {
+        c_lo = nch;
+        c_hi = 0;
+        for (int c = 0; c < nch; ++c) {
+            int u0, u1;
+            chunk_views(C.n_views, g, G, T.bp_chunk, c, u0, u1);
+            if (u0 < u1 && u0 < V1 && u1 > V0) {
+                c_lo = min(c_lo, c);
+                c_hi = c + 1;
+            }
+        }
+    }
     const StageBuf B0(smem, S), B1(smem + stage_f4(S), S);
-    if (nch > 0) stage_entry(T, rec, steps, e0, B0);
-    for (int c = 0; c < nch; ++c) {
+    if (c_lo < c_hi) stage_entry(T, rec, steps, e0 + c_lo, (c_lo & 1) ? B1 : B0);
+    for (int c = c_lo; c < c_hi; ++c) {
         const StageBuf& B = (c & 1) ? B1 : B0;
-        if (c + 1 < nch) {   // the next chunk into the other buffer (free since the barrier ending chunk c - 1)
+        if (c + 1 < c_hi) {   // the next chunk into the other buffer (free since the barrier ending chunk c - 1)
             stage_entry(T, rec, steps, e0 + c + 1, (c & 1) ? B0 : B1);
             asm volatile("cp.async.wait_group 1;" ::: "memory");
         } else {
